@@ -1,0 +1,326 @@
+"""Pins of the FP64 CPU oracle to facts that do not come from the oracle itself:
+symbolic differentiation, exact polynomial identities, numerical quadrature of
+the defining integral, a second closed-form route (Gaussian mean-value
+property of harmonic polynomials), brute-force neighbor enumeration, symmetry
+invariances, and central finite differences.
+
+The method (GMP-Featurizer, arXiv 2303.12980): features = overlap of the
+Gaussian electron density with MCSH angular x Gaussian radial probes, grouped
+by (order, sigma) and reduced to rotation invariants; derivatives w.r.t.
+positions (Examples).  The integral definitions are those written in the
+header of oracle/gmp_oracle.c.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2303_12980_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ polynomials
+def _laplacian(poly):
+    out = {}
+    for (p, q, s), k in poly.items():
+        for ax, e in enumerate((p, q, s)):
+            if e >= 2:
+                m = [p, q, s]
+                m[ax] -= 2
+                out[tuple(m)] = out.get(tuple(m), 0) + k * e * (e - 1)
+    return {m: v for m, v in out.items() if v}
+
+
+def _pmul(a, b):
+    out = {}
+    for m1, v1 in a.items():
+        for m2, v2 in b.items():
+            m = (m1[0] + m2[0], m1[1] + m2[1], m1[2] + m2[2])
+            out[m] = out.get(m, 0) + v1 * v2
+    return {m: v for m, v in out.items() if v}
+
+
+def _r2pow(n):
+    p = {(0, 0, 0): 1}
+    for _ in range(n):
+        p = _pmul(p, {(2, 0, 0): 1, (0, 2, 0): 1, (0, 0, 2): 1})
+    return p
+
+
+def test_mcsh_matches_symbolic_differentiation(oracle_mod):
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    r = sp.sqrt(x * x + y * y + z * z)
+    for l in range(0, 5):
+        for (a, b, c) in oracle_mod.components(l):
+            expr = sp.expand(sp.simplify((-1) ** l * r ** (2 * l + 1) * sp.diff(1 / r, x, a, y, b, z, c)))
+            want = {}
+            for term in sp.Add.make_args(expr):
+                coef, mono = term.as_coeff_Mul()
+                pw = sp.Poly(mono, x, y, z).monoms()[0] if mono != 1 else (0, 0, 0)
+                want[tuple(int(t) for t in pw)] = int(coef)
+            assert oracle_mod.mcsh_poly(a, b, c) == want, (a, b, c)
+
+
+def test_mcsh_harmonic_and_sum_rule(oracle_mod):
+    # Laplacian zero; sum_abc l!/(a!b!c!) S_abc^2 = l! (2l-1)!! r^(2l)
+    for l in range(0, 7):
+        total = {}
+        for (a, b, c) in oracle_mod.components(l):
+            P = oracle_mod.mcsh_poly(a, b, c)
+            assert _laplacian(P) == {}, (a, b, c)
+            w = math.factorial(l) // (math.factorial(a) * math.factorial(b) * math.factorial(c))
+            for m, v in _pmul(P, P).items():
+                total[m] = total.get(m, 0) + w * v
+        dfact = 1
+        for k in range(2 * l - 1, 0, -2):
+            dfact *= k
+        want = {m: v * math.factorial(l) * dfact for m, v in _r2pow(l).items()}
+        assert total == want, l
+
+
+def test_mcsh_golden_low_orders(oracle_mod):
+    # tests/golden/mcsh_low_orders.txt: explicit polynomials of the
+    # definition S_abc = (-1)^l r^(2l+1) d^abc (1/r), written out by hand
+    with open(os.path.join(GOLDEN, "mcsh_low_orders.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            lhs, rhs = line.split(":")
+            a, b, c = (int(t) for t in lhs.split())
+            want = {}
+            for tok in rhs.split(","):
+                k, p, q, s = (int(t) for t in tok.split())
+                want[(p, q, s)] = k
+            assert oracle_mod.mcsh_poly(a, b, c) == want, line
+
+
+# ------------------------------------------------------------ tiny systems
+def _cluster(pos, species, orders, sigmas, coef, expo, n_gauss, cutoff=12.0):
+    pos = np.asarray(pos, np.float64)
+    return synth.Workload(
+        name="tiny", positions=pos, cells=np.zeros((1, 3, 3)), pbc=np.zeros((1, 3), np.uint8),
+        atom_off=np.array([0, len(pos)], np.int64), species=np.asarray(species, np.int32),
+        n_gauss=np.asarray(n_gauss, np.int32), gauss_coef=np.asarray(coef, np.float64),
+        gauss_exp=np.asarray(expo, np.float64), orders=list(orders), sigmas=list(sigmas), cutoff=cutoff)
+
+
+def test_order0_single_pair_matches_1d_quadrature(oracle_mod):
+    from scipy.integrate import quad
+    d = np.array([0.7, -0.4, 1.1])
+    alpha, c, sig = 1.3, 0.8, 0.45
+    w = _cluster([[0, 0, 0], d], [0, 0], [0], [sig], [c], [alpha], [1])
+    mu = oracle_mod.features(w, [0], want_mu=True)[1][0]
+    beta = 1.0 / (2 * sig * sig)
+    Ns = (2 * math.pi * sig * sig) ** -1.5
+
+    def axis(dd):
+        return quad(lambda t: math.exp(-beta * t * t - alpha * (t - dd) ** 2), -20, 20, epsabs=0, epsrel=1e-13)[0]
+
+    want = c * Ns * (np.prod([axis(0.0)] * 3) + np.prod([axis(v) for v in d]))
+    assert abs(mu[0] - want) <= 1e-12 * abs(want)
+
+
+def test_moments_match_3d_quadrature(oracle_mod):
+    # two atoms, one element with two Gaussians, orders 0..3, one sigma:
+    # mu_{l,abc} = int N_s S_abc(r) exp(-beta r^2) rho(r) d^3r on a grid
+    pos = np.array([[0.0, 0.0, 0.0], [0.9, -0.6, 0.5], [-0.5, 0.8, -0.7]])
+    coef, expo = [0.7, 0.4], [1.6, 0.6]
+    sig = 0.55
+    w = _cluster(pos, [0, 0, 0], [0, 1, 2, 3], [sig], coef, expo, [2])
+    mu = oracle_mod.features(w, [0], want_mu=True)[1][0]
+    h = 0.05
+    g = np.arange(-5.0, 5.0 + h / 2, h)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    beta = 1.0 / (2 * sig * sig)
+    Ns = (2 * math.pi * sig * sig) ** -1.5
+    rho = np.zeros_like(X)
+    for p in pos:
+        R2 = (X - p[0]) ** 2 + (Y - p[1]) ** 2 + (Z - p[2]) ** 2
+        for c, a in zip(coef, expo):
+            rho += c * np.exp(-a * R2)
+    base = Ns * np.exp(-beta * (X * X + Y * Y + Z * Z)) * rho * h ** 3
+    col = 0
+    for l in [0, 1, 2, 3]:
+        for (a, b, c) in oracle_mod.components(l):
+            P = oracle_mod.mcsh_poly(a, b, c)
+            S = sum(k * X ** pp * Y ** qq * Z ** ss for (pp, qq, ss), k in P.items())
+            want = float(np.sum(S * base))
+            scale = float(np.sum(np.abs(S) * base))
+            assert abs(mu[col] - want) <= 1e-9 * scale, (l, a, b, c, mu[col], want)
+            col += 1
+
+
+def test_factorised_route_agrees(oracle_mod):
+    # Mean-value property: the Gaussian average of a harmonic polynomial is
+    # its value at the Gaussian's centre, so each overlap integral equals
+    # c N_s (pi/g)^1.5 (alpha/g)^l exp(-(alpha beta/g) r^2) S_abc(d).
+    w = synth.workload("random64_box")
+    centers = np.array([0, 5, 17, 40])
+    f, mu = oracle_mod.features(w, centers, want_mu=True)
+    off, j, sh, d = oracle_mod.neighbors(w, centers)
+    go = w.gauss_off
+    col = 0
+    cols = []
+    for l in w.orders:
+        for s in range(len(w.sigmas)):
+            for abc in oracle_mod.components(l):
+                cols.append((l, s, abc))
+    for t in range(len(centers)):
+        dd = d[off[t]:off[t + 1]]
+        r2 = (dd * dd).sum(1)
+        ee = w.species[j[off[t]:off[t + 1]]]
+        for col, (l, s, abc) in enumerate(cols):
+            sig = w.sigmas[s]
+            beta = 1 / (2 * sig * sig)
+            P = oracle_mod.mcsh_poly(*abc)
+            S = sum(k * dd[:, 0] ** p * dd[:, 1] ** q * dd[:, 2] ** r for (p, q, r), k in P.items())
+            R = np.zeros_like(r2)
+            for e in range(w.n_elements):
+                m = ee == e
+                for k in range(go[e], go[e + 1]):
+                    a, c = w.gauss_exp[k], w.gauss_coef[k]
+                    gm = a + beta
+                    R[m] += c * (2 * math.pi * sig * sig) ** -1.5 * (math.pi / gm) ** 1.5 * (a / gm) ** l * \
+                        np.exp(-(a * beta / gm) * r2[m])
+            want = float(np.sum(R * S))
+            scale = float(np.sum(np.abs(R * S)))
+            assert abs(mu[t, col] - want) <= 1e-12 * scale + 1e-300
+
+
+def test_density_order_matches_direct_sum(oracle_mod):
+    w = synth.workload("random64_box").replace(orders=[-1, 0])
+    f = oracle_mod.features(w, [3, 9])
+    off, j, sh, d = oracle_mod.neighbors(w, [3, 9])
+    go = w.gauss_off
+    for t in range(2):
+        dd = d[off[t]:off[t + 1]]
+        r2 = (dd * dd).sum(1)
+        rho = 0.0
+        for jj, rr in zip(j[off[t]:off[t + 1]], r2):
+            e = w.species[jj]
+            rho += sum(w.gauss_coef[k] * math.exp(-w.gauss_exp[k] * rr) for k in range(go[e], go[e + 1]))
+        assert abs(f[t, 0] - rho) <= 1e-13 * rho
+
+
+# ------------------------------------------------------------ neighbors
+def test_neighbors_match_brute_force(oracle_mod):
+    w = synth.workload("random64_box")
+    off, j, sh, d = oracle_mod.neighbors(w)
+    got = set()
+    for i in range(w.n_atoms):
+        for t in range(off[i], off[i + 1]):
+            got.add((i, int(j[t]), *map(int, sh[t])))
+    A = w.cells[0]
+    rc2 = w.cutoff * w.cutoff
+    want = set()
+    x = w.positions
+    rng = range(-3, 4)  # cell 10 A, cutoff 6 A: |n| <= 2 suffices
+    for n1 in rng:
+        for n2 in rng:
+            for n3 in rng:
+                shift = (n1 * A[0] + n2 * A[1]) + n3 * A[2]
+                D = (x[None, :, :] - x[:, None, :]) + shift
+                r2 = (D[..., 0] * D[..., 0] + D[..., 1] * D[..., 1]) + D[..., 2] * D[..., 2]
+                for i, jj in zip(*np.nonzero(r2 < rc2)):
+                    want.add((int(i), int(jj), n1, n2, n3))
+    assert got == want
+    # ordering: (j, n) ascending within each center
+    for i in range(w.n_atoms):
+        keys = [(int(j[t]), *map(int, sh[t])) for t in range(off[i], off[i + 1])]
+        assert keys == sorted(keys)
+
+
+def test_neighbors_cluster_has_no_images(oracle_mod):
+    w = synth.batched10k(n_struct=6)
+    off, j, sh, d = oracle_mod.neighbors(w)
+    for s in range(w.n_struct):
+        a0, a1 = w.atom_off[s], w.atom_off[s + 1]
+        for i in range(a0, a1):
+            js = j[off[i]:off[i + 1]]
+            assert np.all((js >= a0) & (js < a1))
+            if not w.pbc[s].any():
+                assert np.all(sh[off[i]:off[i + 1]] == 0)
+                # a cluster: exactly the atoms within the cutoff, self included
+                r = np.linalg.norm(w.positions[a0:a1] - w.positions[i], axis=1)
+                assert len(js) == int(np.sum(r < w.cutoff))
+
+
+# ------------------------------------------------------------ invariances
+def _rel(a, b, floor):
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), floor))
+
+
+def test_rotation_translation_permutation_invariance(oracle_mod):
+    w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2, 3, 4])
+    f0, fa = oracle_mod.features(w, want_abs=True)
+    floor = 1e-9 * fa
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    wr = w.replace(positions=w.positions @ Q.T + np.array([0.3, -1.7, 2.2]), cells=w.cells @ Q.T)
+    assert _rel(oracle_mod.features(wr), f0, floor) < 1e-10
+    perm = rng.permutation(w.n_atoms)
+    wp = w.replace(positions=w.positions[perm], species=w.species[perm])
+    assert _rel(oracle_mod.features(wp), f0[perm], floor[perm]) < 1e-12
+    # moving one atom by a lattice vector changes nothing
+    pos = w.positions.copy()
+    pos[11] += 2 * w.cells[0][0] - w.cells[0][2]
+    assert _rel(oracle_mod.features(w.replace(positions=pos)), f0, floor) < 1e-12
+
+
+def test_supercell_replication(oracle_mod):
+    w = synth.workload("random64_box")
+    A = w.cells[0]
+    reps = [(a, b, c) for a in range(2) for b in range(2) for c in range(2)]
+    pos = np.concatenate([w.positions + a * A[0] + b * A[1] + c * A[2] for a, b, c in reps])
+    ws = w.replace(positions=pos, species=np.tile(w.species, 8), cells=(2 * A)[None],
+                   atom_off=np.array([0, 8 * w.n_atoms]))
+    f0, fa = oracle_mod.features(w, want_abs=True)
+    centers = np.array([0, 64 + 3, 5 * 64 + 30, 7 * 64 + 63])
+    fs = oracle_mod.features(ws, centers)
+    assert _rel(fs, f0[centers % 64], 1e-12 * fa[centers % 64]) < 1e-11
+
+
+# ------------------------------------------------------------ gradients
+def test_jacobian_matches_central_differences(oracle_mod):
+    w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2])
+    atoms = [2, 33]
+    h = 1e-4
+    centers = np.arange(w.n_atoms)
+    joff, jj, jac = oracle_mod.jacobian_rows(w, centers)
+    off, j, sh, d = oracle_mod.neighbors(w)
+    r = np.linalg.norm(d, axis=1)
+    for a in atoms:
+        for ax in range(3):
+            pp = w.positions.copy()
+            pm = w.positions.copy()
+            pp[a, ax] += h
+            pm[a, ax] -= h
+            fp = oracle_mod.features(w.replace(positions=pp), centers)
+            fm = oracle_mod.features(w.replace(positions=pm), centers)
+            fd = (fp - fm) / (2 * h)
+            for i in centers:
+                # skip centers with a pair involving atom a within 2h of the cutoff
+                seg = slice(off[i], off[i + 1])
+                near = np.abs(r[seg] - w.cutoff) < 4 * h
+                if near.any() and (i == a or np.any(j[seg][near] == a)):
+                    continue
+                row = np.searchsorted(jj[joff[i]:joff[i + 1]], a)
+                an = np.zeros(w.n_features)
+                if row < joff[i + 1] - joff[i] and jj[joff[i] + row] == a:
+                    an = jac[joff[i] + row, :, ax]
+                scale = np.max(np.abs(jac[joff[i]:joff[i + 1]]), axis=(0, 2)) + 1e-30
+                assert np.all(np.abs(fd[i] - an) <= 1e-6 * scale), (a, ax, i)
+
+
+def test_jacobian_translation_sum_rule(oracle_mod):
+    w = synth.workload("random64_box")
+    joff, jj, jac = oracle_mod.jacobian_rows(w, np.arange(10))
+    for t in range(10):
+        blk = jac[joff[t]:joff[t + 1]]
+        assert np.all(np.abs(blk.sum(0)) <= 1e-11 * np.abs(blk).sum(0).max())
