@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of GMP features + position gradients on GB300.
+
+One step = the whole hot path on one batch of synthetic input resident in
+HBM: exact neighbor images (binning, FP32 pre-screen, FP64-exact cutoff
+decision), per-center MCSH moments and rotation-invariant features, and the
+vector-Jacobian product of a fixed upstream gradient (forces), all through
+the C ABI (gmp_featurize_vjp).  Default workload: the 262,144-atom FCC alloy
+slab (orders 0-6, 16 sigmas, cutoff 8 A).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on the host cores instead (bounded sample of centers per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "atom-features/sec (features + grads)"
+UNIT = "atom-features/s"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ work model
+def work_model(w, pairs: int):
+    """Algorithmic work per step (forward + VJP), per neighbor pair:
+    EX2 = n_sigma K, FMA_fwd = n_sigma K (1 + n_l) + n_sigma C + 2C
+    (C = Cartesian MCSH components of the requested orders), the VJP costing
+    2.5x the forward FMAs and one more set of exps (recompute)."""
+    orders = [l for l in w.orders if l >= 0]
+    n_l = len(orders)
+    C = sum((l + 1) * (l + 2) // 2 for l in orders)
+    ns = len(w.sigmas)
+    # mean primitives per neighbor, weighted by species frequency
+    counts = np.bincount(w.species, minlength=w.n_elements)
+    K = float(np.dot(counts, w.n_gauss) / counts.sum())
+    fma_fwd = ns * K * (1 + n_l) + ns * C + 2 * C
+    fma = 3.5 * fma_fwd * pairs
+    ex2 = 2 * ns * K * pairs
+    return {"fma_per_pair_fwd": fma_fwd, "flop_step": 2.0 * fma, "ex2_step": ex2}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2303_12980_gb300 import build as B, synth
+    B.build()
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.workload)
+    N, F_ = w.n_atoms, w.n_features
+    Fz = GMPFeaturizer.from_workload(w, device=local_rank)
+    pos = torch.from_numpy(w.positions).to(dev)
+    sp = torch.from_numpy(w.species).to(dev)
+    g_np = synth.upstream_gradient(N, F_, seed=2024 + rank)
+    g = torch.from_numpy(g_np).to(dev)
+    feat = torch.empty((N, F_), dtype=torch.float32, device=dev)
+    gp = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    noff, _, _ = Fz.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+    pairs = int(noff[-1].item())
+    wm = work_model(w, pairs)
+
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    Fz.profile(True)
+    launches0 = Fz.kernel_launches
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = Fz.kernel_launches - launches0
+    prof = Fz.profile_read()
+    Fz.profile(False)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * args.steps * N * F_ / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (fused forward + VJP), timed live by
+    # CUDA events on the launching stream inside the library
+    comp_ms, comp_n = prof["compute"]
+    nbr_ms, nbr_n = prof["neighbors"]
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * 2070e6 / 1e12   # FP32 FMA lanes x 2 FLOP x max SM clock
+    achieved = wm["flop_step"] / (comp_ms / comp_n * 1e-3) / 1e12 if comp_n else None
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(w.positions).pin_memory()
+        sp_h = torch.from_numpy(w.species).pin_memory()
+        g_h = torch.from_numpy(g_np).pin_memory()
+        feat_h = torch.empty((N, F_), dtype=torch.float32).pin_memory()
+        gp_h = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+        Fz.featurize_vjp(pos_h, sp_h, w.atom_off, w.cells, w.pbc, g_h, out=(feat_h, gp_h))
+        ke = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            Fz.featurize_vjp(pos_h, sp_h, w.atom_off, w.cells, w.pbc, g_h, out=(feat_h, gp_h))
+        te = (time.perf_counter() - t0) / ke
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * N * F_ / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(N * 3 * 8 + N * 4 + N * F_ * 4),
+               "d2h_bytes_per_step": int(N * F_ * 4 + N * 3 * 4)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "atoms": N, "structures": w.n_struct, "features": F_,
+                   "orders": w.orders, "n_sigmas": len(w.sigmas), "cutoff": w.cutoff, "pairs": pairs,
+                   "step": "neighbors + features + VJP (forces), gmp_featurize_vjp",
+                   "l2": "256 MB buffer written between timed steps (outside the step events)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": "k_vjp (fused forward + VJP)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None,
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
+                     "algorithmic_flop_per_step": wm["flop_step"], "ex2_per_step": wm["ex2_step"],
+                     "kernel_ms": comp_ms / comp_n if comp_n else None,
+                     "neighbor_stage_ms": nbr_ms / nbr_n if nbr_n else None},
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], acc = cpu_baseline(w, feat, gp, g_np, budget_s=args.cpu_budget)
+        out["accuracy"] = acc
+    return out
+
+
+def _oracle_sample(w, centers):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.jacobian_rows(w, centers)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, feat_dev, gp_dev, g_np, budget_s=15.0):
+    """The FP64 oracle (features + full position derivatives of sampled
+    centers) timed on the host cores; the same sample checks accuracy."""
+    from oracle import oracle as O
+    from paper_2303_12980_gb300 import synth
+    O.build()
+    n = 16
+    c = synth.subset_centers(w.n_atoms, n, seed=11)
+    dt = _oracle_sample(w, c)
+    n = int(max(16, min(4096, n * budget_s / max(dt, 1e-3))))
+    c = synth.subset_centers(w.n_atoms, n, seed=11)
+    t0 = time.perf_counter()
+    f_ref, f_abs = O.features(w, c, want_abs=True)
+    O.jacobian_rows(w, c)
+    dt = time.perf_counter() - t0
+    base = {"value": n * w.n_features / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} random centers of {w.name}: FP64 features + d(features)/d(positions) rows"}
+    f = feat_dev.cpu().numpy()[c]
+    ferr = float(np.max(np.abs(f - f_ref) / np.maximum(np.abs(f_ref), 1e-6 * f_abs)))
+    atoms = synth.subset_centers(w.n_atoms, 4, seed=12)
+    gref, gscale = O.vjp_atoms(w, g_np, atoms, want_abs=True)
+    gerr = float(np.max(np.linalg.norm(gp_dev.cpu().numpy()[atoms] - gref, axis=1)
+                        / np.maximum(np.linalg.norm(gref, axis=1), 1e-3 * gscale)))
+    acc = {"features_max_rel_err": ferr, "grad_max_rel_err": gerr,
+           "sample": f"{n} centers (features), 4 atoms (VJP)",
+           "floors": "features: max(|f|, 1e-6 F_abs); grads: max(|g|, 1e-3 G_abs)"}
+    return base, acc
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, each step a bounded sample of
+    centers of the same workload (features + position derivatives)."""
+    from oracle import oracle as O
+    from paper_2303_12980_gb300 import synth
+    O.build()
+    w = synth.workload(args.workload)
+    c0 = synth.subset_centers(w.n_atoms, 8, seed=21)
+    dt = _oracle_sample(w, c0)
+    per = int(max(8, min(2048, 8 * args.ref_step_s / max(dt, 1e-3))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        c = synth.subset_centers(w.n_atoms, per, seed=100 + k)
+        t = _oracle_sample(w, c)
+        if k >= args.warmup:
+            times.append(t)
+    ms = 1e3 * sum(times) / len(times)
+    value = per * w.n_features / (ms * 1e-3)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "atoms": w.n_atoms, "features": w.n_features,
+                   "step": f"{per} random centers: FP64 features + d(features)/d(positions)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{per} random centers per step of {w.name}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fcc_slab262k")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * gmp.h -- C ABI of libgmp: Gaussian Multipole (GMP) features of atomic
+ * structures and their position derivatives on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (GMP-Featurizer, arXiv 2303.12980):
+ *   Each atom's electron density is a sum of Gaussians c_k exp(-alpha_k r^2)
+ *   taken from per-element tables (Overview: pseudopotential files specify
+ *   the Gaussians; Examples: psp_path).  For every center atom i, the
+ *   density of all atoms within the cutoff -- periodic images included --
+ *   is projected on probes = MCSH angular function of order l times a
+ *   Gaussian radial function of width sigma (Examples: "orders", "sigmas");
+ *   the projections of one (l, sigma) group are reduced to one rotation
+ *   invariant number, the weighted sum of squares over the group's
+ *   components.  The feature set is the Cartesian product orders x sigmas,
+ *   order-major; order -1 is the local density at the center, one feature
+ *   (Examples, feature-set listing).  Derivatives of the features with
+ *   respect to atom positions are available (Examples: calc_derivatives,
+ *   feature_primes).
+ *
+ * Conventions for every call below:
+ *   - Units: Angstrom and Angstrom^-2.
+ *   - N = total atoms over a batch of S structures; structure s owns atoms
+ *     atom_off[s] .. atom_off[s+1]-1 (host array, int64, atom_off[0] = 0).
+ *   - pos [N,3] float64 raw Cartesian positions (no wrapping is applied to
+ *     the displacement: d = (x_j - x_i) + n1 a1 + n2 a2 + n3 a3).
+ *   - cell [S,3,3] float64 HOST array, rows are lattice vectors a1, a2, a3;
+ *     pbc [S,3] uint8 HOST array.  A structure with any periodic axis needs
+ *     a non-singular cell; a structure with none ignores its cell (zeros ok).
+ *   - species [N] int32 in 0 .. n_elements-1.
+ *   - pos, species and all outputs may be DEVICE pointers (the call is then
+ *     asynchronous on `stream`) or HOST pointers (pageable or pinned; the
+ *     call then stages copies through device memory and returns after the
+ *     results are in host memory).  Inputs and outputs of one call must be
+ *     all device or all host.
+ *   - The caller owns every buffer it passes; the handle owns its tables and
+ *     a growable device workspace (so concurrent calls on one handle must be
+ *     serialised by the caller).
+ *   - Errors are returned as gmp_status; gmp_last_error() gives a message.
+ *     Conditions detected on the device (bad species id, non-finite
+ *     position, too many neighbors of one center) are reported through a
+ *     device error word checked at the end of the call (device-pointer
+ *     calls synchronise `stream` once per call to read it).
+ */
+#ifndef GMP_H_
+#define GMP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmp_ctx *gmp_handle;
+
+typedef enum {
+  GMP_OK = 0,
+  GMP_ERR_INVALID_ARG = 1, /* bad sizes, pointers, orders, singular cell ... */
+  GMP_ERR_CUDA = 2,        /* a CUDA runtime call failed                      */
+  GMP_ERR_OOM = 3,         /* device allocation failed                        */
+  GMP_ERR_CAPACITY = 4,    /* caller buffer too small (see nnz_out)            */
+  GMP_ERR_TIMEOUT = 5,     /* gmp_sync timed out                               */
+  GMP_ERR_DEVICE = 6       /* a condition flagged by a kernel (see message)    */
+} gmp_status;
+
+/* Flags for gmp_params.flags. */
+#define GMP_FLAG_NONE 0u
+
+/* Probe set and density tables (Examples: the GMPs dictionary). */
+typedef struct {
+  int32_t n_elements;         /* species ids are 0 .. n_elements-1             */
+  const int32_t *n_gauss;     /* [n_elements] Gaussians per element (>= 1)     */
+  const double *gauss_coef;   /* [sum n_gauss] c_k (any sign)                   */
+  const double *gauss_exp;    /* [sum n_gauss] alpha_k > 0, Angstrom^-2         */
+  int32_t n_orders;           /* >= 1                                           */
+  const int32_t *orders;      /* each in {-1, 0, 1, ..., 6}, no repeats         */
+  int32_t n_sigmas;           /* >= 1 when any order >= 0                       */
+  const double *sigmas;       /* each > 0, Angstrom                             */
+  double cutoff;              /* > 0, Angstrom; hard cutoff |d| < cutoff        */
+  uint32_t flags;             /* GMP_FLAG_*                                     */
+} gmp_params;
+
+/* Create a handle on CUDA device `device`: validates `params`, copies the
+ * tables (host memory, read during the call only) and builds the per
+ * (element, sigma, primitive) radial prefactors on the device.
+ * Returns GMP_ERR_INVALID_ARG for any invalid field. */
+gmp_status gmp_create(const gmp_params *params, int device, gmp_handle *out);
+
+/* Number of features per atom F = (#orders >= 0) * n_sigmas + (#order -1). */
+gmp_status gmp_num_features(gmp_handle h, int32_t *F);
+
+/* Features of every atom (Examples: entry["features"]).
+ * features [N, F] float32, order-major: column (o, s) = o * n_sigmas + s for
+ * orders >= 0 in the order given, order -1 (if requested) at its own
+ * position in the order list with a single column. */
+gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                         const double *pos, const double *cell, const uint8_t *pbc,
+                         const int32_t *species, float *features, void *stream);
+
+/* Features and the vector-Jacobian product with an upstream gradient:
+ * grad_pos[j] = sum_i sum_f grad_feat[i, f] * d features[i, f] / d pos[j].
+ * grad_feat [N, F] float32 in; features [N, F] (may be NULL) and
+ * grad_pos [N, 3] float32 out.  This is the force path (autograd backward). */
+gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                             const double *pos, const double *cell, const uint8_t *pbc,
+                             const int32_t *species, const float *grad_feat,
+                             float *features, float *grad_pos, void *stream);
+
+/* Features and the dense per-(center, neighbor atom) Jacobian
+ * (Examples: entry["feature_primes"]).  Row i lists the distinct atoms j
+ * whose position moves feature row i (the center itself included), images
+ * of one atom summed:
+ *   jac_off [N+1] int64, jac_j [cap] int32 (ascending within a row),
+ *   jac [cap, F, 3] float32 = d features[i, :] / d pos[j, :].
+ * If the total nnz exceeds `cap`, nothing but *nnz_out is written and
+ * GMP_ERR_CAPACITY is returned; call again with cap >= *nnz_out.
+ * nnz_out is a host pointer; this call synchronises `stream`. */
+gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                                  const double *pos, const double *cell, const uint8_t *pbc,
+                                  const int32_t *species, float *features, int64_t *jac_off,
+                                  int32_t *jac_j, float *jac, int64_t cap, int64_t *nnz_out,
+                                  void *stream);
+
+/* Exact neighbor images (for checking; the featurize calls build their own).
+ * Pairs (i, j, n) with |(x_j - x_i) + n1 a1 + n2 a2 + n3 a3| < cutoff, the
+ * self pair included, decided in FP64 exactly as that expression reads
+ * (left to right, no FMA).  nbr_off [N+1] int64; nbr_j [cap] int32;
+ * nbr_shift [cap, 3] int32 (n1, n2, n3); each row ordered by (j, n1, n2, n3).
+ * Capacity semantics as in gmp_featurize_jacobian. */
+gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                         const double *pos, const double *cell, const uint8_t *pbc,
+                         const int32_t *species, int64_t *nbr_off, int32_t *nbr_j,
+                         int32_t *nbr_shift, int64_t cap, int64_t *nnz_out, void *stream);
+
+/* Wait for `stream` with a timeout (seconds, <= 0: wait forever) by polling
+ * an event; returns GMP_ERR_TIMEOUT if the work has not finished. */
+gmp_status gmp_sync(gmp_handle h, void *stream, double timeout_s);
+
+/* Message for the last non-OK status on this handle (never NULL). */
+const char *gmp_last_error(gmp_handle h);
+
+/* Number of kernels this handle has launched so far (diagnostics). */
+int64_t gmp_kernel_launches(gmp_handle h);
+
+/* Stage timing (diagnostics, not part of the method).  With enable != 0 the
+ * featurize calls record CUDA events on the caller's stream around
+ *   stage 0: neighbor search (binning, count, fill),
+ *   stage 1: the feature / VJP / Jacobian compute kernels;
+ * gmp_profile_read synchronises those events and writes, per stage, the
+ * summed milliseconds and the number of stage executions since the last
+ * read (arrays of length n_stages <= 2), then clears the counters. */
+gmp_status gmp_profile(gmp_handle h, int enable);
+gmp_status gmp_profile_read(gmp_handle h, double *ms, int64_t *count, int n_stages);
+
+/* Release the handle and its device memory. */
+void gmp_destroy(gmp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMP_H_ */

@@ -577,9 +577,13 @@ int oracle_jacobian_counts(const oracle_problem *P, int64_t n_centers, const int
 }
 
 /* For each listed center i: distinct neighbor atoms j (ascending) and the
- * blocks jac[., F, 3] = d f_i / d x_j.  Offsets from oracle_jacobian_counts. */
+ * blocks jac[., F, 3] = d f_i / d x_j.  Offsets from oracle_jacobian_counts.
+ * jac_abs (optional) [., F]: the cancellation-free scale of each block,
+ * sum over the block's pairs and components of 2 w_c A_c |d t_c / d d|
+ * with A_c = sum over pairs of |t_c| (same for the center's own block,
+ * summed over the other atoms' pairs); used to judge near-zero entries. */
 int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64_t *centers,
-                         const int64_t *offsets, int32_t *j_out, double *jac) {
+                         const int64_t *offsets, int32_t *j_out, double *jac, double *jac_abs) {
   octx X;
   if (ctx_init(&X, P)) return -1;
   const int F = X.F;
@@ -593,6 +597,9 @@ int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64
     double *dt = (double *)calloc(3 * (size_t)X.ncol + 1, sizeof(double));
     double *g = (double *)calloc(3 * (size_t)F, sizeof(double));   /* df/dd of one pair */
     double *self = (double *)calloc(3 * (size_t)F, sizeof(double));
+    double *ab = (double *)calloc((size_t)X.ncol + 1, sizeof(double));
+    double *ga = (double *)calloc((size_t)F, sizeof(double));
+    double *self_abs = (double *)calloc((size_t)F, sizeof(double));
 #pragma omp for schedule(dynamic, 1)
     for (int64_t ti = 0; ti < n_centers; ++ti) {
       const int64_t i = centers[ti];
@@ -600,12 +607,14 @@ int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64
       if (m < 0) { bad = 1; continue; }
       /* forward moments of this center */
       memset(mu, 0, sizeof(double) * X.ncol);
+      memset(ab, 0, sizeof(double) * X.ncol);
       for (int64_t u = 0; u < m; ++u) {
         double r;
         pair_terms(&X, P->species[buf[u].j], buf[u].d, t, NULL, &r, NULL);
-        for (int cI = 0; cI < X.ncol; ++cI) mu[cI] += t[cI];
+        for (int cI = 0; cI < X.ncol; ++cI) { mu[cI] += t[cI]; ab[cI] += fabs(t[cI]); }
       }
       memset(self, 0, sizeof(double) * 3 * F);
+      memset(self_abs, 0, sizeof(double) * F);
       int64_t row = offsets[ti] - 1, self_row = -1;
       for (int64_t u = 0; u < m; ++u) {
         if (u == 0 || buf[u].j != buf[u - 1].j) {
@@ -613,6 +622,7 @@ int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64
           if (row >= offsets[ti + 1]) { bad = 1; break; }
           j_out[row] = buf[u].j;
           memset(jac + row * 3 * F, 0, sizeof(double) * 3 * F);
+          if (jac_abs) memset(jac_abs + row * F, 0, sizeof(double) * F);
           if (buf[u].j == i) self_row = row;
         }
         double r, dr[3];
@@ -623,37 +633,47 @@ int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64
           int l = P->orders[o];
           if (l < 0) {
             for (int a = 0; a < 3; ++a) g[3 * f + a] = dr[a];
+            ga[f] = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
             ++f;
             continue;
           }
           for (int s = 0; s < X.n_sig; ++s, ++f) {
-            double gx = 0.0, gy = 0.0, gz = 0.0;
+            double gx = 0.0, gy = 0.0, gz = 0.0, gabs = 0.0;
             for (int ci = 0; ci < X.T.ncomp[l]; ++ci) {
               int col = col_of(&X, o, s, ci);
               double wmu2 = 2.0 * X.T.comp[l][ci].w * mu[col];
               gx += wmu2 * dt[3 * col + 0];
               gy += wmu2 * dt[3 * col + 1];
               gz += wmu2 * dt[3 * col + 2];
+              gabs += 2.0 * X.T.comp[l][ci].w * ab[col] *
+                      sqrt(dt[3 * col] * dt[3 * col] + dt[3 * col + 1] * dt[3 * col + 1] +
+                           dt[3 * col + 2] * dt[3 * col + 2]);
             }
             g[3 * f + 0] = gx; g[3 * f + 1] = gy; g[3 * f + 2] = gz;
+            ga[f] = gabs;
           }
         }
         /* d = x_j - x_i + shift: +g onto atom j; -g onto the center unless
          * j is the center itself (its images move with it). */
         double *blk = jac + row * 3 * F;
         for (int q = 0; q < 3 * F; ++q) blk[q] += g[q];
-        if (buf[u].j != i)
+        if (jac_abs)
+          for (int q = 0; q < F; ++q) jac_abs[row * F + q] += ga[q];
+        if (buf[u].j != i) {
           for (int q = 0; q < 3 * F; ++q) self[q] -= g[q];
+          for (int q = 0; q < F; ++q) self_abs[q] += ga[q];
+        }
       }
       if (self_row >= 0) {
         /* the center's own images cancel in pairs (d and -d) */
         double *blk = jac + self_row * 3 * F;
         memcpy(blk, self, sizeof(double) * 3 * F);
+        if (jac_abs) memcpy(jac_abs + self_row * F, self_abs, sizeof(double) * F);
       } else {
         bad = 1;
       }
     }
-    free(buf); free(mu); free(t); free(dt); free(g); free(self);
+    free(buf); free(mu); free(t); free(dt); free(g); free(self); free(ab); free(ga); free(self_abs);
   }
   return bad ? -1 : 0;
 }

@@ -76,7 +76,7 @@ def lib():
             L.oracle_neighbor_lists.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             L.oracle_features.argtypes = [P, C.c_int64, vp, vp, vp, vp]
             L.oracle_jacobian_counts.argtypes = [P, C.c_int64, vp, vp]
-            L.oracle_jacobian_rows.argtypes = [P, C.c_int64, vp, vp, vp, vp]
+            L.oracle_jacobian_rows.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -183,9 +183,11 @@ def features(w, centers=None, want_abs=False, want_mu=False):
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def jacobian_rows(w, centers=None):
+def jacobian_rows(w, centers=None, want_abs=False):
     """d f_i / d x_j for the listed centers: (offsets [nc+1], j [nnz],
-    jac [nnz, F, 3]); j ascending within each center's row."""
+    jac [nnz, F, 3]); j ascending within each center's row.  With want_abs,
+    also jac_abs [nnz, F]: the cancellation-free scale of each block (sum of
+    2 w_c A_c |d t_c / d d| over its pairs, A_c = sum of |t_c|)."""
     P = Problem(w)
     c = _centers(w, centers)
     counts = np.zeros(c.size, np.int64)
@@ -194,22 +196,28 @@ def jacobian_rows(w, centers=None):
     off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     j = np.zeros(off[-1], np.int32)
     jac = np.zeros((off[-1], P.F, 3), np.float64)
+    jab = np.zeros((off[-1], P.F), np.float64) if want_abs else None
     if lib().oracle_jacobian_rows(C.byref(P.s), c.size, c.ctypes.data, off.ctypes.data,
-                                  j.ctypes.data, jac.ctypes.data):
+                                  j.ctypes.data, jac.ctypes.data,
+                                  jab.ctypes.data if want_abs else None):
         raise RuntimeError("jacobian failed")
+    if want_abs:
+        return off, j, jac, jab
     return off, j, jac
 
 
-def vjp_atoms(w, g, atoms):
+def vjp_atoms(w, g, atoms, want_abs=False):
     """dL/dx_a = sum_i sum_f g[i,f] d f_i / d x_a for the listed atoms.
     The centers that see atom a are exactly the atoms in a's own neighbor
-    list (the neighbor relation is symmetric), so only those rows are built."""
+    list (the neighbor relation is symmetric), so only those rows are built.
+    With want_abs also the scale sum_i sum_f |g[i,f]| jac_abs[i,f,a]."""
     atoms = np.ascontiguousarray(atoms, np.int64)
     off, j, _, _ = neighbors(w, atoms)
     need = np.unique(j.astype(np.int64))
-    joff, jj, jac = jacobian_rows(w, need)
+    joff, jj, jac, jab = jacobian_rows(w, need, want_abs=True)
     row_of = {int(c): k for k, c in enumerate(need)}
     out = np.zeros((atoms.size, 3), np.float64)
+    scale = np.zeros(atoms.size, np.float64)
     for t, a in enumerate(atoms):
         centers_a = np.unique(j[off[t]:off[t + 1]])
         for ci in centers_a:
@@ -217,5 +225,9 @@ def vjp_atoms(w, g, atoms):
             js = jj[joff[k]:joff[k + 1]]
             pos = np.searchsorted(js, a)
             if pos < js.size and js[pos] == a:
-                out[t] += np.einsum("f,fk->k", g[ci].astype(np.float64), jac[joff[k] + pos])
+                gi = g[ci].astype(np.float64)
+                out[t] += np.einsum("f,fk->k", gi, jac[joff[k] + pos])
+                scale[t] += np.abs(gi) @ jab[joff[k] + pos]
+    if want_abs:
+        return out, scale
     return out

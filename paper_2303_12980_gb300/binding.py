@@ -1,0 +1,336 @@
+"""Thin Python binding of libgmp (include/gmp.h): argument marshalling only.
+
+Every step of the featurization runs in the CUDA library; this module only
+checks shapes and dtypes, passes pointers and the current CUDA stream, and
+turns status codes into exceptions.  There is no CPU fallback: if the
+library is missing or fails to load, an ImportError / RuntimeError is
+raised.
+
+Naming follows GMP-Featurizer (arXiv 2303.12980, Examples): "orders" are the
+MCSH angular probe orders (-1 = local density), "sigmas" the Gaussian radial
+probe widths; features are ordered order-major; the position derivatives are
+"feature_primes" (here: a CSR Jacobian) or, for training, a vector-Jacobian
+product.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgmp.so")
+
+GMP_OK = 0
+_STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
+           5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
+EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp",
+           "gmp_featurize_jacobian", "gmp_neighbors", "gmp_sync", "gmp_profile", "gmp_profile_read",
+           "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class GMPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("n_elements", C.c_int32),
+        ("n_gauss", C.c_void_p),
+        ("gauss_coef", C.c_void_p),
+        ("gauss_exp", C.c_void_p),
+        ("n_orders", C.c_int32),
+        ("orders", C.c_void_p),
+        ("n_sigmas", C.c_int32),
+        ("sigmas", C.c_void_p),
+        ("cutoff", C.c_double),
+        ("flags", C.c_uint32),
+    ]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgmp.so (built by paper_2303_12980_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libgmp.so not found at {path}; build it with "
+                              "paper_2303_12980_gb300.build.build() (needs nvcc)")
+        L = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.gmp_create.argtypes = [C.POINTER(_Params), C.c_int, C.POINTER(vp)]
+        L.gmp_num_features.argtypes = [vp, C.POINTER(i32)]
+        common = [vp, i32, vp, vp, vp, vp, vp]
+        L.gmp_featurize.argtypes = common + [vp, vp]
+        L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
+        L.gmp_featurize_jacobian.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_sync.argtypes = [vp, vp, C.c_double]
+        L.gmp_profile.argtypes = [vp, C.c_int]
+        L.gmp_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.c_int]
+        L.gmp_last_error.argtypes = [vp]
+        L.gmp_last_error.restype = C.c_char_p
+        L.gmp_kernel_launches.argtypes = [vp]
+        L.gmp_kernel_launches.restype = i64
+        L.gmp_destroy.argtypes = [vp]
+        L.gmp_destroy.restype = None
+        for name in EXPORTS[:-3]:
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_ptr(stream, on_device: bool):
+    if not on_device:
+        return None
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class GMPFeaturizer:
+    """Handle on a GMP probe set + density tables on one CUDA device.
+
+    orders: MCSH orders (each -1..6), sigmas: radial widths (A), cutoff (A),
+    n_gauss/gauss_coef/gauss_exp: per-element Gaussian densities
+    rho_e(r) = sum_k c_k exp(-alpha_k r^2).
+    """
+
+    def __init__(self, orders, sigmas, cutoff, n_gauss, gauss_coef, gauss_exp, device: int = 0,
+                 flags: int = 0):
+        self._L = load_library()
+        self.orders = [int(o) for o in orders]
+        self.sigmas = [float(s) for s in sigmas]
+        self.cutoff = float(cutoff)
+        self.device = int(device)
+        self._keep = dict(
+            n_gauss=np.ascontiguousarray(n_gauss, np.int32),
+            coef=np.ascontiguousarray(gauss_coef, np.float64),
+            expo=np.ascontiguousarray(gauss_exp, np.float64),
+            orders=np.ascontiguousarray(self.orders, np.int32),
+            sigmas=np.ascontiguousarray(self.sigmas if self.sigmas else [1.0], np.float64),
+        )
+        k = self._keep
+        p = _Params(n_elements=k["n_gauss"].size, n_gauss=k["n_gauss"].ctypes.data,
+                    gauss_coef=k["coef"].ctypes.data, gauss_exp=k["expo"].ctypes.data,
+                    n_orders=len(self.orders), orders=k["orders"].ctypes.data,
+                    n_sigmas=len(self.sigmas), sigmas=k["sigmas"].ctypes.data,
+                    cutoff=self.cutoff, flags=int(flags))
+        h = C.c_void_p()
+        st = self._L.gmp_create(C.byref(p), self.device, C.byref(h))
+        if st != GMP_OK:
+            raise GMPError(st, "gmp_create rejected the parameters (see stderr)")
+        self._h = h
+        F = C.c_int32()
+        self._check(self._L.gmp_num_features(self._h, C.byref(F)))
+        self.num_features = int(F.value)
+
+    @classmethod
+    def from_workload(cls, w, device: int = 0):
+        return cls(w.orders, w.sigmas, w.cutoff, w.n_gauss, w.gauss_coef, w.gauss_exp, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.gmp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != GMP_OK:
+            msg = self._L.gmp_last_error(self._h)
+            raise GMPError(st, msg.decode() if msg else "")
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._L.gmp_kernel_launches(self._h))
+
+    # ---------------------------------------------------------------- inputs
+    @staticmethod
+    def _struct(atom_off, cell, pbc):
+        off = np.ascontiguousarray(atom_off, np.int64)
+        S = off.size - 1
+        cell = np.ascontiguousarray(np.asarray(cell, np.float64).reshape(S, 3, 3))
+        pbc = np.ascontiguousarray(np.asarray(pbc, np.uint8).reshape(S, 3))
+        return off, cell, pbc
+
+    def _inputs(self, pos, species):
+        torch = _torch()
+        on_dev = isinstance(pos, torch.Tensor) and pos.is_cuda
+        if isinstance(pos, torch.Tensor):
+            if pos.dtype != torch.float64 or not pos.is_contiguous() or pos.dim() != 2 or pos.shape[1] != 3:
+                raise ValueError("pos must be a contiguous float64 [N,3] tensor")
+            if species.dtype != torch.int32 or not species.is_contiguous() or species.is_cuda != on_dev:
+                raise ValueError("species must be a contiguous int32 tensor on the same device as pos")
+            if not on_dev:
+                pos, species = pos.numpy(), species.numpy()
+        else:
+            pos = np.ascontiguousarray(pos, np.float64)
+            species = np.ascontiguousarray(species, np.int32)
+        return pos, species, on_dev
+
+    def _alloc(self, shape, dtype, on_dev, like=None):
+        torch = _torch()
+        if on_dev:
+            return torch.empty(shape, dtype=dtype, device=like.device)
+        return torch.empty(shape, dtype=dtype).pin_memory() if torch.cuda.is_available() else \
+            torch.empty(shape, dtype=dtype)
+
+    # ----------------------------------------------------------------- calls
+    def featurize(self, pos, species, atom_off, cell, pbc, out=None, stream=None):
+        """features [N, F] float32 (device tensor for device inputs)."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        N = int(off[-1])
+        feat = out if out is not None else self._alloc((N, self.num_features), torch.float32, on_dev, pos)
+        self._check(self._L.gmp_featurize(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                          pbc.ctypes.data, _ptr(species), _ptr(feat),
+                                          _stream_ptr(stream, on_dev)))
+        return feat
+
+    def featurize_vjp(self, pos, species, atom_off, cell, pbc, grad_feat, want_features=True,
+                      stream=None, out=None):
+        """(features or None, grad_pos [N,3] float32) with
+        grad_pos[j] = sum_{i,f} grad_feat[i,f] d features[i,f] / d pos[j]."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        N = int(off[-1])
+        if isinstance(grad_feat, np.ndarray):
+            grad_feat = torch.from_numpy(np.ascontiguousarray(grad_feat, np.float32))
+        if grad_feat.dtype != torch.float32 or tuple(grad_feat.shape) != (N, self.num_features):
+            raise ValueError("grad_feat must be float32 [N, F]")
+        grad_feat = grad_feat.contiguous()
+        if out is not None:
+            feat, gp = out
+        else:
+            feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos) if want_features else None
+            gp = self._alloc((N, 3), torch.float32, on_dev, pos)
+        self._check(self._L.gmp_featurize_vjp(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                              pbc.ctypes.data, _ptr(species), _ptr(grad_feat), _ptr(feat),
+                                              _ptr(gp), _stream_ptr(stream, on_dev)))
+        return feat, gp
+
+    def featurize_jacobian(self, pos, species, atom_off, cell, pbc, stream=None):
+        """(features [N,F], jac_off [N+1] int64, jac_j [nnz] int32, jac [nnz,F,3] float32):
+        jac[r] = d features[i] / d pos[jac_j[r]] for r in jac_off[i]:jac_off[i+1]."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        N = int(off[-1])
+        feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos)
+        joff = self._alloc((N + 1,), torch.int64, on_dev, pos)
+        nnz = C.c_int64()
+        st = self._L.gmp_featurize_jacobian(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                            pbc.ctypes.data, _ptr(species), _ptr(feat), _ptr(joff), None, None,
+                                            0, C.byref(nnz), _stream_ptr(stream, on_dev))
+        if st not in (GMP_OK, 4):
+            self._check(st)
+        cap = int(nnz.value)
+        jj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
+        jac = self._alloc((max(cap, 1), self.num_features, 3), torch.float32, on_dev, pos)
+        self._check(self._L.gmp_featurize_jacobian(self._h, off.size - 1, off.ctypes.data, _ptr(pos),
+                                                   cell.ctypes.data, pbc.ctypes.data, _ptr(species), _ptr(feat),
+                                                   _ptr(joff), _ptr(jj), _ptr(jac), cap, C.byref(nnz),
+                                                   _stream_ptr(stream, on_dev)))
+        return feat, joff, jj[:cap], jac[:cap]
+
+    def neighbors(self, pos, species, atom_off, cell, pbc, stream=None):
+        """Exact neighbor images: (nbr_off [N+1], nbr_j [P], nbr_shift [P,3])."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        N = int(off[-1])
+        noff = self._alloc((N + 1,), torch.int64, on_dev, pos)
+        nnz = C.c_int64()
+        st = self._L.gmp_neighbors(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                   pbc.ctypes.data, _ptr(species), _ptr(noff), None, None, 0, C.byref(nnz),
+                                   _stream_ptr(stream, on_dev))
+        if st not in (GMP_OK, 4):
+            self._check(st)
+        cap = int(nnz.value)
+        nj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
+        ns = self._alloc((max(cap, 1), 3), torch.int32, on_dev, pos)
+        self._check(self._L.gmp_neighbors(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                          pbc.ctypes.data, _ptr(species), _ptr(noff), _ptr(nj), _ptr(ns), cap,
+                                          C.byref(nnz), _stream_ptr(stream, on_dev)))
+        return noff, nj[:cap], ns[:cap]
+
+    def profile(self, enable: bool = True):
+        """Per-stage CUDA-event timing on the caller's stream (diagnostics)."""
+        self._check(self._L.gmp_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """{'neighbors': (ms, count), 'compute': (ms, count)} since the last read."""
+        ms = (C.c_double * 2)()
+        cnt = (C.c_int64 * 2)()
+        self._check(self._L.gmp_profile_read(self._h, ms, cnt, 2))
+        return {"neighbors": (ms[0], cnt[0]), "compute": (ms[1], cnt[1])}
+
+    def sync(self, stream=None, timeout_s: float = 0.0):
+        torch = _torch()
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        self._check(self._L.gmp_sync(self._h, s, float(timeout_s)))
+
+
+def _make_function():
+    torch = _torch()
+
+    class GMPFeatures(torch.autograd.Function):
+        """features = GMPFeatures.apply(pos, featurizer, species, atom_off, cell, pbc).
+
+        Forward: gmp_featurize.  Backward: gmp_featurize_vjp (recomputes the
+        per-neighbor terms from the saved positions; no per-pair storage)."""
+
+        @staticmethod
+        def forward(ctx, pos, featurizer, species, atom_off, cell, pbc):
+            ctx.featurizer = featurizer
+            ctx.meta = (species, atom_off, cell, pbc)
+            ctx.save_for_backward(pos)
+            return featurizer.featurize(pos.detach(), species, atom_off, cell, pbc)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (pos,) = ctx.saved_tensors
+            species, atom_off, cell, pbc = ctx.meta
+            _, gp = ctx.featurizer.featurize_vjp(pos.detach(), species, atom_off, cell, pbc,
+                                                 grad_out.contiguous().float(), want_features=False)
+            return gp.to(pos.dtype), None, None, None, None, None
+
+    return GMPFeatures
+
+
+_fn_cache = {}
+
+
+def gmp_features(pos, featurizer, species, atom_off, cell, pbc):
+    """Differentiable features (torch.autograd.Function around the C ABI)."""
+    if "f" not in _fn_cache:
+        _fn_cache["f"] = _make_function()
+    return _fn_cache["f"].apply(pos, featurizer, species, atom_off, cell, pbc)

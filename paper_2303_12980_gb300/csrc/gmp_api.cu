@@ -1,0 +1,861 @@
+// C ABI of libgmp (declared in include/gmp.h): validation, device tables,
+// workspace, and the launch sequences of the featurize calls.
+#include "gmp.h"
+#include "gmp_internal.cuh"
+#include "gmp_kernels.cuh"
+#include "gmp_launch.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+cudaError_t gmp_launch_struct_of(const int64_t* d_atom_off, int n_struct, int32_t* struct_of,
+                                 cudaStream_t stream, int64_t* launches);
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t n = need < 256 ? 256 : need + need / 8;  // grow with slack
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+struct PassData {
+  GmpPass pass;
+  int L;
+  int NS;
+  DevBuf rad;
+};
+
+}  // namespace
+
+struct gmp_ctx {
+  int device = 0;
+  int sm_count = 0;
+  // parameters
+  int n_el = 0;
+  std::vector<int> n_gauss;
+  std::vector<double> coef, alpha;
+  std::vector<int> orders;
+  std::vector<double> sigmas;
+  double cutoff = 0.0;
+  uint32_t flags = 0;
+  int F = 0;
+  int kmax = 0;
+  std::vector<PassData> passes;
+  DevBuf dens;
+  // cached structure description
+  std::vector<int64_t> last_off;
+  std::vector<double> last_cell;
+  std::vector<uint8_t> last_pbc;
+  int64_t n_bins = 0;
+  // workspace
+  DevBuf structs, grid, atom_off, struct_of, bbox, atom_xh, atom_xl, atom_u, atom_bin;
+  DevBuf bin_count, bin_cursor, bin_start, bin_y, counts, nbr_off, scan_tmp, pairs;
+  DevBuf scalars;  // err word, maxm, counter
+  DevBuf grad_acc, jac_counts;
+  DevBuf ktab;   // FP64 radial constants [n_el][n_sigmas][kmax][3] for the refinement kernel
+  DevBuf flagq;  // queued ill-conditioned features
+  DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp;
+  int64_t P = 0;  // pairs of the last neighbor build
+  int max_m = 0;
+  // pinned host scratch for small readbacks
+  int64_t* h_small = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  cudaEvent_t ev = nullptr;
+  // stage timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev[2];  // start/stop pairs per stage
+  size_t prof_used[2] = {0, 0};
+};
+
+namespace {
+
+gmp_status fail(gmp_ctx* h, gmp_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+gmp_status cuda_fail(gmp_ctx* h, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, GMP_ERR_OOM, std::string("device allocation failed in ") + where);
+  }
+  return fail(h, GMP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GMP_CK(expr, where)                      \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+int pad_sigmas(int n) { return n <= 4 ? 4 : (n <= 8 ? 8 : 16); }
+
+cudaError_t launch_compute(int L, int kind, int ns, const gmpk::KParams& K, cudaStream_t st, int sm,
+                           int64_t* launches) {
+  switch (L) {
+    case 0: return gmp_launch_compute_L0(kind, ns, K, st, sm, launches);
+    case 1: return gmp_launch_compute_L1(kind, ns, K, st, sm, launches);
+    case 2: return gmp_launch_compute_L2(kind, ns, K, st, sm, launches);
+    case 3: return gmp_launch_compute_L3(kind, ns, K, st, sm, launches);
+    case 4: return gmp_launch_compute_L4(kind, ns, K, st, sm, launches);
+    case 5: return gmp_launch_compute_L5(kind, ns, K, st, sm, launches);
+    case 6: return gmp_launch_compute_L6(kind, ns, K, st, sm, launches);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool inv3(const double* A, double* Ai) {
+  double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+               A[2] * (A[3] * A[7] - A[4] * A[6]);
+  double scale = 0.0;
+  for (int k = 0; k < 9; ++k) scale = std::fmax(scale, std::fabs(A[k]));
+  if (!(std::fabs(det) > 1e-12 * scale * scale * scale) || !std::isfinite(det)) return false;
+  Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  return true;
+}
+
+// Validates the batch description and uploads per-structure data when it
+// changed since the previous call.
+gmp_status upload_structures(gmp_ctx* h, int32_t S, const int64_t* atom_off, const double* cell,
+                             const uint8_t* pbc, cudaStream_t st) {
+  if (S < 1 || !atom_off) return fail(h, GMP_ERR_INVALID_ARG, "n_struct must be >= 1 with atom_off");
+  if (atom_off[0] != 0) return fail(h, GMP_ERR_INVALID_ARG, "atom_off[0] must be 0");
+  for (int s = 0; s < S; ++s)
+    if (atom_off[s + 1] < atom_off[s]) return fail(h, GMP_ERR_INVALID_ARG, "atom_off must be non-decreasing");
+  const int64_t N = atom_off[S];
+  if (N > (int64_t)INT32_MAX / 2) return fail(h, GMP_ERR_INVALID_ARG, "too many atoms");
+  if (!cell || !pbc) return fail(h, GMP_ERR_INVALID_ARG, "cell and pbc (host arrays) are required");
+  const bool same = (int64_t)h->last_off.size() == S + 1 &&
+                    std::memcmp(h->last_off.data(), atom_off, sizeof(int64_t) * (S + 1)) == 0 &&
+                    std::memcmp(h->last_cell.data(), cell, sizeof(double) * 9 * S) == 0 &&
+                    std::memcmp(h->last_pbc.data(), pbc, S * 3) == 0;
+  if (same) return GMP_OK;
+  std::vector<GmpStruct> info(S);
+  int64_t bin_base = 0;
+  for (int s = 0; s < S; ++s) {
+    GmpStruct& g = info[s];
+    std::memset(&g, 0, sizeof(g));
+    const double* A = cell + 9 * s;
+    bool any = false;
+    for (int k = 0; k < 3; ++k) {
+      g.periodic[k] = pbc[3 * s + k] ? 1 : 0;
+      any = any || g.periodic[k];
+    }
+    if (any) {
+      for (int k = 0; k < 9; ++k) {
+        if (!std::isfinite(A[k])) return fail(h, GMP_ERR_INVALID_ARG, "non-finite cell");
+        g.A[k] = A[k];
+      }
+      if (!inv3(g.A, g.Ainv))
+        return fail(h, GMP_ERR_INVALID_ARG, "singular cell for a structure with a periodic axis (structure " +
+                                                std::to_string(s) + ")");
+    } else {
+      for (int k = 0; k < 9; ++k) g.A[k] = g.Ainv[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    }
+    for (int k = 0; k < 3; ++k) {
+      double bk = std::sqrt(g.Ainv[k] * g.Ainv[k] + g.Ainv[3 + k] * g.Ainv[3 + k] + g.Ainv[6 + k] * g.Ainv[6 + k]);
+      g.reach[k] = h->cutoff * bk;
+      if (g.periodic[k] && g.reach[k] > 64.0)
+        return fail(h, GMP_ERR_INVALID_ARG, "cutoff spans more than 64 cell widths along a periodic axis");
+    }
+    for (int k = 0; k < 9; ++k) {
+      g.Ahi[k] = (float)g.A[k];
+      g.Alo[k] = (float)(g.A[k] - (double)g.Ahi[k]);
+    }
+    g.atom_base = atom_off[s];
+    g.n_atoms = (int32_t)(atom_off[s + 1] - atom_off[s]);
+    g.bin_base = bin_base;
+    g.bin_cap = 2 * g.n_atoms + 8;
+    bin_base += g.bin_cap;
+  }
+  h->n_bins = bin_base;
+  GMP_CK(h->structs.ensure(sizeof(GmpStruct) * S), "structs");
+  GMP_CK(h->grid.ensure(sizeof(GmpGrid) * S), "grid");
+  GMP_CK(h->atom_off.ensure(sizeof(int64_t) * (S + 1)), "atom_off");
+  GMP_CK(h->bbox.ensure(sizeof(unsigned long long) * 6 * S), "bbox");
+  GMP_CK(cudaMemcpyAsync(h->structs.p, info.data(), sizeof(GmpStruct) * S, cudaMemcpyHostToDevice, st), "upload structs");
+  GMP_CK(cudaMemcpyAsync(h->atom_off.p, atom_off, sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, st), "upload atom_off");
+  GMP_CK(h->struct_of.ensure(sizeof(int32_t) * (N > 0 ? N : 1)), "struct_of");
+  if (N > 0) GMP_CK(gmp_launch_struct_of(h->atom_off.as<int64_t>(), S, h->struct_of.as<int32_t>(), st, &h->launches), "struct_of");
+  // the copies above read host memory asynchronously: wait before returning
+  GMP_CK(cudaStreamSynchronize(st), "upload sync");
+  h->last_off.assign(atom_off, atom_off + S + 1);
+  h->last_cell.assign(cell, cell + 9 * S);
+  h->last_pbc.assign(pbc, pbc + 3 * S);
+  return GMP_OK;
+}
+
+gmp_status decode_device_error(gmp_ctx* h, uint32_t w) {
+  if (!w) return GMP_OK;
+  std::string m = "device reported:";
+  if (w & GMP_DEV_BAD_SPECIES) m += " species id out of range;";
+  if (w & GMP_DEV_NONFINITE) m += " non-finite position;";
+  if (w & GMP_DEV_TOO_MANY_NEIGHBORS) m += " neighbor list inconsistent;";
+  if (w & GMP_DEV_SHIFT_RANGE) m += " periodic image index beyond +-511 (position far outside its cell?);";
+  if (w & GMP_DEV_CAPACITY) m += " capacity exceeded;";
+  return fail(h, GMP_ERR_DEVICE, m);
+}
+
+// Records a start (begin = true) or stop event of `stage` on `st`.
+cudaError_t prof_mark(gmp_ctx* h, int stage, bool begin, cudaStream_t st) {
+  if (!h->profiling) return cudaSuccess;
+  auto& v = h->prof_ev[stage];
+  size_t& u = h->prof_used[stage];
+  if (begin && u + 2 > v.size()) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      v.push_back(e);
+    }
+  }
+  cudaError_t r = cudaEventRecord(v[begin ? u : u + 1], st);
+  if (!begin) u += 2;
+  return r;
+}
+
+// Binning + exact neighbor lists into h->pairs / h->nbr_off.  Synchronises
+// `st` once (to size the pair buffer).
+gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
+                           int64_t N, cudaStream_t st) {
+  int64_t* L = &h->launches;
+  GMP_CK(prof_mark(h, 0, true, st), "profile");
+  uint32_t* d_err = h->scalars.as<uint32_t>();
+  int32_t* d_maxm = reinterpret_cast<int32_t*>(d_err + 1);
+  // the error word is cleared after it is read (below), so a condition
+  // raised after the read of the previous call is reported here
+  GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
+  GMP_CK(h->atom_xh.ensure(sizeof(float4) * N), "atom_xh");
+  GMP_CK(h->atom_xl.ensure(sizeof(float4) * N), "atom_xl");
+  GMP_CK(h->atom_u.ensure(sizeof(GmpD4) * N), "atom_u");
+  GMP_CK(h->atom_bin.ensure(sizeof(int32_t) * N), "atom_bin");
+  GMP_CK(h->bin_count.ensure(sizeof(int32_t) * h->n_bins), "bin_count");
+  GMP_CK(h->bin_cursor.ensure(sizeof(int32_t) * h->n_bins), "bin_cursor");
+  GMP_CK(h->bin_start.ensure(sizeof(int32_t) * (h->n_bins + 1)), "bin_start");
+  GMP_CK(h->bin_y.ensure(sizeof(float4) * N), "bin_y");
+  GMP_CK(h->counts.ensure(sizeof(int64_t) * N), "counts");
+  GMP_CK(h->nbr_off.ensure(sizeof(int64_t) * (N + 1)), "nbr_off");
+  const int64_t scan_n = std::max<int64_t>(N, h->n_bins);
+  GMP_CK(h->scan_tmp.ensure(gmp_scan_tmp_bytes(scan_n)), "scan_tmp");
+
+  GMP_CK(gmp_launch_neighbors_prepare(h->structs.as<GmpStruct>(), S, h->struct_of.as<int32_t>(), N, h->cutoff,
+                                      pos, species, h->n_el, h->grid.as<GmpGrid>(), h->atom_xh.as<float4>(),
+                                      h->atom_xl.as<float4>(), h->atom_u.as<GmpD4>(), h->atom_bin.as<int32_t>(),
+                                      h->bbox.as<unsigned long long>(), d_err, st, h->sm_count, L),
+         "prepare");
+  GMP_CK(gmp_launch_bins(h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(), N,
+                         h->n_bins, h->atom_bin.as<int32_t>(), h->bin_count.as<int32_t>(),
+                         h->bin_start.as<int32_t>(), h->bin_cursor.as<int32_t>(), nullptr, h->bin_y.as<float4>(),
+                         h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->atom_u.as<GmpD4>(), h->scan_tmp.p,
+                         h->scan_tmp.bytes, st, h->sm_count, L),
+         "bins");
+  GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
+                                  N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
+                                  h->atom_u.as<GmpD4>(), h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
+                                  h->counts.as<int64_t>(), nullptr, nullptr, 0, d_maxm, d_err, st, h->sm_count, L),
+         "neighbor count");
+  GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), N, h->scan_tmp.p, st, L), "scan");
+  GMP_CK(cudaMemcpyAsync(h->h_small, h->nbr_off.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read P");
+  GMP_CK(cudaMemcpyAsync(h->h_small + 1, d_err, 8, cudaMemcpyDeviceToHost, st), "read err");
+  GMP_CK(cudaStreamSynchronize(st), "neighbor sync");
+  const uint32_t w = (uint32_t)(h->h_small[1] & 0xffffffffu);
+  const int maxm = (int)(h->h_small[1] >> 32);
+  if (w) {
+    GMP_CK(cudaMemsetAsync(d_err, 0, 4, st), "clear err");
+    return decode_device_error(h, w);
+  }
+  h->P = h->h_small[0];
+  h->max_m = maxm;
+  int keys = 32;
+  while (keys < maxm) keys <<= 1;
+  if ((size_t)keys * 8 > 200 * 1024)
+    return fail(h, GMP_ERR_CAPACITY, "a center has " + std::to_string(maxm) + " neighbor images (limit 25600)");
+  GMP_CK(h->pairs.ensure(sizeof(GmpPair) * (h->P > 0 ? h->P : 1)), "pairs");
+  GMP_CK(gmp_launch_neighbor_pass(1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
+                                  N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
+                                  h->atom_u.as<GmpD4>(), h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
+                                  nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), keys, d_maxm, d_err, st,
+                                  h->sm_count, L),
+         "neighbor fill");
+  GMP_CK(prof_mark(h, 0, false, st), "profile");
+  return GMP_OK;
+}
+
+// Features below this fraction of their FP32 resolution bound are recomputed
+// in FP64 (see gmp_refine.cu and the flag test in write_features).
+constexpr float kFlagTau = 3e-5f;
+
+int64_t flag_capacity(int64_t N) { return 4 * N + 1024; }
+
+gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_t N) {
+  gmpk::KParams K;
+  std::memset(&K, 0, sizeof(K));
+  K.pass = pd.pass;
+  K.N = N;
+  K.nbr_off = h->nbr_off.as<int64_t>();
+  K.pairs = h->pairs.as<GmpPair>();
+  K.counter = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 2);
+  K.flags = h->flagq.as<unsigned long long>();
+  K.flag_count = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3);
+  K.flag_cap = flag_capacity(N);
+  K.sig0 = 16 * pass_index;
+  K.flag_tau = kFlagTau;
+  return K;
+}
+
+// Prepares the flag queue before the compute kernels of one call.
+gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
+  GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * flag_capacity(N)), "flags");
+  GMP_CK(cudaMemsetAsync(h->scalars.as<uint32_t>() + 3, 0, sizeof(int32_t), st), "flag reset");
+  return GMP_OK;
+}
+
+// FP64 recomputation of the queued features.
+gmp_status refine(gmp_ctx* h, int64_t N, const double* pos, float* features, cudaStream_t st) {
+  GMP_CK(gmp_launch_refine(h->flagq.as<unsigned long long>(),
+                           reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3), flag_capacity(N),
+                           features, h->F, pos, h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
+                           h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->ktab.as<double>(),
+                           (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->scalars.as<uint32_t>(),
+                           h->sm_count, st, &h->launches),
+         "refine");
+  return GMP_OK;
+}
+
+// Inputs/outputs either all on the device or all in host memory.
+struct Io {
+  bool host = false;
+  const double* pos = nullptr;
+  const int32_t* species = nullptr;
+};
+
+gmp_status stage_inputs(gmp_ctx* h, int64_t N, const double* pos, const int32_t* species, Io& io,
+                        cudaStream_t st) {
+  io.host = !is_device_ptr(pos);
+  if (io.host != !is_device_ptr(species))
+    return fail(h, GMP_ERR_INVALID_ARG, "pos and species must both be device or both be host pointers");
+  if (!io.host) {
+    io.pos = pos;
+    io.species = species;
+    return GMP_OK;
+  }
+  GMP_CK(h->stage_pos.ensure(sizeof(double) * 3 * N), "stage pos");
+  GMP_CK(h->stage_species.ensure(sizeof(int32_t) * N), "stage species");
+  GMP_CK(cudaMemcpyAsync(h->stage_pos.p, pos, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st), "h2d pos");
+  GMP_CK(cudaMemcpyAsync(h->stage_species.p, species, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st), "h2d species");
+  io.pos = h->stage_pos.as<double>();
+  io.species = h->stage_species.as<int32_t>();
+  return GMP_OK;
+}
+
+gmp_status common_checks(gmp_ctx* h, int32_t S, const int64_t* atom_off, const double* pos,
+                         const double* cell, const uint8_t* pbc, const int32_t* species,
+                         cudaStream_t st, int64_t& N) {
+  if (!h) return GMP_ERR_INVALID_ARG;
+  GMP_CK(cudaSetDevice(h->device), "cudaSetDevice");
+  gmp_status r = upload_structures(h, S, atom_off, cell, pbc, st);
+  if (r != GMP_OK) return r;
+  N = atom_off[S];
+  if (N > 0 && (!pos || !species)) return fail(h, GMP_ERR_INVALID_ARG, "pos and species are required");
+  return GMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
+  if (!out) return GMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!p) return GMP_ERR_INVALID_ARG;
+  gmp_ctx* h = new gmp_ctx();
+  auto bad = [&](const std::string& m) {
+    std::fprintf(stderr, "gmp_create: %s\n", m.c_str());
+    gmp_destroy(h);
+    return GMP_ERR_INVALID_ARG;
+  };
+  if (p->n_elements < 1 || !p->n_gauss || !p->gauss_coef || !p->gauss_exp) return bad("density tables missing");
+  if (p->n_orders < 1 || p->n_orders > 8 || !p->orders) return bad("orders: 1..8 entries required");
+  if (!(p->cutoff > 0.0) || !std::isfinite(p->cutoff)) return bad("cutoff must be > 0");
+  h->n_el = p->n_elements;
+  int64_t tot = 0;
+  for (int e = 0; e < p->n_elements; ++e) {
+    if (p->n_gauss[e] < 1 || p->n_gauss[e] > 64) return bad("n_gauss must be in 1..64");
+    h->n_gauss.push_back(p->n_gauss[e]);
+    h->kmax = std::max(h->kmax, p->n_gauss[e]);
+    tot += p->n_gauss[e];
+  }
+  for (int64_t k = 0; k < tot; ++k) {
+    if (!(p->gauss_exp[k] > 0.0) || !std::isfinite(p->gauss_exp[k]) || !std::isfinite(p->gauss_coef[k]))
+      return bad("Gaussian exponents must be finite and > 0, coefficients finite");
+    h->coef.push_back(p->gauss_coef[k]);
+    h->alpha.push_back(p->gauss_exp[k]);
+  }
+  int lmax = -1;
+  bool dens = false;
+  for (int o = 0; o < p->n_orders; ++o) {
+    int l = p->orders[o];
+    if (l < -1 || l > 6) return bad("orders must be in -1..6");
+    for (int q = 0; q < o; ++q)
+      if (p->orders[q] == l) return bad("repeated order");
+    if (l == -1) dens = true;
+    else lmax = std::max(lmax, l);
+    h->orders.push_back(l);
+  }
+  if (lmax >= 0) {
+    if (p->n_sigmas < 1 || !p->sigmas) return bad("sigmas required");
+    for (int s = 0; s < p->n_sigmas; ++s) {
+      if (!(p->sigmas[s] > 0.0) || !std::isfinite(p->sigmas[s])) return bad("sigmas must be > 0");
+      h->sigmas.push_back(p->sigmas[s]);
+    }
+  }
+  if (h->sigmas.size() > 1024) return bad("at most 1024 sigmas");
+  h->cutoff = p->cutoff;
+  h->flags = p->flags;
+  const int nsig = (int)h->sigmas.size();
+  h->F = (dens ? 1 : 0);
+  for (int l : h->orders)
+    if (l >= 0) h->F += nsig;
+  // feature column of (order slot o, sigma 0); order -1 takes one column
+  std::vector<int> col(h->orders.size());
+  {
+    int c = 0;
+    for (size_t o = 0; o < h->orders.size(); ++o) {
+      col[o] = c;
+      c += h->orders[o] < 0 ? 1 : nsig;
+    }
+  }
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return bad("cudaSetDevice failed"); }
+  h->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { cudaGetLastError(); return bad("no CUDA device"); }
+  h->sm_count = prop.multiProcessorCount;
+  const int L = lmax < 0 ? 0 : lmax;
+  const int nsplit = lmax < 0 ? 1 : (nsig + 15) / 16;
+  const double LOG2E = 1.4426950408889634;
+  for (int g = 0; g < nsplit; ++g) {
+    PassData pd;
+    std::memset(&pd.pass, 0, sizeof(pd.pass));
+    const int s0 = g * 16;
+    const int ns = lmax < 0 ? 0 : std::min(16, nsig - s0);
+    pd.L = L;
+    pd.NS = pad_sigmas(std::max(ns, 1));
+    GmpPass& P = pd.pass;
+    P.lmax = L;
+    P.nsig = ns;
+    P.nsig_pad = pd.NS;
+    P.kmax = h->kmax;
+    P.n_el = h->n_el;
+    P.want_density = (g == 0 && dens) ? 1 : 0;
+    P.F = h->F;
+    P.dens_col = -1;
+    P.n_ord = 0;
+    for (size_t o = 0; o < h->orders.size(); ++o) {
+      if (h->orders[o] < 0) {
+        P.dens_col = col[o];
+        continue;
+      }
+      if (ns == 0) continue;
+      P.ord_l[P.n_ord] = h->orders[o];
+      P.ord_col[P.n_ord] = col[o] + s0;
+      ++P.n_ord;
+    }
+    std::vector<float> tab((size_t)h->n_el * pd.NS * h->kmax * GMP_RAD_STRIDE, 0.0f);
+    int64_t off = 0;
+    for (int e = 0; e < h->n_el; ++e) {
+      for (int s = 0; s < ns; ++s) {
+        const double sig = h->sigmas[s0 + s];
+        const double beta = 1.0 / (2.0 * sig * sig);
+        const double Ns = std::pow(2.0 * M_PI * sig * sig, -1.5);
+        for (int q = 0; q < h->n_gauss[e]; ++q) {
+          const double a = h->alpha[off + q], c = h->coef[off + q];
+          const double gam = a + beta;
+          const double b = a * beta / gam;
+          const double B = b * LOG2E;
+          float* ent = &tab[(((size_t)e * pd.NS + s) * h->kmax + q) * GMP_RAD_STRIDE];
+          ent[0] = (float)B;
+          ent[1] = (float)(B - (double)ent[0]);
+          ent[2] = (float)b;
+          const double K0 = c * Ns * std::pow(M_PI / gam, 1.5);
+          for (int l = 0; l < 8; ++l) ent[4 + l] = (float)(K0 * std::pow(a / gam, l));
+        }
+      }
+      off += h->n_gauss[e];
+    }
+    if (pd.rad.ensure(tab.size() * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(pd.rad.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      pd.rad.release();
+      return bad("device allocation for tables failed");
+    }
+    P.rad = pd.rad.as<float>();
+    h->passes.push_back(pd);
+  }
+  {
+    std::vector<float> dt((size_t)h->n_el * h->kmax * GMP_DENS_STRIDE, 0.0f);
+    int64_t off = 0;
+    for (int e = 0; e < h->n_el; ++e) {
+      for (int q = 0; q < h->n_gauss[e]; ++q) {
+        const double a = h->alpha[off + q];
+        const double B = a * LOG2E;
+        float* ent = &dt[((size_t)e * h->kmax + q) * GMP_DENS_STRIDE];
+        ent[0] = (float)B;
+        ent[1] = (float)(B - (double)ent[0]);
+        ent[2] = (float)a;
+        ent[3] = (float)h->coef[off + q];
+      }
+      off += h->n_gauss[e];
+    }
+    if (h->dens.ensure(dt.size() * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(h->dens.p, dt.data(), dt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return bad("device allocation for tables failed");
+    }
+    for (auto& pd : h->passes) pd.pass.dens = h->dens.as<float>();
+  }
+  {
+    // FP64 constants for the refinement kernel: per (element, sigma, primitive)
+    // c N_s (pi/g)^(3/2), alpha/g, alpha beta/g
+    const int ns = std::max<int>((int)h->sigmas.size(), 1);
+    std::vector<double> kt((size_t)h->n_el * ns * h->kmax * 3, 0.0);
+    int64_t off = 0;
+    for (int e = 0; e < h->n_el; ++e) {
+      for (int s = 0; s < (int)h->sigmas.size(); ++s) {
+        const double sig = h->sigmas[s];
+        const double beta = 1.0 / (2.0 * sig * sig);
+        const double Ns = std::pow(2.0 * M_PI * sig * sig, -1.5);
+        for (int q = 0; q < h->n_gauss[e]; ++q) {
+          const double a = h->alpha[off + q], c = h->coef[off + q];
+          const double gam = a + beta;
+          double* ent = &kt[(((size_t)e * ns + s) * h->kmax + q) * 3];
+          ent[0] = c * Ns * std::pow(M_PI / gam, 1.5);
+          ent[1] = a / gam;
+          ent[2] = a * beta / gam;
+        }
+      }
+      off += h->n_gauss[e];
+    }
+    if (h->ktab.ensure(kt.size() * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(h->ktab.p, kt.data(), kt.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        h->scalars.ensure(64) != cudaSuccess || cudaMemset(h->scalars.p, 0, 64) != cudaSuccess) {
+      cudaGetLastError();
+      return bad("device allocation for tables failed");
+    }
+  }
+  if (cudaMallocHost((void**)&h->h_small, 64) != cudaSuccess) { cudaGetLastError(); return bad("pinned alloc failed"); }
+  if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return bad("event"); }
+  *out = h;
+  return GMP_OK;
+}
+
+gmp_status gmp_num_features(gmp_handle h, int32_t* F) {
+  if (!h || !F) return GMP_ERR_INVALID_ARG;
+  *F = h->F;
+  return GMP_OK;
+}
+
+gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                         const double* cell, const uint8_t* pbc, const int32_t* species, float* features,
+                         void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (N == 0) return GMP_OK;
+  if (!features) return fail(h, GMP_ERR_INVALID_ARG, "features is required");
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  float* feat = features;
+  if (io.host) {
+    GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "stage features");
+    feat = h->stage_feat.as<float>();
+  } else if (!is_device_ptr(features)) {
+    return fail(h, GMP_ERR_INVALID_ARG, "features must be a device pointer when inputs are");
+  }
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, true, st), "profile");
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
+    K.features = feat;
+    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_FORWARD, h->passes[g].NS, K, st, h->sm_count, &h->launches),
+           "forward");
+  }
+  if ((r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, false, st), "profile");
+  if (io.host) {
+    GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
+    GMP_CK(cudaStreamSynchronize(st), "sync");
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                             const double* cell, const uint8_t* pbc, const int32_t* species,
+                             const float* grad_feat, float* features, float* grad_pos, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (N == 0) return GMP_OK;
+  if (!grad_feat || !grad_pos) return fail(h, GMP_ERR_INVALID_ARG, "grad_feat and grad_pos are required");
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  const float* gf = grad_feat;
+  float* feat = features;
+  float* gp = grad_pos;
+  if (io.host) {
+    GMP_CK(h->stage_gradf.ensure(sizeof(float) * N * h->F), "stage grad_feat");
+    GMP_CK(cudaMemcpyAsync(h->stage_gradf.p, grad_feat, sizeof(float) * N * h->F, cudaMemcpyHostToDevice, st), "h2d grad_feat");
+    gf = h->stage_gradf.as<float>();
+    if (features) {
+      GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "stage features");
+      feat = h->stage_feat.as<float>();
+    }
+    GMP_CK(h->stage_gradp.ensure(sizeof(float) * N * 3), "stage grad_pos");
+    gp = h->stage_gradp.as<float>();
+  }
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
+  GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
+  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, true, st), "profile");
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
+    K.features = feat;
+    K.grad_feat = gf;
+    K.grad_acc = h->grad_acc.as<double>();
+    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_VJP, h->passes[g].NS, K, st, h->sm_count, &h->launches), "vjp");
+  }
+  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, false, st), "profile");
+  GMP_CK(gmp_launch_grad_finish(N, h->grad_acc.as<double>(), gp, st, &h->launches), "grad finish");
+  if (io.host) {
+    if (features)
+      GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
+    GMP_CK(cudaMemcpyAsync(grad_pos, gp, sizeof(float) * N * 3, cudaMemcpyDeviceToHost, st), "d2h grad");
+    GMP_CK(cudaStreamSynchronize(st), "sync");
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                                  const double* cell, const uint8_t* pbc, const int32_t* species, float* features,
+                                  int64_t* jac_off, int32_t* jac_j, float* jac, int64_t cap, int64_t* nnz_out,
+                                  void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (!nnz_out) return fail(h, GMP_ERR_INVALID_ARG, "nnz_out is required");
+  *nnz_out = 0;
+  if (N == 0) return GMP_OK;
+  if (!jac_off) return fail(h, GMP_ERR_INVALID_ARG, "jac_off is required");
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  GMP_CK(h->jac_counts.ensure(sizeof(int64_t) * (2 * N + 1)), "jac counts");
+  int64_t* cnt = h->jac_counts.as<int64_t>();
+  int64_t* joff = cnt + N;
+  GMP_CK(gmp_launch_jacobian_count(N, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), cnt, st, h->sm_count,
+                                   &h->launches), "jac count");
+  GMP_CK(gmp_exclusive_scan_i64(cnt, joff, N, h->scan_tmp.p, st, &h->launches), "jac scan");
+  GMP_CK(cudaMemcpyAsync(h->h_small, joff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read nnz");
+  GMP_CK(cudaStreamSynchronize(st), "jac sync");
+  const int64_t nnz = h->h_small[0];
+  *nnz_out = nnz;
+  if (nnz > cap) return fail(h, GMP_ERR_CAPACITY, "jacobian needs " + std::to_string(nnz) + " rows, cap is " + std::to_string(cap));
+  if (!jac_j || !jac) return fail(h, GMP_ERR_INVALID_ARG, "jac_j and jac are required");
+  float* feat = features;
+  float* jd = jac;
+  int32_t* jj = jac_j;
+  DevBuf tmp_feat, tmp_jac, tmp_jj;
+  if (io.host) {
+    if (features) {
+      GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "stage features");
+      feat = h->stage_feat.as<float>();
+    }
+    GMP_CK(tmp_jac.ensure(sizeof(float) * nnz * h->F * 3), "stage jac");
+    GMP_CK(tmp_jj.ensure(sizeof(int32_t) * nnz), "stage jac_j");
+    jd = tmp_jac.as<float>();
+    jj = tmp_jj.as<int32_t>();
+  }
+  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, true, st), "profile");
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
+    K.features = feat;
+    K.jac_off = joff;
+    K.jac_j = jj;
+    K.jac = jd;
+    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_JACOBIAN, h->passes[g].NS, K, st, h->sm_count, &h->launches),
+           "jacobian");
+  }
+  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 1, false, st), "profile");
+  const cudaMemcpyKind k_off = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (N + 1), k_off, st), "copy jac_off");
+  if (io.host) {
+    if (features) GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
+    GMP_CK(cudaMemcpyAsync(jac, jd, sizeof(float) * nnz * h->F * 3, cudaMemcpyDeviceToHost, st), "d2h jac");
+    GMP_CK(cudaMemcpyAsync(jac_j, jj, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st), "d2h jac_j");
+    GMP_CK(cudaStreamSynchronize(st), "sync");
+    tmp_jac.release();
+    tmp_jj.release();
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                         const double* cell, const uint8_t* pbc, const int32_t* species, int64_t* nbr_off,
+                         int32_t* nbr_j, int32_t* nbr_shift, int64_t cap, int64_t* nnz_out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (!nnz_out) return fail(h, GMP_ERR_INVALID_ARG, "nnz_out is required");
+  *nnz_out = 0;
+  if (N == 0) return GMP_OK;
+  if (!nbr_off) return fail(h, GMP_ERR_INVALID_ARG, "nbr_off is required");
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  *nnz_out = h->P;
+  if (h->P > cap) return fail(h, GMP_ERR_CAPACITY, "neighbor list needs " + std::to_string(h->P) + " entries");
+  if (h->P > 0 && (!nbr_j || !nbr_shift)) return fail(h, GMP_ERR_INVALID_ARG, "nbr_j and nbr_shift are required");
+  DevBuf tj, ts;
+  int32_t* dj = nbr_j;
+  int32_t* ds = nbr_shift;
+  if (io.host) {
+    GMP_CK(tj.ensure(sizeof(int32_t) * (h->P + 1)), "stage nbr_j");
+    GMP_CK(ts.ensure(sizeof(int32_t) * 3 * (h->P + 1)), "stage nbr_shift");
+    dj = tj.as<int32_t>();
+    ds = ts.as<int32_t>();
+  }
+  GMP_CK(gmp_launch_unpack_neighbors(h->P, h->pairs.as<GmpPair>(), dj, ds, st, &h->launches), "unpack");
+  const cudaMemcpyKind k = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  GMP_CK(cudaMemcpyAsync(nbr_off, h->nbr_off.p, sizeof(int64_t) * (N + 1), k, st), "copy nbr_off");
+  if (io.host) {
+    GMP_CK(cudaMemcpyAsync(nbr_j, dj, sizeof(int32_t) * h->P, cudaMemcpyDeviceToHost, st), "d2h nbr_j");
+    GMP_CK(cudaMemcpyAsync(nbr_shift, ds, sizeof(int32_t) * 3 * h->P, cudaMemcpyDeviceToHost, st), "d2h shift");
+    GMP_CK(cudaStreamSynchronize(st), "sync");
+    tj.release();
+    ts.release();
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_sync(gmp_handle h, void* stream, double timeout_s) {
+  if (!h) return GMP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  GMP_CK(cudaEventRecord(h->ev, st), "event record");
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    cudaError_t e = cudaEventQuery(h->ev);
+    if (e == cudaSuccess) {
+      uint32_t w = 0;
+      GMP_CK(cudaMemcpy(&w, h->scalars.p, sizeof(w), cudaMemcpyDeviceToHost), "read err");
+      if (w) {
+        GMP_CK(cudaMemset(h->scalars.p, 0, sizeof(w)), "clear err");
+        return decode_device_error(h, w);
+      }
+      return GMP_OK;
+    }
+    if (e != cudaErrorNotReady) return cuda_fail(h, e, "event query");
+    if (timeout_s > 0) {
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_s) return fail(h, GMP_ERR_TIMEOUT, "gmp_sync timed out");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+const char* gmp_last_error(gmp_handle h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+int64_t gmp_kernel_launches(gmp_handle h) { return h ? h->launches : 0; }
+
+gmp_status gmp_profile(gmp_handle h, int enable) {
+  if (!h) return GMP_ERR_INVALID_ARG;
+  h->profiling = enable != 0;
+  h->prof_used[0] = h->prof_used[1] = 0;
+  return GMP_OK;
+}
+
+gmp_status gmp_profile_read(gmp_handle h, double* ms, int64_t* count, int n_stages) {
+  if (!h || !ms || !count || n_stages < 1 || n_stages > 2) return GMP_ERR_INVALID_ARG;
+  for (int s = 0; s < n_stages; ++s) {
+    double tot = 0.0;
+    for (size_t u = 0; u + 1 < h->prof_used[s] + 1 && u < h->prof_used[s]; u += 2) {
+      GMP_CK(cudaEventSynchronize(h->prof_ev[s][u + 1]), "profile sync");
+      float t = 0.0f;
+      GMP_CK(cudaEventElapsedTime(&t, h->prof_ev[s][u], h->prof_ev[s][u + 1]), "profile elapsed");
+      tot += t;
+    }
+    ms[s] = tot;
+    count[s] = (int64_t)(h->prof_used[s] / 2);
+    h->prof_used[s] = 0;
+  }
+  return GMP_OK;
+}
+
+void gmp_destroy(gmp_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  for (auto& pd : h->passes) pd.rad.release();
+  DevBuf* bufs[] = {&h->ktab, &h->flagq, &h->dens, &h->structs, &h->grid, &h->atom_off, &h->struct_of, &h->bbox, &h->atom_xh,
+                    &h->atom_xl, &h->atom_u, &h->atom_bin, &h->bin_count, &h->bin_cursor, &h->bin_start,
+                    &h->bin_y, &h->counts, &h->nbr_off, &h->scan_tmp, &h->pairs, &h->scalars, &h->grad_acc,
+                    &h->jac_counts, &h->stage_pos, &h->stage_species, &h->stage_feat, &h->stage_gradf,
+                    &h->stage_gradp};
+  for (DevBuf* b : bufs) b->release();
+  if (h->h_small) cudaFreeHost(h->h_small);
+  for (auto& v : h->prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  if (h->ev) cudaEventDestroy(h->ev);
+  delete h;
+}
+
+}  // extern "C"

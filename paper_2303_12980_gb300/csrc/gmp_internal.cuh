@@ -1,0 +1,206 @@
+// Internal declarations shared by the libgmp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GMP_WARP 32
+#define GMP_MAX_SIGMAS 16      // sigmas per kernel pass (host splits larger sets)
+#define GMP_TILE 32            // neighbor pairs staged per warp tile
+
+// Device error word bits (OR-ed by kernels, read by the host after a call).
+#define GMP_DEV_BAD_SPECIES 1u
+#define GMP_DEV_NONFINITE 2u
+#define GMP_DEV_TOO_MANY_NEIGHBORS 4u
+#define GMP_DEV_SHIFT_RANGE 8u
+#define GMP_DEV_CAPACITY 16u
+
+struct __align__(32) GmpD4 {
+  double x, y, z, w;
+};
+
+// Per-structure geometry used by binning and neighbor search (host-built).
+struct GmpStruct {
+  double A[9];        // lattice vectors as rows (identity frame when no axis is periodic)
+  double Ainv[9];     // inverse: frac = x . Ainv (u_k = sum_c x_c Ainv[c*3+k])
+  float Ahi[9], Alo[9];  // double-float split of A
+  double reach[3];    // cutoff * |b_k| in fractional units (b_k = column k of Ainv)
+  int periodic[3];
+  int64_t atom_base;  // first atom
+  int32_t n_atoms;
+  int32_t pad0;
+  int64_t bin_base;   // first bin slot of this structure
+  int32_t bin_cap;    // bin slots reserved
+  int32_t pad1;
+  float prescreen2;   // FP32 pre-screen bound on r^2 (rigorous, see neighbors.cu)
+  float pad2[3];
+};
+
+// Per-structure bin grid (device-built from bounding boxes).
+struct GmpGrid {
+  double umin[3];     // fractional coordinate of bin 0 edge
+  double binw[3];     // bin width (fractional)
+  int nb[3];          // bins per axis
+  int pad;
+};
+
+// One neighbor image of a center, 32 bytes.
+struct __align__(16) GmpPair {
+  float dx, dy, dz, r2hi;   // displacement x_j + shift - x_i (FP32), r^2 high part
+  float r2lo;               // r^2 = r2hi + r2lo (double-float)
+  int32_t e;                // species of j
+  int32_t j;                // neighbor atom (global index)
+  int32_t shift;            // packed image n: (n1+512) | (n2+512)<<10 | (n3+512)<<20
+};
+
+__host__ __device__ inline int32_t gmp_pack_shift(int n1, int n2, int n3) {
+  return (n1 + 512) | ((n2 + 512) << 10) | ((n3 + 512) << 20);
+}
+__host__ __device__ inline void gmp_unpack_shift(int32_t s, int* n) {
+  n[0] = (s & 1023) - 512;
+  n[1] = ((s >> 10) & 1023) - 512;
+  n[2] = ((s >> 20) & 1023) - 512;
+}
+
+// Radial table entry per (element, sigma, primitive): 12 floats.
+//   [0] Bhi, [1] Blo : B = alpha*beta/gamma * log2(e) as a double-float
+//   [2] b            : alpha*beta/gamma (natural-log rate, for d/dr^2)
+//   [3] unused
+//   [4 + l] A_l      : c * N_sigma * (pi/gamma)^(3/2) * (alpha/gamma)^l, l = 0..7
+#define GMP_RAD_STRIDE 12
+// Density table entry per (element, primitive): Bhi, Blo, b, c with B = alpha*log2(e), b = alpha.
+#define GMP_DENS_STRIDE 4
+
+// Shapes of one forward/backward pass.
+struct GmpPass {
+  int lmax;            // highest non-negative order computed
+  int nsig;            // sigmas in this pass (<= 16)
+  int nsig_pad;        // 4, 8 or 16
+  int kmax;            // primitives per element (padded)
+  int n_el;
+  int want_density;    // order -1 requested
+  int F;               // total feature columns
+  int n_ord;           // number of orders >= 0 written by this pass
+  int ord_l[8];        // orders written
+  int ord_col[8];      // feature column of (order, sigma 0) for this pass
+  int dens_col;        // column of order -1 or -1
+  const float* rad;    // [n_el][nsig_pad][kmax][GMP_RAD_STRIDE]
+  const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]
+};
+
+// ---------------------------------------------------------------- double-float
+struct gmp_f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ gmp_f2 gmp_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ gmp_f2 gmp_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ gmp_f2 gmp_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+// Accurate double-float addition (two TwoSums, two renormalisations).
+__device__ __forceinline__ gmp_f2 gmp_df_add(gmp_f2 a, gmp_f2 b) {
+  gmp_f2 s = gmp_two_sum(a.hi, b.hi);
+  gmp_f2 t = gmp_two_sum(a.lo, b.lo);
+  float e = __fadd_rn(s.lo, t.hi);
+  gmp_f2 u = gmp_fast_two_sum(s.hi, e);
+  e = __fadd_rn(t.lo, u.lo);
+  return gmp_fast_two_sum(u.hi, e);
+}
+__device__ __forceinline__ gmp_f2 gmp_df_neg(gmp_f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ gmp_f2 gmp_df_mul(gmp_f2 a, gmp_f2 b) {
+  gmp_f2 p = gmp_two_prod(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return gmp_fast_two_sum(p.hi, e);
+}
+// Integer (|n| < 2^24) times double-float, exact product of the high part.
+__device__ __forceinline__ gmp_f2 gmp_df_mul_int(int n, gmp_f2 a) {
+  float fn = (float)n;
+  gmp_f2 p = gmp_two_prod(fn, a.hi);
+  float e = __fmaf_rn(fn, a.lo, p.lo);
+  return gmp_fast_two_sum(p.hi, e);
+}
+
+// 2^x on the SFU (PTX ex2.approx.ftz.f32): about 2 ulp, flushes tiny results to 0.
+__device__ __forceinline__ float gmp_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// exp(-B r^2) with B and r^2 given as double-floats: the product is formed
+// to about 2^-44 relative, the SFU takes its high part and the low part is
+// applied to first order, exp2(-(h+l)) = exp2(-h) (1 - ln2 l).
+__device__ __forceinline__ float gmp_exp_neg(float Bhi, float Blo, float r2hi, float r2lo) {
+  float xh = __fmul_rn(Bhi, r2hi);
+  float xl = __fmaf_rn(Bhi, r2hi, -xh);
+  xl = __fmaf_rn(Bhi, r2lo, xl);
+  xl = __fmaf_rn(Blo, r2hi, xl);
+  float E = gmp_ex2(-xh);
+  return __fmaf_rn(E, -0.69314718055994531f * xl, E);
+}
+
+// ---------------------------------------------------------------- host side
+struct GmpWorkspace;
+
+// Launchers implemented in the .cu files (all asynchronous on `stream`).
+cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struct,
+                                         const int32_t* d_struct_of, int64_t N, double cutoff,
+                                         const double* pos, const int32_t* species, int n_el,
+                                         GmpGrid* d_grid, float4* atom_xh, float4* atom_xl,
+                                         GmpD4* atom_u, int32_t* atom_bin,
+                                         unsigned long long* d_bbox, uint32_t* d_err,
+                                         cudaStream_t stream, int sm_count, int64_t* launches);
+cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
+                            const int32_t* d_struct_of, int64_t N, int64_t n_bins,
+                            const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
+                            int32_t* bin_cursor, int32_t* bin_atoms, float4* bin_y,
+                            const float4* atom_xh, const float4* atom_xl, const GmpD4* atom_u,
+                            void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
+                            int sm_count, int64_t* launches);
+size_t gmp_scan_tmp_bytes(int64_t n);
+cudaError_t gmp_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp,
+                                   cudaStream_t stream, int64_t* launches);
+cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
+                                     const int32_t* d_struct_of, int64_t N, double cutoff,
+                                     const double* pos, const float4* atom_xh, const float4* atom_xl,
+                                     const GmpD4* atom_u, const int32_t* bin_start,
+                                     const float4* bin_y, int64_t* counts, const int64_t* offsets,
+                                     GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
+                                     cudaStream_t stream, int sm_count, int64_t* launches);
+cudaError_t gmp_launch_forward(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
+                               const GmpPair* pairs, float* features, float* mu_out,
+                               int32_t* work_counter, cudaStream_t stream, int sm_count,
+                               int64_t* launches);
+cudaError_t gmp_launch_vjp(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
+                           const GmpPair* pairs, const float* grad_feat, float* features,
+                           double* grad_acc, int32_t* work_counter, cudaStream_t stream,
+                           int sm_count, int64_t* launches);
+cudaError_t gmp_launch_jacobian(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
+                                const GmpPair* pairs, const int64_t* jac_off, int32_t* jac_j,
+                                float* jac, float* features, int32_t* work_counter,
+                                cudaStream_t stream, int sm_count, int64_t* launches);
+cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
+                                      int64_t* counts, cudaStream_t stream, int sm_count,
+                                      int64_t* launches);
+cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,
+                                   cudaStream_t stream, int64_t* launches);
+cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
+                              float* features, int F, const double* pos, const int32_t* struct_of,
+                              const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
+                              const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
+                              cudaStream_t stream, int64_t* launches);
+cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,
+                                        int32_t* nbr_shift, cudaStream_t stream,
+                                        int64_t* launches);

@@ -1,0 +1,738 @@
+// GMP moment, feature, VJP and Jacobian kernels (templates on the highest
+// MCSH order L and the padded sigma count NS).
+//
+// Per center i the moments are (GMP-Featurizer, Statement of Needs: the
+// local density as a multipole expansion; Examples: MCSH orders x sigmas)
+//   mu_{l,s,k}(i) = sum over neighbor images p of R_{l,s}(r_p^2) S_k(d_p)
+// with S_k the MCSH polynomial of component k and the radial factor
+//   R_{l,s}(r^2) = sum_q c_q N_s (pi/g)^(3/2) (alpha_q/g)^l exp(-(alpha_q beta_s/g) r^2),
+//   beta_s = 1/(2 s^2), g = alpha_q + beta_s, N_s = (2 pi s^2)^(-3/2).
+// This factorised form is the Gaussian overlap integral of the density
+// primitive c_q exp(-alpha_q |r - d|^2) with the probe N_s S_k(r) exp(-beta_s r^2):
+// the Gaussian product theorem moves the product to a Gaussian centred at
+// (alpha/g) d, and the Gaussian average of a harmonic polynomial equals its
+// value at the centre, so the integral is K S_k((alpha/g) d) = K (alpha/g)^l S_k(d).
+// Feature f_{l,s} = sum over all components of l!/(a!b!c!) mu^2 (the
+// rotation invariant of the group).  Only the 2l+1 independent components
+// (a <= 1) are accumulated; the rest follow from tracelessness.
+//
+// Layout: one warp per center (persistent warps take centers from an atomic
+// counter).  A warp walks its center's neighbor list in tiles of 32 pairs:
+//   phase 1, lane = pair: exps and radial factors R[l][s] (double-float
+//            exponent argument), MCSH values S[k] -> shared-memory tile;
+//   phase 2, lane = block of 4 sigmas x 4 components: FP32 FMAs over the
+//            tile, then the tile partial is folded into a (hi, lo) pair by
+//            TwoSum (blocked compensated summation over neighbors).
+#pragma once
+
+#include "gmp_internal.cuh"
+#include "mcsh_gen.cuh"
+
+#include <utility>
+
+namespace gmpk {
+
+// Compile-time loop: f(std::integral_constant<int, 0>), ..., f(<N-1>).
+template <typename F, int... Cs>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Cs...>) {
+  (f(std::integral_constant<int, Cs>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+__host__ __device__ constexpr int chunks_of_order(int l) { return (l + 2) / 2; }  // ceil((2l+1)/4)
+__host__ __device__ constexpr int nchunks(int L) {
+  int n = 0;
+  for (int l = 0; l <= L; ++l) n += chunks_of_order(l);
+  return n;
+}
+__host__ __device__ constexpr int chunk_l(int c) {
+  int l = 0;
+  while (c >= chunks_of_order(l)) { c -= chunks_of_order(l); ++l; }
+  return l;
+}
+__host__ __device__ constexpr int chunk_k0(int c) {
+  int l = 0;
+  while (c >= chunks_of_order(l)) { c -= chunks_of_order(l); ++l; }
+  return l * l + 4 * c;
+}
+// order l of flat independent component k (k in [l^2, (l+1)^2))
+__host__ __device__ constexpr int order_of(int k) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= k) ++l;
+  return l;
+}
+// float count rounded to a multiple of 4 holding an odd number of float4s
+// (conflict-free 16-byte stores by 8 consecutive lanes)
+__host__ __device__ constexpr int odd4(int n) {
+  int q = (n + 3) / 4;
+  if ((q & 1) == 0) ++q;
+  return 4 * q;
+}
+
+template <int L, int NS>
+struct Shape {
+  static constexpr int NIND = (L + 1) * (L + 1);   // independent components, orders 0..L
+  static constexpr int NIND1 = (L + 2) * (L + 2);  // ... orders 0..L+1
+  static constexpr int NSB = NS / 4;
+  static constexpr int NCH = nchunks(L);
+  static constexpr int NITEM = NSB * NCH;
+  static constexpr int Q = (NITEM + 31) / 32;
+  static constexpr int RL4 = (L + 1 + 3) / 4 * 4;  // r^l, l = 0..L, after the S chunks
+  static constexpr int RSTR = odd4((L + 1) * NS);
+  static constexpr int SSTR = odd4(NCH * 4 + RL4);
+  static constexpr int TILE = 16;                  // pairs staged per tile (2 lanes per pair)
+  static constexpr int FOLD = 8;                   // pairs per FP32 partial before the TwoSum fold
+  static constexpr int NINDP = (NIND + 3) / 4 * 4; // padded row of per-sigma vectors
+  static constexpr int WARP_FLOATS = TILE * RSTR + TILE * SSTR;
+  static_assert(NS * NIND + NS * (L + 1) <= TILE * RSTR, "moments and bounds must fit the R tile");
+  static_assert(NS * NINDP <= TILE * SSTR, "adjoints must fit the S tile");
+};
+
+// Per-element strides of the shared-memory tables: an odd number of float4s,
+// so lanes reading different elements hit different banks.
+__host__ __device__ inline int rad_elem_stride(int NS, int kmax) {
+  int q = NS * kmax * (GMP_RAD_STRIDE / 4);
+  if ((q & 1) == 0) ++q;
+  return 4 * q;
+}
+__host__ __device__ inline int dens_elem_stride(int kmax) {
+  int q = kmax * (GMP_DENS_STRIDE / 4);
+  if ((q & 1) == 0) ++q;
+  return 4 * q;
+}
+
+struct KParams {
+  GmpPass pass;
+  int64_t N;
+  const int64_t* nbr_off;
+  const GmpPair* pairs;
+  float* features;        // [N, F] or null
+  float* mu_out;          // [N, nsig, NIND] or null
+  const float* grad_feat; // [N, F] (vjp)
+  double* grad_acc;       // [N, 3] (vjp)
+  const int64_t* jac_off; // [N+1] (jacobian)
+  int32_t* jac_j;
+  float* jac;             // [nnz, F, 3]
+  int32_t* counter;
+  // features too ill-conditioned for FP32 (recomputed in FP64 afterwards)
+  unsigned long long* flags;  // packed (center, order, sigma, column)
+  int32_t* flag_count;
+  int64_t flag_cap;
+  int sig0;                   // global index of this pass's first sigma
+  float flag_tau;             // flag when f < flag_tau * C_l l! (2l-1)!! B^2
+};
+
+// Packed flag entry: center (31 bits) | order (4) | global sigma (12) | column (12)
+__host__ __device__ inline unsigned long long pack_flag(int64_t i, int l, int sig, int col) {
+  return ((unsigned long long)i << 28) | ((unsigned long long)l << 24) | ((unsigned long long)sig << 12) |
+         (unsigned long long)col;
+}
+
+// C_l l! (2l-1)!!: with B = sum_pairs |R_{l,s}| r^l, sum_c w_c (sum_pairs |R S_c|)^2
+// <= C_l l! (2l-1)!! B^2 since sum_c w_c S_c^2 = l! (2l-1)!! r^(2l).
+__host__ __device__ constexpr float flag_scale(int l) {
+  return l == 0 ? 1.0f : l == 1 ? 3.0f : l == 2 ? 36.0f : l == 3 ? 900.0f : l == 4 ? 37800.0f
+       : l == 5 ? 2381400.0f : 209563200.0f;
+}
+
+__device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int64_t idx, float& dx,
+                                          float& dy, float& dz, float& r2h, float& r2l, int& e,
+                                          int& j) {
+  const float4* p4 = reinterpret_cast<const float4*>(pairs + idx);
+  const float4 a = __ldg(p4);
+  const float4 b = __ldg(p4 + 1);
+  dx = a.x; dy = a.y; dz = a.z; r2h = a.w;
+  r2l = b.x;
+  e = __float_as_int(b.y);
+  j = __float_as_int(b.z);
+}
+
+// Radial factors of one pair for a group of 4 sigmas: R[u][l] (and dR/dr^2).
+template <int L, int NS, bool DERIV>
+__device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+                                        float r2l, float (&R)[4][L + 1], float (&Rd)[4][L + 1]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+      R[u][l] = 0.0f;
+      if (DERIV) Rd[u][l] = 0.0f;
+    }
+  for (int q = 0; q < kmax; ++q) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float* ent = tab_e + ((sg * 4 + u) * kmax + q) * GMP_RAD_STRIDE;
+      const float4 h = *reinterpret_cast<const float4*>(ent);
+      const float4 a0 = *reinterpret_cast<const float4*>(ent + 4);
+      float A[8] = {a0.x, a0.y, a0.z, a0.w, 0.f, 0.f, 0.f, 0.f};
+      if (L >= 4) {
+        const float4 a1 = *reinterpret_cast<const float4*>(ent + 8);
+        A[4] = a1.x; A[5] = a1.y; A[6] = a1.z; A[7] = a1.w;
+      }
+      const float E = gmp_exp_neg(h.x, h.y, r2h, r2l);
+      const float mb = -h.z;
+#pragma unroll
+      for (int l = 0; l <= L; ++l) {
+        R[u][l] = __fmaf_rn(A[l], E, R[u][l]);
+        if (DERIV) Rd[u][l] = __fmaf_rn(mb, __fmul_rn(A[l], E), Rd[u][l]);
+      }
+    }
+  }
+}
+
+// Density at the center from one pair: sum_q c_q exp(-alpha_q r^2).
+__device__ __forceinline__ float density_term(const float* __restrict__ dens_e, int kmax, float r2h,
+                                              float r2l, float* deriv) {
+  float rho = 0.0f, drho = 0.0f;
+  for (int q = 0; q < kmax; ++q) {
+    const float4 h = *reinterpret_cast<const float4*>(dens_e + q * GMP_DENS_STRIDE);
+    const float t = __fmul_rn(h.w, gmp_exp_neg(h.x, h.y, r2h, r2l));
+    rho = __fadd_rn(rho, t);
+    drho = __fmaf_rn(-h.z, t, drho);
+  }
+  if (deriv) *deriv = drho;
+  return rho;
+}
+
+// Shared memory: tables first (radial then density), then one region per warp.
+template <int L, int NS>
+__host__ __device__ constexpr size_t warp_region_floats() {
+  return (size_t)Shape<L, NS>::WARP_FLOATS;
+}
+
+__host__ __device__ inline size_t table_floats(int n_el, int NS, int kmax) {
+  return (size_t)n_el * rad_elem_stride(NS, kmax) + (size_t)n_el * dens_elem_stride(kmax);
+}
+
+// Copies the radial and density tables to shared memory, padding each
+// element's block to its bank-spreading stride.
+__device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_rad, float* s_dens) {
+  const int per = NS * P.kmax * (GMP_RAD_STRIDE / 4);  // float4s per element in global memory
+  const int es = rad_elem_stride(NS, P.kmax) / 4;
+  for (int t = threadIdx.x; t < P.n_el * per; t += blockDim.x) {
+    const int e = t / per, r = t - e * per;
+    reinterpret_cast<float4*>(s_rad)[e * es + r] = __ldg(reinterpret_cast<const float4*>(P.rad) + t);
+  }
+  if (P.want_density) {
+    const int dper = P.kmax * (GMP_DENS_STRIDE / 4);
+    const int ds = dens_elem_stride(P.kmax) / 4;
+    for (int t = threadIdx.x; t < P.n_el * dper; t += blockDim.x) {
+      const int e = t / dper, r = t - e * dper;
+      reinterpret_cast<float4*>(s_dens)[e * ds + r] = __ldg(reinterpret_cast<const float4*>(P.dens) + t);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Forward sweep over one center's pairs: leaves mu (FP32, rounded from the
+// compensated pair) in Mu[s * NIND + k] and the conditioning bound
+// B_{l,s} = sum_pairs |R_{l,s}| r^l in Mu[NS * NIND + s * (L+1) + l]
+// (warp-private shared memory), and returns the density (all lanes).
+template <int L, int NS>
+__device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __restrict__ s_rad,
+                                               const float* __restrict__ s_dens,
+                                               const GmpPair* __restrict__ pairs, int64_t p0,
+                                               int M, float* Rt, float* St,
+                                               float* Mu, const int (&it_l)[Shape<L, NS>::Q],
+                                               const int (&it_sb)[Shape<L, NS>::Q],
+                                               const int (&it_ch)[Shape<L, NS>::Q],
+                                               const bool (&it_ok)[Shape<L, NS>::Q]) {
+  using SH = Shape<L, NS>;
+  const int lane = threadIdx.x & 31;
+  float hi[SH::Q][16], lo[SH::Q][16];
+#pragma unroll
+  for (int q = 0; q < SH::Q; ++q)
+#pragma unroll
+    for (int v = 0; v < 16; ++v) { hi[q][v] = 0.0f; lo[q][v] = 0.0f; }
+  float rho_hi = 0.0f, rho_lo = 0.0f;
+  float bnd[SH::Q][4];  // B_{l,s} partials (items holding the first chunk of an order)
+#pragma unroll
+  for (int q = 0; q < SH::Q; ++q)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bnd[q][u] = 0.0f;
+
+  const int half = lane >> 4;         // phase 1: two lanes per pair
+  const int pl = lane & 15;
+  constexpr int SG_LO = (SH::NSB + 1) / 2;  // sigma groups of half 0: [0, SG_LO)
+  const int sg0 = half ? SG_LO : 0, sg1 = half ? SH::NSB : SG_LO;
+  for (int base = 0; base < M; base += SH::TILE) {
+    const int np = min(SH::TILE, M - base);
+    // ---- phase 1: lanes (pair, half); both halves evaluate S and store
+    // alternate chunks, each half computes the radial factors of half the
+    // sigma groups
+    if (pl < np) {
+      float dx, dy, dz, r2h, r2l;
+      int e, j;
+      load_pair(pairs, p0 + base + pl, dx, dy, dz, r2h, r2l, e, j);
+      float S[SH::NIND];
+      GmpMcsh<L>::eval(dx, dy, dz, r2h, S);
+      float* srow = St + pl * SH::SSTR;
+      static_for<SH::NCH>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        constexpr int k0 = chunk_k0(c);
+        constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
+        if ((c & 1) == half) {
+          float4 v;
+          v.x = S[k0];
+          v.y = (k0 + 1 < kend) ? S[(k0 + 1 < kend) ? k0 + 1 : k0] : 0.0f;
+          v.z = (k0 + 2 < kend) ? S[(k0 + 2 < kend) ? k0 + 2 : k0] : 0.0f;
+          v.w = (k0 + 3 < kend) ? S[(k0 + 3 < kend) ? k0 + 3 : k0] : 0.0f;
+          *reinterpret_cast<float4*>(srow + 4 * c) = v;
+        }
+      });
+      if (half == 0) {  // r^l for the conditioning bound
+        const float r = __fsqrt_rn(r2h);
+        float rl[SH::RL4];
+        rl[0] = 1.0f;
+#pragma unroll
+        for (int l = 1; l < SH::RL4; ++l) rl[l] = __fmul_rn(rl[l - 1], r);
+#pragma unroll
+        for (int c = 0; c < SH::RL4 / 4; ++c)
+          *reinterpret_cast<float4*>(srow + 4 * SH::NCH + 4 * c) =
+              make_float4(rl[4 * c], rl[4 * c + 1], rl[4 * c + 2], rl[4 * c + 3]);
+      }
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+      float* rrow = Rt + pl * SH::RSTR;
+      for (int sg = sg0; sg < sg1; ++sg) {
+        float R[4][L + 1], Rd[4][L + 1];
+        radial4<L, NS, false>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
+#pragma unroll
+        for (int l = 0; l <= L; ++l)
+          *reinterpret_cast<float4*>(rrow + l * NS + 4 * sg) = make_float4(R[0][l], R[1][l], R[2][l], R[3][l]);
+      }
+      if (P.want_density && half == 0) {
+        const float t = density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, nullptr);
+        const gmp_f2 s2 = gmp_two_sum(rho_hi, t);
+        rho_hi = s2.hi;
+        rho_lo += s2.lo;
+      }
+    }
+    __syncwarp();
+    // ---- phase 2: lane = (4 sigmas) x (4 components) blocks; FP32 partials
+    // over FOLD pairs, folded into (hi, lo) by TwoSum
+#pragma unroll
+    for (int q = 0; q < SH::Q; ++q) {
+      if (!it_ok[q]) continue;
+      const float* rp = Rt + it_l[q] * NS + 4 * it_sb[q];
+      const float* sp = St + 4 * it_ch[q];
+      if (chunk_k0(it_ch[q]) == it_l[q] * it_l[q]) {  // first chunk of order l: bound B
+        const float* rlp = St + 4 * SH::NCH + it_l[q];
+        for (int pp = 0; pp < np; ++pp) {
+          const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+          const float rl = rlp[pp * SH::SSTR];
+          bnd[q][0] = __fmaf_rn(fabsf(r.x), rl, bnd[q][0]);
+          bnd[q][1] = __fmaf_rn(fabsf(r.y), rl, bnd[q][1]);
+          bnd[q][2] = __fmaf_rn(fabsf(r.z), rl, bnd[q][2]);
+          bnd[q][3] = __fmaf_rn(fabsf(r.w), rl, bnd[q][3]);
+        }
+      }
+      for (int b0 = 0; b0 < np; b0 += SH::FOLD) {
+        const int b1 = min(np, b0 + SH::FOLD);
+        float acc[16];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) acc[v] = 0.0f;
+#pragma unroll 4
+        for (int pp = b0; pp < b1; ++pp) {
+          const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+          const float4 s = *reinterpret_cast<const float4*>(sp + pp * SH::SSTR);
+          const float rv[4] = {r.x, r.y, r.z, r.w};
+          const float sv[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[4 * u + c] = __fmaf_rn(rv[u], sv[c], acc[4 * u + c]);
+        }
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+          const gmp_f2 s2 = gmp_two_sum(hi[q][v], acc[v]);
+          hi[q][v] = s2.hi;
+          lo[q][v] += s2.lo;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // ---- moments to shared memory
+#pragma unroll
+  for (int q = 0; q < SH::Q; ++q) {
+    if (!it_ok[q]) continue;
+    const int l = it_l[q];
+    const int kend = (l + 1) * (l + 1);
+    const int kbase = chunk_k0(it_ch[q]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (kbase + c < kend) Mu[(4 * it_sb[q] + u) * SH::NIND + kbase + c] = __fadd_rn(hi[q][4 * u + c], lo[q][4 * u + c]);
+    if (kbase == l * l)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] = bnd[q][u];
+  }
+  // density: warp total
+  float rho = __fadd_rn(rho_hi, rho_lo);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) rho = __fadd_rn(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+  __syncwarp();
+  return rho;
+}
+
+template <int L, int NS>
+__device__ __forceinline__ void setup_items(int (&it_l)[Shape<L, NS>::Q], int (&it_sb)[Shape<L, NS>::Q],
+                                            int (&it_ch)[Shape<L, NS>::Q], bool (&it_ok)[Shape<L, NS>::Q]) {
+  using SH = Shape<L, NS>;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < SH::Q; ++q) {
+    const int item = lane + 32 * q;
+    it_ok[q] = item < SH::NITEM;
+    const int it = it_ok[q] ? item : 0;
+    // sigma-block major within a chunk group: consecutive lanes share a chunk
+    // of S values across sigma blocks -> broadcast-friendly loads
+    it_sb[q] = it % SH::NSB;
+    it_ch[q] = it / SH::NSB;
+    it_l[q] = chunk_l(it_ch[q]);
+  }
+}
+
+__device__ __forceinline__ int64_t next_center(int32_t* counter) {
+  int64_t c = 0;
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, (int)c, 0);
+}
+
+// Features of center i from Mu; features whose value is below the FP32
+// resolution bound are queued for the FP64 refinement kernel.
+template <int L, int NS>
+__device__ __forceinline__ void write_features(const KParams& K, int64_t i, const float* Mu, float rho) {
+  using SH = Shape<L, NS>;
+  const GmpPass& P = K.pass;
+  const int lane = threadIdx.x & 31;
+  float* frow = K.features + i * P.F;
+  const int nf = P.n_ord * P.nsig;
+  for (int t = lane; t < nf; t += 32) {
+    const int o = t / P.nsig, s = t - o * P.nsig;
+    const int l = P.ord_l[o];
+    const float f = gmp_mcsh_invariant(l, Mu + s * SH::NIND + l * l);
+    frow[P.ord_col[o] + s] = f;
+    const float B = Mu[NS * SH::NIND + s * (L + 1) + l];
+    if (K.flags && f < __fmul_rn(__fmul_rn(K.flag_tau, flag_scale(l)), __fmul_rn(B, B))) {
+      const int slot = atomicAdd(K.flag_count, 1);
+      if (slot < K.flag_cap) K.flags[slot] = pack_flag(i, l, K.sig0 + s, P.ord_col[o] + s);
+    }
+  }
+  if (P.want_density && lane == 0) frow[P.dens_col] = rho;
+}
+
+// ------------------------------------------------------------------------
+template <int L, int NS>
+__global__ void __launch_bounds__(512) k_forward(KParams K) {
+  using SH = Shape<L, NS>;
+  extern __shared__ __align__(16) float smem[];
+  const GmpPass& P = K.pass;
+  float* s_rad = smem;
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
+  load_tables(P, NS, s_rad, s_dens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* St = Rt + SH::TILE * SH::RSTR;
+  float* Mu = Rt;  // reused after the sweep
+  int it_l[SH::Q], it_sb[SH::Q], it_ch[SH::Q];
+  bool it_ok[SH::Q];
+  setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
+  for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
+    const int64_t p0 = K.nbr_off[i];
+    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
+    write_features<L, NS>(K, i, Mu, rho);
+    if (K.mu_out) {
+      float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
+      for (int t = lane; t < P.nsig * SH::NIND; t += 32) mrow[t] = Mu[t];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------
+// Adjoints lam[s][k] = sum over requested orders of g_{l,s} d f_{l,s} / d mu_{l,s,k}
+// into Lam (warp-private shared memory, NS rows of NINDP floats).
+template <int L, int NS>
+__device__ __forceinline__ void adjoints(const GmpPass& P, const float* __restrict__ Mu,
+                                         const float* __restrict__ grow, float* __restrict__ Lam) {
+  using SH = Shape<L, NS>;
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < NS * SH::NINDP; t += 32) Lam[t] = 0.0f;
+  __syncwarp();
+  const int nf = P.n_ord * P.nsig;
+  for (int t = lane; t < nf; t += 32) {
+    const int o = t / P.nsig, s = t - o * P.nsig;
+    const int l = P.ord_l[o];
+    const float g = grow ? grow[P.ord_col[o] + s] : 1.0f;
+    gmp_mcsh_invariant_adjoint(l, Mu + s * SH::NIND + l * l, g, Lam + s * SH::NINDP + l * l);
+  }
+  __syncwarp();
+}
+
+// d/dd of sum_k lam_k R(r^2) S_k(d) pieces for one pair, from
+//   A = sum_k lamd_k S_k, B = sum_k (2l_k+1) lam_k S_k, V = sum_k lam_k S_{k+e}:
+//   grad = d (2 A + B / r^2) - V / r^2      (r^2 > 0)
+// where lam already carries R (and lamd carries dR/dr^2).  At d = 0 only
+// order 1 has a gradient: (lam_x, lam_y, lam_z).
+template <int L>
+__device__ __forceinline__ void pair_gradient(const float* lam, const float* lamd, float dx, float dy,
+                                              float dz, float r2, float* g) {
+  float S1[(L + 2) * (L + 2)];
+  GmpMcsh<L + 1>::eval(dx, dy, dz, r2, S1);
+  float A = 0.0f, B = 0.0f;
+#pragma unroll
+  for (int l = 0; l <= L; ++l)
+#pragma unroll
+    for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
+      A = __fmaf_rn(lamd[k], S1[k], A);
+      B = __fmaf_rn((float)(2 * l + 1) * lam[k], S1[k], B);
+    }
+  float V[3];
+  GmpMcsh<L>::shift_contract(lam, S1, V);
+  if (r2 > 0.0f) {
+    const float inv = 1.0f / r2;
+    const float c = 2.0f * A + B * inv;
+    g[0] = dx * c - V[0] * inv;
+    g[1] = dy * c - V[1] * inv;
+    g[2] = dz * c - V[2] * inv;
+  } else if (L >= 1) {
+    // independent order-1 components: (0,1,0), (0,0,1), (1,0,0) at flat 1, 2, 3
+    g[0] = lam[3]; g[1] = lam[1]; g[2] = lam[2];
+  } else {
+    g[0] = g[1] = g[2] = 0.0f;
+  }
+}
+
+template <int L, int NS>
+__global__ void __launch_bounds__(256) k_vjp(KParams K) {
+  using SH = Shape<L, NS>;
+  extern __shared__ __align__(16) float smem[];
+  const GmpPass& P = K.pass;
+  float* s_rad = smem;
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
+  load_tables(P, NS, s_rad, s_dens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* St = Rt + SH::TILE * SH::RSTR;
+  float* Mu = Rt;
+  float* Lam = St;
+  int it_l[SH::Q], it_sb[SH::Q], it_ch[SH::Q];
+  bool it_ok[SH::Q];
+  setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
+  for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
+    const int64_t p0 = K.nbr_off[i];
+    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
+    const float* grow = K.grad_feat + i * P.F;
+    if (K.features) write_features<L, NS>(K, i, Mu, rho);
+    adjoints<L, NS>(P, Mu, grow, Lam);
+    const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
+    // ---- sweep 2: lane = pair
+    float own[3] = {0.0f, 0.0f, 0.0f};
+    for (int pp = lane; pp < M; pp += 32) {
+      float dx, dy, dz, r2h, r2l;
+      int e, j;
+      load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
+      float lam[SH::NIND], lamd[SH::NIND];
+#pragma unroll
+      for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+      for (int sg = 0; sg < SH::NSB; ++sg) {
+        float R[4][L + 1], Rd[4][L + 1];
+        radial4<L, NS, true>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float* lrow = Lam + (4 * sg + u) * SH::NINDP;
+          static_for<SH::NINDP / 4>([&](auto cq) {
+            constexpr int c4 = decltype(cq)::value;
+            const float4 lv4 = *reinterpret_cast<const float4*>(lrow + 4 * c4);
+            const float lv[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+            static_for<4>([&](auto tt) {
+              constexpr int k = 4 * c4 + decltype(tt)::value;
+              if constexpr (k < SH::NIND) {
+                constexpr int l = order_of(k);
+                lam[k] = __fmaf_rn(lv[decltype(tt)::value], R[u][l], lam[k]);
+                lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[u][l], lamd[k]);
+              }
+            });
+          });
+        }
+      }
+      float g[3];
+      pair_gradient<L>(lam, lamd, dx, dy, dz, r2h, g);
+      if (P.want_density && gd != 0.0f) {
+        float drho;
+        density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
+        // d rho / d d = 2 d * d rho / d r^2
+        g[0] = __fmaf_rn(gd * 2.0f * drho, dx, g[0]);
+        g[1] = __fmaf_rn(gd * 2.0f * drho, dy, g[1]);
+        g[2] = __fmaf_rn(gd * 2.0f * drho, dz, g[2]);
+      }
+      atomicAdd(K.grad_acc + 3 * (int64_t)j + 0, (double)g[0]);
+      atomicAdd(K.grad_acc + 3 * (int64_t)j + 1, (double)g[1]);
+      atomicAdd(K.grad_acc + 3 * (int64_t)j + 2, (double)g[2]);
+      own[0] -= g[0];
+      own[1] -= g[1];
+      own[2] -= g[2];
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double o = (double)own[v];
+#pragma unroll
+      for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
+      if (lane == 0) atomicAdd(K.grad_acc + 3 * i + v, o);
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------
+// Jacobian: lane = feature (order slot, sigma); per pair
+//   d f_{l,s} / d d = 2 d dR_{l,s} P + R_{l,s} grad P,   P = sum_k lam_k S_k,
+//   r^2 grad P = (2l+1) d P - V,  V = sum_k lam_k S_{k+e}.
+// Rows are per distinct neighbor atom (images summed, lists are sorted by
+// atom), the center's own row is minus the sum of the other rows.
+template <int L, int NS>
+__global__ void __launch_bounds__(256) k_jacobian(KParams K) {
+  using SH = Shape<L, NS>;
+  extern __shared__ __align__(16) float smem[];
+  const GmpPass& P = K.pass;
+  float* s_rad = smem;
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
+  load_tables(P, NS, s_rad, s_dens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* St = Rt + SH::TILE * SH::RSTR;
+  float* Mu = Rt;
+  float* Lam = St;
+  int it_l[SH::Q], it_sb[SH::Q], it_ch[SH::Q];
+  bool it_ok[SH::Q];
+  setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
+  constexpr int QF = (8 * 16 + 1 + 31) / 32;  // features per lane (<= 8 orders x 16 sigmas + density)
+  for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
+    const int64_t p0 = K.nbr_off[i];
+    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
+    const int nf = P.n_ord * P.nsig;
+    if (K.features) write_features<L, NS>(K, i, Mu, rho);
+    // per-feature adjoints: Lam[s][k] with g = 1 for every (l, s); orders do
+    // not share components, so one array holds all of them
+    adjoints<L, NS>(P, Mu, nullptr, Lam);
+    // this lane's features
+    int f_col[QF], f_l[QF], f_s[QF];
+    bool f_ok[QF];
+#pragma unroll
+    for (int q = 0; q < QF; ++q) {
+      const int t = lane + 32 * q;
+      f_ok[q] = t < nf || (P.want_density && t == nf);
+      if (t < nf) {
+        const int o = t / P.nsig;
+        f_s[q] = t - o * P.nsig;
+        f_l[q] = P.ord_l[o];
+        f_col[q] = P.ord_col[o] + f_s[q];
+      } else {
+        f_s[q] = 0; f_l[q] = -1; f_col[q] = P.dens_col;
+      }
+    }
+    float self[QF][3], acc[QF][3];
+#pragma unroll
+    for (int q = 0; q < QF; ++q)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) { self[q][v] = 0.0f; acc[q][v] = 0.0f; }
+    int64_t row = K.jac_off[i] - 1;
+    int64_t self_row = -1;
+    int prev_j = -1;
+    for (int pp = 0; pp < M; ++pp) {
+      float dx, dy, dz, r2h, r2l;
+      int e, j;
+      load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
+      if (j != prev_j) {
+        if (prev_j >= 0) {
+#pragma unroll
+          for (int q = 0; q < QF; ++q)
+            if (f_ok[q]) {
+              float* dst = K.jac + (row * P.F + f_col[q]) * 3;
+              dst[0] = acc[q][0]; dst[1] = acc[q][1]; dst[2] = acc[q][2];
+              acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
+            }
+        }
+        ++row;
+        if (lane == 0) K.jac_j[row] = j;
+        if (j == i) self_row = row;
+        prev_j = j;
+      }
+      // radial factors of this pair for every sigma (all lanes need their own)
+      float S1[SH::NIND1];
+      GmpMcsh<L + 1>::eval(dx, dy, dz, r2h, S1);
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        if (!f_ok[q]) continue;
+        float g[3];
+        if (f_l[q] < 0) {
+          float drho;
+          density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
+          g[0] = 2.0f * drho * dx; g[1] = 2.0f * drho * dy; g[2] = 2.0f * drho * dz;
+        } else {
+          const int l = f_l[q], s = f_s[q];
+          float R = 0.0f, Rd = 0.0f;
+          for (int qq = 0; qq < P.kmax; ++qq) {
+            const float* ent = tab_e + (s * P.kmax + qq) * GMP_RAD_STRIDE;
+            const float E = gmp_exp_neg(ent[0], ent[1], r2h, r2l);
+            const float t = ent[4 + l] * E;
+            R += t;
+            Rd = __fmaf_rn(-ent[2], t, Rd);
+          }
+          const float* lam = Lam + s * SH::NINDP;
+          float Pv = 0.0f, V[3];
+          for (int k = l * l; k < (l + 1) * (l + 1); ++k) Pv = __fmaf_rn(lam[k], S1[k], Pv);
+          gmp_mcsh_shift_contract_order(l, lam, S1, V);
+          if (r2h > 0.0f) {
+            const float inv = 1.0f / r2h;
+            const float c = 2.0f * Rd * Pv + R * (float)(2 * l + 1) * Pv * inv;
+            g[0] = dx * c - R * V[0] * inv;
+            g[1] = dy * c - R * V[1] * inv;
+            g[2] = dz * c - R * V[2] * inv;
+          } else if (l == 1) {
+            g[0] = R * lam[3]; g[1] = R * lam[1]; g[2] = R * lam[2];
+          } else {
+            g[0] = g[1] = g[2] = 0.0f;
+          }
+        }
+        acc[q][0] += g[0]; acc[q][1] += g[1]; acc[q][2] += g[2];
+        if (j != i) { self[q][0] -= g[0]; self[q][1] -= g[1]; self[q][2] -= g[2]; }
+      }
+    }
+    if (prev_j >= 0) {
+#pragma unroll
+      for (int q = 0; q < QF; ++q)
+        if (f_ok[q]) {
+          float* dst = K.jac + (row * P.F + f_col[q]) * 3;
+          dst[0] = acc[q][0]; dst[1] = acc[q][1]; dst[2] = acc[q][2];
+        }
+    }
+    if (self_row >= 0) {
+#pragma unroll
+      for (int q = 0; q < QF; ++q)
+        if (f_ok[q]) {
+          float* dst = K.jac + (self_row * P.F + f_col[q]) * 3;
+          dst[0] = self[q][0]; dst[1] = self[q][1]; dst[2] = self[q][2];
+        }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace gmpk

@@ -1,0 +1,602 @@
+// Cell-list binning and exact neighbor images on the GPU.
+//
+// Neighbor set (GMP-Featurizer, Statement of Needs / Overview: molecules,
+// clusters and periodic crystals given lattice vectors and positions): all
+// (j, n in Z^3, n_k = 0 on non-periodic axes) with
+//   d = (x_j - x_i) + ((n1 a1 + n2 a2) + n3 a3),   dx*dx + dy*dy + dz*dz < rc*rc
+// where the expression is FP64, evaluated left to right without FMA.  The
+// GPU reaches the same decision with far less FP64 work:
+//   1. atoms are binned on a grid in (wrapped) fractional coordinates;
+//   2. a center scans the bins that its cutoff sphere can touch (periodic
+//      axes wrap, giving an image index m); each candidate is pre-screened
+//      in FP32 against a rigorous bound on the FP32 error;
+//   3. survivors get d and r^2 in double-float arithmetic (about 2^-44
+//      relative), which decides every case except a shell of relative width
+//      ~1e-9 around rc^2; inside that shell the FP64 expression above is
+//      evaluated exactly as written, so the set equals the FP64 one;
+//   4. each center's accepted (j, n) keys are sorted in shared memory, which
+//      makes every later sum over a center's neighbors deterministic.
+#include "gmp_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_to_double(unsigned long long k) {
+  unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
+  int q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+__device__ __forceinline__ int32_t pack_wrap(int w0, int w1, int w2) {
+  return gmp_pack_shift(w0, w1, w2);
+}
+
+// Sort key of a neighbor image: atom first, then n1, n2, n3 (each biased by 512).
+__device__ __forceinline__ unsigned long long sort_key(int64_t j, const int* n) {
+  return ((unsigned long long)j << 30) | ((unsigned long long)(n[0] + 512) << 20) |
+         ((unsigned long long)(n[1] + 512) << 10) | (unsigned long long)(n[2] + 512);
+}
+__device__ __forceinline__ void sort_key_image(unsigned long long key, int* n) {
+  n[0] = (int)((key >> 20) & 1023) - 512;
+  n[1] = (int)((key >> 10) & 1023) - 512;
+  n[2] = (int)(key & 1023) - 512;
+}
+
+// Per atom: checks, fractional coordinates, wrap, double-float split, bbox.
+__global__ void k_prepare(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
+                          int64_t N, const double* __restrict__ pos,
+                          const int32_t* __restrict__ species, int n_el,
+                          float4* __restrict__ atom_xh, float4* __restrict__ atom_xl,
+                          GmpD4* __restrict__ atom_u, unsigned long long* __restrict__ bbox,
+                          uint32_t* __restrict__ err) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int s = struct_of[a];
+    const GmpStruct& st = S[s];
+    double x[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
+    int e = species[a];
+    if (e < 0 || e >= n_el) {
+      atomicOr(err, GMP_DEV_BAD_SPECIES);
+      e = 0;
+    }
+    if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+      atomicOr(err, GMP_DEV_NONFINITE);
+      x[0] = x[1] = x[2] = 0.0;
+    }
+    double u[3];
+    int w[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
+      if (st.periodic[k]) {
+        double f = floor(u[k]);
+        if (fabs(f) > 500.0) {  // image index would not fit the packed shift
+          atomicOr(err, GMP_DEV_SHIFT_RANGE);
+          f = 0.0;
+        }
+        w[k] = (int)f;
+        u[k] -= f;
+        if (u[k] >= 1.0) { u[k] -= 1.0; w[k] += 1; }
+        if (u[k] < 0.0) u[k] = 0.0;
+      } else {
+        // both slots start at all-ones; the max slot stores the complemented key
+        atomicMin(&bbox[6 * s + 2 * k], order_key(u[k]));
+        atomicMin(&bbox[6 * s + 2 * k + 1], ~order_key(u[k]));
+      }
+    }
+    float h[3], l[3];
+    for (int k = 0; k < 3; ++k) {
+      h[k] = (float)x[k];
+      l[k] = (float)(x[k] - (double)h[k]);
+    }
+    atom_xh[a] = make_float4(h[0], h[1], h[2], __int_as_float(e));
+    atom_xl[a] = make_float4(l[0], l[1], l[2], __int_as_float(pack_wrap(w[0], w[1], w[2])));
+    atom_u[a] = GmpD4{u[0], u[1], u[2], 0.0};
+  }
+}
+
+// Per structure: bin grid and the FP32 pre-screen bound.
+__global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
+                       const unsigned long long* __restrict__ bbox, GmpGrid* __restrict__ G,
+                       double cutoff) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_struct) return;
+  const GmpStruct& st = S[s];
+  GmpGrid g;
+  double umax[3], ext[3];
+  for (int k = 0; k < 3; ++k) {
+    if (st.periodic[k]) {
+      g.umin[k] = 0.0;
+      umax[k] = 1.0;
+      ext[k] = 1.0;
+      double target = 0.5 * st.reach[k];
+      double nbf = target > 0.0 ? floor(1.0 / target) : 1.0;
+      g.nb[k] = (int)fmin(fmax(nbf, 1.0), 1024.0);
+      g.binw[k] = 1.0 / g.nb[k];
+    } else {
+      double lo = st.n_atoms ? key_to_double(bbox[6 * s + 2 * k]) : 0.0;
+      double hi = st.n_atoms ? key_to_double(~bbox[6 * s + 2 * k + 1]) : 0.0;
+      g.umin[k] = lo;
+      umax[k] = hi;
+      ext[k] = hi - lo;
+      g.binw[k] = fmax(0.5 * st.reach[k], 1e-12);
+      double nbf = floor(ext[k] / g.binw[k]) + 1.0;
+      g.nb[k] = (int)fmin(fmax(nbf, 1.0), 1024.0);
+      if (g.nb[k] == 1024) g.binw[k] = fmax(ext[k] / 1023.0, g.binw[k]);
+    }
+  }
+  // keep the grid within the reserved bin slots
+  while ((int64_t)g.nb[0] * g.nb[1] * g.nb[2] > st.bin_cap) {
+    int k = 0;
+    if (g.nb[1] > g.nb[k]) k = 1;
+    if (g.nb[2] > g.nb[k]) k = 2;
+    if (st.periodic[k]) {
+      g.nb[k] = (g.nb[k] + 1) / 2;
+      g.binw[k] = 1.0 / g.nb[k];
+    } else {
+      g.binw[k] *= 2.0;
+      g.nb[k] = (int)fmin(floor(ext[k] / g.binw[k]) + 1.0, 1024.0);
+    }
+  }
+  // Rigorous FP32 pre-screen bound.  Wrapped Cartesian coordinates are
+  // |y_c| <= Y, image shifts |s_c| <= Sh; the FP32 displacement
+  // (y_j - y_i) + s has per-component error below 2^-21 (Y + Sh) (a few
+  // roundings of magnitude <= 2Y + Sh each), so any pair with exact
+  // |d| < rc has FP32 |d| < rc + sqrt(3) delta and FP32 r^2 below
+  // (rc + 2 delta)^2 (1 + 2^-20).
+  double Y = 0.0, Sh = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    double yc = 0.0, sc = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      double a = fabs(st.A[3 * k + c]);
+      double uk = fmax(fabs(g.umin[k]), fabs(umax[k])) + 1.0;
+      yc += uk * a;
+      sc += (ceil(st.reach[k]) + 2.0) * a;
+    }
+    Y = fmax(Y, yc);
+    Sh = fmax(Sh, sc);
+  }
+  double delta = ldexp(Y + Sh + cutoff, -21);
+  double b = (cutoff + 2.0 * delta);
+  g.pad = 0;
+  G[s] = g;
+  float p2 = (float)(b * b * (1.0 + ldexp(1.0, -20)));
+  S[s].prescreen2 = nextafterf(p2, INFINITY);
+}
+
+__global__ void k_bin_assign(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
+                             const int32_t* __restrict__ struct_of, int64_t N,
+                             const GmpD4* __restrict__ atom_u, int32_t* __restrict__ atom_bin,
+                             int32_t* __restrict__ bin_count) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int s = struct_of[a];
+    const GmpGrid& g = G[s];
+    GmpD4 u4 = atom_u[a];
+    double u[3] = {u4.x, u4.y, u4.z};
+    int b[3];
+    for (int k = 0; k < 3; ++k) {
+      double t = floor((u[k] - g.umin[k]) / g.binw[k]);
+      t = fmin(fmax(t, 0.0), (double)(g.nb[k] - 1));
+      b[k] = (int)t;
+    }
+    int64_t bin = S[s].bin_base + b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]);
+    atom_bin[a] = (int32_t)bin;
+    atomicAdd(&bin_count[bin], 1);
+  }
+}
+
+__global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
+                              int64_t N, const int32_t* __restrict__ atom_bin,
+                              const int32_t* __restrict__ bin_start, int32_t* __restrict__ bin_cursor,
+                              const GmpD4* __restrict__ atom_u, float4* __restrict__ bin_y) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int s = struct_of[a];
+    const GmpStruct& st = S[s];
+    const int32_t bin = atom_bin[a];
+    const int32_t slot = bin_start[bin] + atomicAdd(&bin_cursor[bin], 1);
+    GmpD4 u4 = atom_u[a];
+    float y[3];
+    for (int c = 0; c < 3; ++c)
+      y[c] = (float)(u4.x * st.A[c] + u4.y * st.A[3 + c] + u4.z * st.A[6 + c]);
+    bin_y[slot] = make_float4(y[0], y[1], y[2], __int_as_float((int32_t)a));
+  }
+}
+
+// ------------------------------------------------------------------ scan
+template <typename T>
+__global__ void k_scan_block(const T* __restrict__ in, T* __restrict__ out, T* __restrict__ sums,
+                             int64_t n) {
+  __shared__ T sh[1024];
+  const int64_t base = (int64_t)blockIdx.x * 1024;
+  const int t = threadIdx.x;
+  T v = (base + t < n) ? in[base + t] : T(0);
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    T add = (t >= off) ? sh[t - off] : T(0);
+    __syncthreads();
+    sh[t] += add;
+    __syncthreads();
+  }
+  if (base + t < n) out[base + t] = sh[t] - v;  // exclusive
+  if (t == 1023) sums[blockIdx.x] = sh[1023];
+}
+
+template <typename T>
+__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ offs, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += offs[blockIdx.x];
+}
+
+// out[0..n] exclusive scan of in[0..n-1]; out[n] = total.  tmp sized by
+// gmp_scan_tmp_bytes(n).
+template <typename T>
+cudaError_t exclusive_scan(const T* in, T* out, int64_t n, void* tmp, cudaStream_t st,
+                           int64_t* launches) {
+  if (n <= 0) {
+    return cudaMemsetAsync(out, 0, sizeof(T), st);
+  }
+  const int64_t nb = (n + 1023) / 1024;
+  T* sums = (T*)tmp;
+  T* sums_scan = sums + nb + 1;
+  void* rest = (void*)(sums_scan + nb + 1);
+  k_scan_block<T><<<(unsigned)nb, 1024, 0, st>>>(in, out, sums, n);
+  ++*launches;
+  if (nb == 1) {
+    // total = sums[0]
+    cudaError_t e = cudaMemcpyAsync(out + n, sums, sizeof(T), cudaMemcpyDeviceToDevice, st);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  cudaError_t e = exclusive_scan<T>(sums, sums_scan, nb, rest, st, launches);
+  if (e != cudaSuccess) return e;
+  k_scan_add<T><<<(unsigned)nb, 1024, 0, st>>>(out, sums_scan, n);
+  ++*launches;
+  return cudaMemcpyAsync(out + n, sums_scan + nb, sizeof(T), cudaMemcpyDeviceToDevice, st);
+}
+
+// ----------------------------------------------------------- neighbor pass
+struct Cand {
+  bool ok;
+  int n[3];
+};
+
+// Double-float displacement of j's image n from i, and its r^2.
+__device__ __forceinline__ void df_disp(const float4& xhi, const float4& xli, const float4& xhj,
+                                        const float4& xlj, const GmpStruct& st, const int* n,
+                                        gmp_f2* d, gmp_f2& r2, float& mag) {
+  const float xi_h[3] = {xhi.x, xhi.y, xhi.z}, xi_l[3] = {xli.x, xli.y, xli.z};
+  const float xj_h[3] = {xhj.x, xhj.y, xhj.z}, xj_l[3] = {xlj.x, xlj.y, xlj.z};
+  const bool shifted = (n[0] | n[1] | n[2]) != 0;
+  mag = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    gmp_f2 dd = gmp_df_add(gmp_f2{xj_h[c], xj_l[c]}, gmp_f2{-xi_h[c], -xi_l[c]});
+    float m = fabsf(xj_h[c]) + fabsf(xi_h[c]);
+    if (shifted) {
+      gmp_f2 s0 = gmp_df_mul_int(n[0], gmp_f2{st.Ahi[c], st.Alo[c]});
+      gmp_f2 s1 = gmp_df_mul_int(n[1], gmp_f2{st.Ahi[3 + c], st.Alo[3 + c]});
+      gmp_f2 s2 = gmp_df_mul_int(n[2], gmp_f2{st.Ahi[6 + c], st.Alo[6 + c]});
+      gmp_f2 sh = gmp_df_add(gmp_df_add(s0, s1), s2);
+      dd = gmp_df_add(dd, sh);
+      m += fabsf(s0.hi) + fabsf(s1.hi) + fabsf(s2.hi);
+    }
+    d[c] = dd;
+    mag = fmaxf(mag, m);
+  }
+  r2 = gmp_df_add(gmp_df_add(gmp_df_mul(d[0], d[0]), gmp_df_mul(d[1], d[1])), gmp_df_mul(d[2], d[2]));
+}
+
+// The FP64 expression of the neighbor definition, evaluated exactly as written.
+__device__ __noinline__ bool fp64_within(const double* __restrict__ pos, int64_t i, int64_t j,
+                                         const GmpStruct& st, const int* n, double rc2) {
+  double d[3];
+  for (int c = 0; c < 3; ++c) {
+    double sh = __dadd_rn(__dadd_rn(__dmul_rn((double)n[0], st.A[c]), __dmul_rn((double)n[1], st.A[3 + c])),
+                          __dmul_rn((double)n[2], st.A[6 + c]));
+    d[c] = __dadd_rn(__dsub_rn(pos[3 * j + c], pos[3 * i + c]), sh);
+  }
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+  return r2 < rc2;
+}
+
+__device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, int64_t i, int64_t j,
+                                             const float4& xhi, const float4& xli, const float4& xhj,
+                                             const float4& xlj, const GmpStruct& st, const int* n,
+                                             float rc2hi, float rc2lo, double rc2, float cutoff) {
+  gmp_f2 d[3], r2;
+  float mag;
+  df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
+  gmp_f2 diff = gmp_df_add(r2, gmp_f2{-rc2hi, -rc2lo});
+  // double-float error bound (generous): 2^-36 (mag + rc + 1) (rc + 1) * 16
+  const float tol = ldexpf((mag + cutoff + 1.0f) * (cutoff + 1.0f) * 16.0f, -36);
+  if (diff.hi < -tol) return true;
+  if (diff.hi > tol) return false;
+  return fp64_within(pos, i, j, st, n, rc2);
+}
+
+// Warp per center.  fill = 0: count exact neighbors; fill = 1: collect keys,
+// sort, and write the pair records at offsets[i].
+__global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
+                            const int32_t* __restrict__ struct_of, int64_t N, float cutoff,
+                            float rc2hi, float rc2lo, double rc2, const double* __restrict__ pos,
+                            const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
+                            const GmpD4* __restrict__ atom_u, const int32_t* __restrict__ bin_start,
+                            const float4* __restrict__ bin_y, int64_t* __restrict__ counts,
+                            const int64_t* __restrict__ offsets, GmpPair* __restrict__ pairs,
+                            int max_keys, int32_t* __restrict__ maxm, uint32_t* __restrict__ err) {
+  extern __shared__ unsigned long long sh_keys[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= N) return;
+  unsigned long long* keys = sh_keys + (size_t)wib * max_keys;
+  __shared__ int s_cnt[32];
+  if (lane == 0) s_cnt[wib] = 0;
+  __syncwarp();
+
+  const int s = struct_of[i];
+  const GmpStruct& st = S[s];
+  const GmpGrid g = G[s];
+  const float4 xhi = atom_xh[i], xli = atom_xl[i];
+  int wi[3];
+  gmp_unpack_shift(__float_as_int(xli.w), wi);
+  const GmpD4 ui4 = atom_u[i];
+  const double ui[3] = {ui4.x, ui4.y, ui4.z};
+  int lo[3], span[3];
+  for (int k = 0; k < 3; ++k) {
+    double a = (ui[k] - st.reach[k] - g.umin[k]) / g.binw[k];
+    double b = (ui[k] + st.reach[k] - g.umin[k]) / g.binw[k];
+    int l0 = (int)floor(a - 1e-7), h0 = (int)floor(b + 1e-7);
+    if (!st.periodic[k]) {
+      l0 = max(l0, 0);
+      h0 = min(h0, g.nb[k] - 1);
+    }
+    lo[k] = l0;
+    span[k] = max(h0 - l0 + 1, 0);
+  }
+  // wrapped FP32 position of the center
+  float yi[3];
+  for (int c = 0; c < 3; ++c)
+    yi[c] = (float)(ui[0] * st.A[c] + ui[1] * st.A[3 + c] + ui[2] * st.A[6 + c]);
+  const float p2 = st.prescreen2;
+  const int total = span[0] * span[1] * span[2];
+  int count = 0;
+  for (int cidx = lane; cidx < total; cidx += 32) {
+    int c0 = cidx % span[0];
+    int c1 = (cidx / span[0]) % span[1];
+    int c2 = cidx / (span[0] * span[1]);
+    int bb[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
+    int m[3], bw[3];
+    for (int k = 0; k < 3; ++k) {
+      if (st.periodic[k]) {
+        m[k] = floor_div(bb[k], g.nb[k]);
+        bw[k] = bb[k] - m[k] * g.nb[k];
+      } else {
+        m[k] = 0;
+        bw[k] = bb[k];
+      }
+    }
+    const int64_t bin = st.bin_base + bw[0] + (int64_t)g.nb[0] * (bw[1] + (int64_t)g.nb[1] * bw[2]);
+    float sh[3];
+    for (int c = 0; c < 3; ++c)
+      sh[c] = (float)m[0] * st.Ahi[c] + (float)m[1] * st.Ahi[3 + c] + (float)m[2] * st.Ahi[6 + c];
+    const int b0 = bin_start[bin], b1 = bin_start[bin + 1];
+    for (int slot = b0; slot < b1; ++slot) {
+      const float4 yj = bin_y[slot];
+      const float dx = (yj.x - yi[0]) + sh[0];
+      const float dy = (yj.y - yi[1]) + sh[1];
+      const float dz = (yj.z - yi[2]) + sh[2];
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 > p2) continue;
+      const int64_t j = __float_as_int(yj.w);
+      const float4 xhj = atom_xh[j], xlj = atom_xl[j];
+      int wj[3];
+      gmp_unpack_shift(__float_as_int(xlj.w), wj);
+      int n[3] = {m[0] + wi[0] - wj[0], m[1] + wi[1] - wj[1], m[2] + wi[2] - wj[2]};
+      if (!exact_accept(pos, i, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff)) continue;
+      if (abs(n[0]) >= 512 || abs(n[1]) >= 512 || abs(n[2]) >= 512) {
+        atomicOr(err, GMP_DEV_SHIFT_RANGE);  // reported after the count pass
+        continue;
+      }
+      if (fill) {
+        int slot_k = atomicAdd(&s_cnt[wib], 1);
+        if (slot_k < max_keys)
+          keys[slot_k] = sort_key(j, n);
+      }
+      ++count;
+    }
+  }
+  // warp total
+  for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+  if (!fill) {
+    if (lane == 0) {
+      counts[i] = count;
+      atomicMax(maxm, count);
+    }
+    return;
+  }
+  __syncwarp();
+  const int M = s_cnt[wib];
+  const int64_t base = offsets[i];
+  if (M != (int)(offsets[i + 1] - base) || M > max_keys) {
+    if (lane == 0) atomicOr(err, GMP_DEV_TOO_MANY_NEIGHBORS);
+    return;
+  }
+  // bitonic sort of the M keys (padded to a power of two with ~0)
+  int P2 = 1;
+  while (P2 < M) P2 <<= 1;
+  for (int t = M + lane; t < P2; t += 32) keys[t] = ~0ull;
+  __syncwarp();
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int t = lane; t < P2; t += 32) {
+        int partner = t ^ jj;
+        if (partner > t) {
+          unsigned long long a = keys[t], b = keys[partner];
+          bool up = (t & k) == 0;
+          if ((a > b) == up) {
+            keys[t] = b;
+            keys[partner] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // records (recompute the same double-float displacement)
+  for (int t = lane; t < M; t += 32) {
+    const unsigned long long key = keys[t];
+    const int64_t j = (int64_t)(key >> 30);
+    int n[3];
+    sort_key_image(key, n);
+    const int32_t packed = gmp_pack_shift(n[0], n[1], n[2]);
+    const float4 xhj = atom_xh[j], xlj = atom_xl[j];
+    gmp_f2 d[3], r2;
+    float mag;
+    df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
+    GmpPair p;
+    p.dx = d[0].hi + d[0].lo;
+    p.dy = d[1].hi + d[1].lo;
+    p.dz = d[2].hi + d[2].lo;
+    p.r2hi = r2.hi;
+    p.r2lo = r2.lo;
+    p.e = __float_as_int(xhj.w);
+    p.j = (int32_t)j;
+    p.shift = packed;
+    pairs[base + t] = p;
+  }
+}
+
+__global__ void k_unpack(int64_t P, const GmpPair* __restrict__ pairs, int32_t* __restrict__ nbr_j,
+                         int32_t* __restrict__ nbr_shift) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    GmpPair p = pairs[t];
+    int n[3];
+    gmp_unpack_shift(p.shift, n);
+    nbr_j[t] = p.j;
+    nbr_shift[3 * t] = n[0];
+    nbr_shift[3 * t + 1] = n[1];
+    nbr_shift[3 * t + 2] = n[2];
+  }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int sm_count) {
+  int64_t b = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+size_t gmp_scan_tmp_bytes(int64_t n) {
+  size_t total = 0;
+  while (true) {
+    int64_t nb = (n + 1023) / 1024;
+    total += 2 * (size_t)(nb + 1) * sizeof(int64_t);
+    if (nb <= 1) break;
+    n = nb;
+  }
+  return total + 256;
+}
+
+cudaError_t gmp_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp,
+                                   cudaStream_t stream, int64_t* launches) {
+  return exclusive_scan<int64_t>(in, out, n, tmp, stream, launches);
+}
+
+cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struct,
+                                         const int32_t* d_struct_of, int64_t N, double cutoff,
+                                         const double* pos, const int32_t* species, int n_el,
+                                         GmpGrid* d_grid, float4* atom_xh, float4* atom_xl,
+                                         GmpD4* atom_u, int32_t* atom_bin,
+                                         unsigned long long* d_bbox, uint32_t* d_err,
+                                         cudaStream_t stream, int sm_count, int64_t* launches) {
+  (void)atom_bin;
+  cudaError_t e = cudaMemsetAsync(d_bbox, 0xFF, sizeof(unsigned long long) * 6 * n_struct, stream);
+  if (e != cudaSuccess) return e;
+  k_prepare<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, pos, species,
+                                                            n_el, atom_xh, atom_xl, atom_u, d_bbox,
+                                                            d_err);
+  ++*launches;
+  k_grid<<<(n_struct + 127) / 128, 128, 0, stream>>>((GmpStruct*)d_structs, n_struct, d_bbox, d_grid,
+                                                     cutoff);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
+                            const int32_t* d_struct_of, int64_t N, int64_t n_bins,
+                            const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
+                            int32_t* bin_cursor, int32_t* bin_atoms, float4* bin_y,
+                            const float4* atom_xh, const float4* atom_xl, const GmpD4* atom_u,
+                            void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
+                            int sm_count, int64_t* launches) {
+  (void)atom_xh;
+  (void)atom_xl;
+  (void)scan_tmp_bytes;
+  cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * n_bins, stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(bin_cursor, 0, sizeof(int32_t) * n_bins, stream);
+  if (e != cudaSuccess) return e;
+  k_bin_assign<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, d_struct_of, N,
+                                                               atom_u, (int32_t*)atom_bin, bin_count);
+  ++*launches;
+  e = exclusive_scan<int32_t>(bin_count, bin_start, n_bins, scan_tmp, stream, launches);
+  if (e != cudaSuccess) return e;
+  k_bin_scatter<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, atom_bin,
+                                                                bin_start, bin_cursor, atom_u, bin_y);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
+                                     const int32_t* d_struct_of, int64_t N, double cutoff,
+                                     const double* pos, const float4* atom_xh, const float4* atom_xl,
+                                     const GmpD4* atom_u, const int32_t* bin_start,
+                                     const float4* bin_y, int64_t* counts, const int64_t* offsets,
+                                     GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
+                                     cudaStream_t stream, int sm_count, int64_t* launches) {
+  (void)sm_count;
+  const double rc2 = cutoff * cutoff;
+  const float rc2hi = (float)rc2;
+  const float rc2lo = (float)(rc2 - (double)rc2hi);
+  int warps = 4;
+  size_t smem = 0;
+  if (fill) {
+    while (warps > 1 && (size_t)warps * max_keys * 8 > 96 * 1024) warps >>= 1;
+    smem = (size_t)warps * max_keys * 8;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const unsigned blocks = (unsigned)((N + warps - 1) / warps);
+  k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, d_struct_of, N,
+                                                    (float)cutoff, rc2hi, rc2lo, rc2, pos, atom_xh,
+                                                    atom_xl, atom_u, bin_start, bin_y, counts,
+                                                    offsets, pairs, max_keys, d_maxm, d_err);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,
+                                        int32_t* nbr_shift, cudaStream_t stream,
+                                        int64_t* launches) {
+  if (P <= 0) return cudaSuccess;
+  k_unpack<<<grid_for(P, 256, 152), 256, 0, stream>>>(P, pairs, nbr_j, nbr_shift);
+  ++*launches;
+  return cudaGetLastError();
+}
