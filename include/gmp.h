@@ -131,6 +131,31 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t *atom_off
                          const int32_t *species, int64_t *nbr_off, int32_t *nbr_j,
                          int32_t *nbr_shift, int64_t cap, int64_t *nnz_out, void *stream);
 
+/* Neighbor-image counts of one structure without allocating device memory.
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * call cudaMalloc -- code running inside another library's allocator or
+ * memory-pool callbacks, loops that cannot afford cudaMalloc's implicit
+ * device-wide synchronisation, processes that reserve all device memory up
+ * front.  It runs the same binning and exact count kernels as gmp_neighbors
+ * and needs no handle: all scratch lives in a fixed static device array
+ * (about 4 MB, held by every GPU that loads the library until the process
+ * exits), sized for at most 32768 atoms; larger n_atoms returns
+ * GMP_ERR_CAPACITY with a message on stderr before any GPU work.
+ *   pos [n_atoms, 3] float64 DEVICE pointer (raw Cartesian, Angstrom);
+ *   cell [3,3] float64 and pbc [3] uint8 HOST arrays (as in gmp_featurize);
+ *   counts [n_atoms] int64 DEVICE output: neighbor images of each atom
+ *   within `cutoff`, self included (equal to nbr_off[i+1] - nbr_off[i] of
+ *   gmp_neighbors with the same cutoff).
+ * The call runs on `stream` and synchronises it before returning (to read
+ * the device error word).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array and each call resets what must start at zero, so calls that overlap
+ * on the GPU (other streams, other host threads) race: serialise them. */
+gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double *pos, const double *cell,
+                                       const uint8_t *pbc, double cutoff, int64_t *counts,
+                                       void *stream);
+
 /* Wait for `stream` with a timeout (seconds, <= 0: wait forever) by polling
  * an event; returns GMP_ERR_TIMEOUT if the work has not finished. */
 gmp_status gmp_sync(gmp_handle h, void *stream, double timeout_s);
