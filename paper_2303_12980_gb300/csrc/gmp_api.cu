@@ -70,10 +70,11 @@ struct gmp_ctx {
   std::vector<uint8_t> last_pbc;
   int64_t n_bins = 0;
   // workspace
-  DevBuf structs, grid, atom_off, struct_of, bbox, atom_xh, atom_xl, atom_u, atom_bin;
+  DevBuf structs, grid, atom_off, struct_of, bbox, atom_xh, atom_xl, atom_u, atom_bin, atom_rng, atom_y;
   DevBuf bin_count, bin_cursor, bin_start, bin_y, counts, nbr_off, scan_tmp, pairs;
   DevBuf scalars;  // err word, maxm, counter
   DevBuf grad_acc, jac_counts;
+  DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // FP64 radial constants [n_el][n_sigmas][kmax][3] for the refinement kernel
   DevBuf flagq;  // queued ill-conditioned features
   DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp;
@@ -257,7 +258,7 @@ cudaError_t prof_mark(gmp_ctx* h, int stage, bool begin, cudaStream_t st) {
 // Binning + exact neighbor lists into h->pairs / h->nbr_off.  Synchronises
 // `st` once (to size the pair buffer).
 gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
-                           int64_t N, cudaStream_t st) {
+                           int64_t N, cudaStream_t st, bool sorted) {
   int64_t* L = &h->launches;
   GMP_CK(prof_mark(h, 0, true, st), "profile");
   uint32_t* d_err = h->scalars.as<uint32_t>();
@@ -269,6 +270,8 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   GMP_CK(h->atom_xl.ensure(sizeof(float4) * N), "atom_xl");
   GMP_CK(h->atom_u.ensure(sizeof(GmpD4) * N), "atom_u");
   GMP_CK(h->atom_bin.ensure(sizeof(int32_t) * N), "atom_bin");
+  GMP_CK(h->atom_rng.ensure(sizeof(int4) * N), "atom_rng");
+  GMP_CK(h->atom_y.ensure(sizeof(float4) * N), "atom_y");
   GMP_CK(h->bin_count.ensure(sizeof(int32_t) * h->n_bins), "bin_count");
   GMP_CK(h->bin_cursor.ensure(sizeof(int32_t) * h->n_bins), "bin_cursor");
   GMP_CK(h->bin_start.ensure(sizeof(int32_t) * (h->n_bins + 1)), "bin_start");
@@ -285,14 +288,15 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
          "prepare");
   GMP_CK(gmp_launch_bins(h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(), N,
                          h->n_bins, h->atom_bin.as<int32_t>(), h->bin_count.as<int32_t>(),
-                         h->bin_start.as<int32_t>(), h->bin_cursor.as<int32_t>(), nullptr, h->bin_y.as<float4>(),
-                         h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->atom_u.as<GmpD4>(), h->scan_tmp.p,
+                         h->bin_start.as<int32_t>(), h->bin_cursor.as<int32_t>(), h->atom_rng.as<int4>(),
+                         h->atom_y.as<float4>(), h->bin_y.as<float4>(), h->atom_u.as<GmpD4>(), h->scan_tmp.p,
                          h->scan_tmp.bytes, st, h->sm_count, L),
          "bins");
   GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
                                   N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                                  h->atom_u.as<GmpD4>(), h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
-                                  h->counts.as<int64_t>(), nullptr, nullptr, 0, d_maxm, d_err, st, h->sm_count, L),
+                                  h->atom_rng.as<int4>(), h->atom_y.as<float4>(), h->bin_start.as<int32_t>(),
+                                  h->bin_y.as<float4>(), h->counts.as<int64_t>(), nullptr, nullptr, 0, d_maxm, d_err,
+                                  st, h->sm_count, L),
          "neighbor count");
   GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), N, h->scan_tmp.p, st, L), "scan");
   GMP_CK(cudaMemcpyAsync(h->h_small, h->nbr_off.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read P");
@@ -311,9 +315,10 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   if ((size_t)keys * 8 > 200 * 1024)
     return fail(h, GMP_ERR_CAPACITY, "a center has " + std::to_string(maxm) + " neighbor images (limit 25600)");
   GMP_CK(h->pairs.ensure(sizeof(GmpPair) * (h->P > 0 ? h->P : 1)), "pairs");
-  GMP_CK(gmp_launch_neighbor_pass(1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
-                                  N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                                  h->atom_u.as<GmpD4>(), h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
+  GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(),
+                                  h->struct_of.as<int32_t>(), N, h->cutoff, pos, h->atom_xh.as<float4>(),
+                                  h->atom_xl.as<float4>(), h->atom_rng.as<int4>(), h->atom_y.as<float4>(),
+                                  h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
                                   nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), keys, d_maxm, d_err, st,
                                   h->sm_count, L),
          "neighbor fill");
@@ -612,7 +617,7 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
   } else if (!is_device_ptr(features)) {
     return fail(h, GMP_ERR_INVALID_ARG, "features must be a device pointer when inputs are");
   }
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, false)) != GMP_OK) return r;
   if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 1, true, st), "profile");
   for (size_t g = 0; g < h->passes.size(); ++g) {
@@ -655,17 +660,31 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     GMP_CK(h->stage_gradp.ensure(sizeof(float) * N * 3), "stage grad_pos");
     gp = h->stage_gradp.as<float>();
   }
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, false)) != GMP_OK) return r;
   GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
   if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 1, true, st), "profile");
   for (size_t g = 0; g < h->passes.size(); ++g) {
-    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
-    K.features = feat;
+    const PassData& pd = h->passes[g];
+    // forward kernel (features + moments), then the backward kernel reading
+    // the moments: two lean kernels instead of one fused kernel
+    const size_t mu_floats = (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1);
+    GMP_CK(h->mu.ensure(sizeof(float) * mu_floats), "moments");
+    float* fout = feat;
+    if (!fout) {
+      GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
+      fout = h->stage_feat.as<float>();
+    }
+    gmpk::KParams K = base_params(h, pd, (int)g, N);
+    K.features = fout;
+    K.mu_out = h->mu.as<float>();
+    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, st, h->sm_count, &h->launches), "forward");
+    K.features = nullptr;
+    K.flags = nullptr;
     K.grad_feat = gf;
     K.grad_acc = h->grad_acc.as<double>();
-    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_VJP, h->passes[g].NS, K, st, h->sm_count, &h->launches), "vjp");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_BACKWARD, pd.NS, K, st, h->sm_count, &h->launches), "backward");
   }
   if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 1, false, st), "profile");
@@ -693,7 +712,7 @@ gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t*
   if (!jac_off) return fail(h, GMP_ERR_INVALID_ARG, "jac_off is required");
   Io io;
   if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true)) != GMP_OK) return r;
   GMP_CK(h->jac_counts.ensure(sizeof(int64_t) * (2 * N + 1)), "jac counts");
   int64_t* cnt = h->jac_counts.as<int64_t>();
   int64_t* joff = cnt + N;
@@ -759,7 +778,7 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t* atom_off
   if (!nbr_off) return fail(h, GMP_ERR_INVALID_ARG, "nbr_off is required");
   Io io;
   if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true)) != GMP_OK) return r;
   *nnz_out = h->P;
   if (h->P > cap) return fail(h, GMP_ERR_CAPACITY, "neighbor list needs " + std::to_string(h->P) + " entries");
   if (h->P > 0 && (!nbr_j || !nbr_shift)) return fail(h, GMP_ERR_INVALID_ARG, "nbr_j and nbr_shift are required");
@@ -845,8 +864,8 @@ void gmp_destroy(gmp_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   for (auto& pd : h->passes) pd.rad.release();
-  DevBuf* bufs[] = {&h->ktab, &h->flagq, &h->dens, &h->structs, &h->grid, &h->atom_off, &h->struct_of, &h->bbox, &h->atom_xh,
-                    &h->atom_xl, &h->atom_u, &h->atom_bin, &h->bin_count, &h->bin_cursor, &h->bin_start,
+  DevBuf* bufs[] = {&h->mu, &h->ktab, &h->flagq, &h->dens, &h->structs, &h->grid, &h->atom_off, &h->struct_of, &h->bbox, &h->atom_xh,
+                    &h->atom_xl, &h->atom_u, &h->atom_bin, &h->atom_rng, &h->atom_y, &h->bin_count, &h->bin_cursor, &h->bin_start,
                     &h->bin_y, &h->counts, &h->nbr_off, &h->scan_tmp, &h->pairs, &h->scalars, &h->grad_acc,
                     &h->jac_counts, &h->stage_pos, &h->stage_species, &h->stage_feat, &h->stage_gradf,
                     &h->stage_gradp};

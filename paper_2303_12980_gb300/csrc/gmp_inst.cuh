@@ -14,9 +14,10 @@ size_t smem_bytes(const GmpPass& P, int warps) {
 
 template <int L, int NS>
 cudaError_t launch(int kind, const KParams& K, cudaStream_t st, int sm_count, int64_t* launches) {
-  void (*fn)(KParams) = kind == GMP_KIND_FORWARD ? k_forward<L, NS>
-                        : kind == GMP_KIND_VJP   ? k_vjp<L, NS>
-                                                 : k_jacobian<L, NS>;
+  void (*fn)(KParams) = kind == GMP_KIND_FORWARD    ? k_forward<L, NS>
+                        : kind == GMP_KIND_VJP      ? k_vjp<L, NS>
+                        : kind == GMP_KIND_BACKWARD ? k_backward<L, NS>
+                                                    : k_jacobian<L, NS>;
   // as many warps per CTA as the kernel allows (launch bounds) and 227 KB of
   // shared memory fit
   cudaFuncAttributes fa;

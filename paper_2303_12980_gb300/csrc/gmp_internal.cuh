@@ -32,14 +32,16 @@ struct GmpStruct {
   int64_t bin_base;   // first bin slot of this structure
   int32_t bin_cap;    // bin slots reserved
   int32_t pad1;
-  float prescreen2;   // FP32 pre-screen bound on r^2 (rigorous, see neighbors.cu)
-  float pad2[3];
+  float prescreen2;   // FP32 r^2 above this: certainly outside the cutoff (see neighbors.cu)
+  float inside2;      // FP32 r^2 below this: certainly inside the cutoff
+  float pad2[2];
 };
 
 // Per-structure bin grid (device-built from bounding boxes).
 struct GmpGrid {
   double umin[3];     // fractional coordinate of bin 0 edge
   double binw[3];     // bin width (fractional)
+  double inv_binw[3]; // 1 / binw
   int nb[3];          // bins per axis
   int pad;
 };
@@ -165,17 +167,18 @@ cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struc
 cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
                             const int32_t* d_struct_of, int64_t N, int64_t n_bins,
                             const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
-                            int32_t* bin_cursor, int32_t* bin_atoms, float4* bin_y,
-                            const float4* atom_xh, const float4* atom_xl, const GmpD4* atom_u,
-                            void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
+                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y,
+                            const GmpD4* atom_u, void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
                             int sm_count, int64_t* launches);
 size_t gmp_scan_tmp_bytes(int64_t n);
 cudaError_t gmp_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp,
                                    cudaStream_t stream, int64_t* launches);
+// fill: 0 = count only, 1 = records in enumeration order (deterministic),
+// 2 = records sorted by (neighbor atom, image)
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const int32_t* d_struct_of, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const GmpD4* atom_u, const int32_t* bin_start,
+                                     const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
                                      cudaStream_t stream, int sm_count, int64_t* launches);

@@ -84,7 +84,7 @@ struct Shape {
   static constexpr int RSTR = odd4((L + 1) * NS);
   static constexpr int SSTR = odd4(NCH * 4 + RL4);
   static constexpr int TILE = 16;                  // pairs staged per tile (2 lanes per pair)
-  static constexpr int FOLD = 8;                   // pairs per FP32 partial before the TwoSum fold
+  static constexpr int FOLD = 16;                  // pairs per FP32 partial before the TwoSum fold
   static constexpr int NINDP = (NIND + 3) / 4 * 4; // padded row of per-sigma vectors
   static constexpr int WARP_FLOATS = TILE * RSTR + TILE * SSTR;
   static_assert(NS * NIND + NS * (L + 1) <= TILE * RSTR, "moments and bounds must fit the R tile");
@@ -267,23 +267,22 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       float dx, dy, dz, r2h, r2l;
       int e, j;
       load_pair(pairs, p0 + base + pl, dx, dy, dz, r2h, r2l, e, j);
-      float S[SH::NIND];
-      GmpMcsh<L>::eval(dx, dy, dz, r2h, S);
       float* srow = St + pl * SH::SSTR;
-      static_for<SH::NCH>([&](auto cc) {
-        constexpr int c = decltype(cc)::value;
-        constexpr int k0 = chunk_k0(c);
-        constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
-        if ((c & 1) == half) {
+      if (half == 0) {  // MCSH components
+        float S[SH::NIND];
+        GmpMcsh<L>::eval(dx, dy, dz, r2h, S);
+        static_for<SH::NCH>([&](auto cc) {
+          constexpr int c = decltype(cc)::value;
+          constexpr int k0 = chunk_k0(c);
+          constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
           float4 v;
           v.x = S[k0];
           v.y = (k0 + 1 < kend) ? S[(k0 + 1 < kend) ? k0 + 1 : k0] : 0.0f;
           v.z = (k0 + 2 < kend) ? S[(k0 + 2 < kend) ? k0 + 2 : k0] : 0.0f;
           v.w = (k0 + 3 < kend) ? S[(k0 + 3 < kend) ? k0 + 3 : k0] : 0.0f;
           *reinterpret_cast<float4*>(srow + 4 * c) = v;
-        }
-      });
-      if (half == 0) {  // r^l for the conditioning bound
+        });
+      } else {  // r^l for the conditioning bound
         const float r = __fsqrt_rn(r2h);
         float rl[SH::RL4];
         rl[0] = 1.0f;
@@ -511,6 +510,73 @@ __device__ __forceinline__ void pair_gradient(const float* lam, const float* lam
   }
 }
 
+// ------------------------------------------------------------------------
+// Backward only: moments come from the forward kernel (K.mu_out, read), the
+// per-pair terms are recomputed.  Lane = pair.
+template <int L, int NS>
+__device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
+                                               const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
+                                               const float* __restrict__ Lam, float gd) {
+  using SH = Shape<L, NS>;
+  const GmpPass& P = K.pass;
+  const int lane = threadIdx.x & 31;
+  float own[3] = {0.0f, 0.0f, 0.0f};
+  for (int pp = lane; pp < M; pp += 32) {
+    float dx, dy, dz, r2h, r2l;
+    int e, j;
+    load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
+    float lam[SH::NIND], lamd[SH::NIND];
+#pragma unroll
+    for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
+    const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+    for (int sg = 0; sg < SH::NSB; ++sg) {
+      float R[4][L + 1], Rd[4][L + 1];
+      radial4<L, NS, true>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* lrow = Lam + (4 * sg + u) * SH::NINDP;
+        static_for<SH::NINDP / 4>([&](auto cq) {
+          constexpr int c4 = decltype(cq)::value;
+          const float4 lv4 = *reinterpret_cast<const float4*>(lrow + 4 * c4);
+          const float lv[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+          static_for<4>([&](auto tt) {
+            constexpr int k = 4 * c4 + decltype(tt)::value;
+            if constexpr (k < SH::NIND) {
+              constexpr int l = order_of(k);
+              lam[k] = __fmaf_rn(lv[decltype(tt)::value], R[u][l], lam[k]);
+              lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[u][l], lamd[k]);
+            }
+          });
+        });
+      }
+    }
+    float g[3];
+    pair_gradient<L>(lam, lamd, dx, dy, dz, r2h, g);
+    if (P.want_density && gd != 0.0f) {
+      float drho;
+      density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
+      const float c = __fmul_rn(__fmul_rn(gd, 2.0f), drho);
+      g[0] = __fmaf_rn(c, dx, g[0]);
+      g[1] = __fmaf_rn(c, dy, g[1]);
+      g[2] = __fmaf_rn(c, dz, g[2]);
+    }
+    atomicAdd(K.grad_acc + 3 * (int64_t)j + 0, (double)g[0]);
+    atomicAdd(K.grad_acc + 3 * (int64_t)j + 1, (double)g[1]);
+    atomicAdd(K.grad_acc + 3 * (int64_t)j + 2, (double)g[2]);
+    own[0] -= g[0];
+    own[1] -= g[1];
+    own[2] -= g[2];
+  }
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    double o = (double)own[v];
+#pragma unroll
+    for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
+    if (lane == 0) atomicAdd(K.grad_acc + 3 * i + v, o);
+  }
+}
+
+// Fused forward + backward for one center at a time (moments stay on chip).
 template <int L, int NS>
 __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   using SH = Shape<L, NS>;
@@ -537,61 +603,34 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
     if (K.features) write_features<L, NS>(K, i, Mu, rho);
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    // ---- sweep 2: lane = pair
-    float own[3] = {0.0f, 0.0f, 0.0f};
-    for (int pp = lane; pp < M; pp += 32) {
-      float dx, dy, dz, r2h, r2l;
-      int e, j;
-      load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
-      float lam[SH::NIND], lamd[SH::NIND];
-#pragma unroll
-      for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
-      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
-      for (int sg = 0; sg < SH::NSB; ++sg) {
-        float R[4][L + 1], Rd[4][L + 1];
-        radial4<L, NS, true>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float* lrow = Lam + (4 * sg + u) * SH::NINDP;
-          static_for<SH::NINDP / 4>([&](auto cq) {
-            constexpr int c4 = decltype(cq)::value;
-            const float4 lv4 = *reinterpret_cast<const float4*>(lrow + 4 * c4);
-            const float lv[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
-            static_for<4>([&](auto tt) {
-              constexpr int k = 4 * c4 + decltype(tt)::value;
-              if constexpr (k < SH::NIND) {
-                constexpr int l = order_of(k);
-                lam[k] = __fmaf_rn(lv[decltype(tt)::value], R[u][l], lam[k]);
-                lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[u][l], lamd[k]);
-              }
-            });
-          });
-        }
-      }
-      float g[3];
-      pair_gradient<L>(lam, lamd, dx, dy, dz, r2h, g);
-      if (P.want_density && gd != 0.0f) {
-        float drho;
-        density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
-        // d rho / d d = 2 d * d rho / d r^2
-        g[0] = __fmaf_rn(gd * 2.0f * drho, dx, g[0]);
-        g[1] = __fmaf_rn(gd * 2.0f * drho, dy, g[1]);
-        g[2] = __fmaf_rn(gd * 2.0f * drho, dz, g[2]);
-      }
-      atomicAdd(K.grad_acc + 3 * (int64_t)j + 0, (double)g[0]);
-      atomicAdd(K.grad_acc + 3 * (int64_t)j + 1, (double)g[1]);
-      atomicAdd(K.grad_acc + 3 * (int64_t)j + 2, (double)g[2]);
-      own[0] -= g[0];
-      own[1] -= g[1];
-      own[2] -= g[2];
-    }
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      double o = (double)own[v];
-#pragma unroll
-      for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
-      if (lane == 0) atomicAdd(K.grad_acc + 3 * i + v, o);
-    }
+    backward_sweep<L, NS>(K, s_rad, s_dens, i, p0, M, Lam, gd);
+    __syncwarp();
+  }
+}
+
+template <int L, int NS>
+__global__ void __launch_bounds__(256) k_backward(KParams K) {
+  using SH = Shape<L, NS>;
+  extern __shared__ __align__(16) float smem[];
+  const GmpPass& P = K.pass;
+  float* s_rad = smem;
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
+  load_tables(P, NS, s_rad, s_dens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* Lam = Mu + SH::TILE * SH::RSTR;
+  for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
+    const int64_t p0 = K.nbr_off[i];
+    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
+    for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
+    __syncwarp();
+    const float* grow = K.grad_feat + i * P.F;
+    adjoints<L, NS>(P, Mu, grow, Lam);
+    const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
+    backward_sweep<L, NS>(K, s_rad, s_dens, i, p0, M, Lam, gd);
     __syncwarp();
   }
 }

@@ -7,6 +7,7 @@
 #define GMP_KIND_FORWARD 0
 #define GMP_KIND_VJP 1
 #define GMP_KIND_JACOBIAN 2
+#define GMP_KIND_BACKWARD 3
 
 namespace gmpk {
 struct KParams;

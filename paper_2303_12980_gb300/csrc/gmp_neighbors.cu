@@ -146,12 +146,16 @@ __global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
       g.nb[k] = (int)fmin(floor(ext[k] / g.binw[k]) + 1.0, 1024.0);
     }
   }
-  // Rigorous FP32 pre-screen bound.  Wrapped Cartesian coordinates are
+  // Rigorous two-sided FP32 bounds.  Wrapped Cartesian coordinates are
   // |y_c| <= Y, image shifts |s_c| <= Sh; the FP32 displacement
-  // (y_j - y_i) + s has per-component error below 2^-21 (Y + Sh) (a few
-  // roundings of magnitude <= 2Y + Sh each), so any pair with exact
-  // |d| < rc has FP32 |d| < rc + sqrt(3) delta and FP32 r^2 below
-  // (rc + 2 delta)^2 (1 + 2^-20).
+  // (y_j - y_i) + s has per-component error below 2^-22 (4Y + 4Sh + rc)
+  // <= delta = 2^-21 (Y + Sh + rc) (a few roundings of magnitude <= 2Y + Sh
+  // each, plus the rounding of the cell to FP32), so | |d32| - |d| | <=
+  // sqrt(3) delta, and the three-term FP32 r^2 is within 2^-21 relative of
+  // |d32|^2.  Hence FP32 r^2 > (rc + 2 delta)^2 (1 + 2^-20) means |d| > rc
+  // and FP32 r^2 < (rc - 2 delta)^2 (1 - 2^-20) means |d| < rc, both by a
+  // margin far above the FP64 rounding of the defining expression; only the
+  // shell in between needs the exact test.
   double Y = 0.0, Sh = 0.0;
   for (int c = 0; c < 3; ++c) {
     double yc = 0.0, sc = 0.0;
@@ -167,9 +171,13 @@ __global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
   double delta = ldexp(Y + Sh + cutoff, -21);
   double b = (cutoff + 2.0 * delta);
   g.pad = 0;
+  for (int k = 0; k < 3; ++k) g.inv_binw[k] = 1.0 / g.binw[k];
   G[s] = g;
   float p2 = (float)(b * b * (1.0 + ldexp(1.0, -20)));
   S[s].prescreen2 = nextafterf(p2, INFINITY);
+  const double bi = fmax(cutoff - 2.0 * delta, 0.0);
+  float q2 = (float)(bi * bi * (1.0 - ldexp(1.0, -20)));
+  S[s].inside2 = fmaxf(nextafterf(q2, 0.0f), 0.0f);
 }
 
 __global__ void k_bin_assign(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
@@ -209,6 +217,58 @@ __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __
     for (int c = 0; c < 3; ++c)
       y[c] = (float)(u4.x * st.A[c] + u4.y * st.A[3 + c] + u4.z * st.A[6 + c]);
     bin_y[slot] = make_float4(y[0], y[1], y[2], __int_as_float((int32_t)a));
+  }
+}
+
+// Per atom: the bins its cutoff sphere can touch, lo[k] .. lo[k]+span[k]-1
+// (periodic axes unwrapped), and its wrapped FP32 position.  Once per atom,
+// so the neighbor kernels need no FP64 set-up.  atom_u is overwritten with
+// {yx, yy, yz, packed (lo, span)} in a second array.
+__global__ void k_ranges(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
+                         const int32_t* __restrict__ struct_of, int64_t N, const GmpD4* __restrict__ atom_u,
+                         int4* __restrict__ atom_rng, float4* __restrict__ atom_y) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int s = struct_of[a];
+    const GmpStruct& st = S[s];
+    const GmpGrid& g = G[s];
+    const GmpD4 u4 = atom_u[a];
+    const double u[3] = {u4.x, u4.y, u4.z};
+    int lo[3], span[3];
+    for (int k = 0; k < 3; ++k) {
+      const double lo_f = (u[k] - st.reach[k] - g.umin[k]) * g.inv_binw[k];
+      const double hi_f = (u[k] + st.reach[k] - g.umin[k]) * g.inv_binw[k];
+      int l0 = (int)floor(lo_f - 1e-7), h0 = (int)floor(hi_f + 1e-7);
+      if (!st.periodic[k]) {
+        l0 = max(l0, 0);
+        h0 = min(h0, g.nb[k] - 1);
+      }
+      lo[k] = l0;
+      span[k] = max(h0 - l0 + 1, 0);
+    }
+    float y[3];
+    for (int c = 0; c < 3; ++c) y[c] = (float)(u[0] * st.A[c] + u[1] * st.A[3 + c] + u[2] * st.A[6 + c]);
+    atom_rng[a] = make_int4(lo[0], lo[1], lo[2], span[0] | (span[1] << 10) | (span[2] << 20));
+    atom_y[a] = make_float4(y[0], y[1], y[2], 0.0f);
+  }
+}
+
+// Orders each bin's atoms by index (the scatter above fills bins in
+// arbitrary order), which makes neighbor enumeration deterministic.
+__global__ void k_bin_sort(int64_t n_bins, const int32_t* __restrict__ bin_start, float4* __restrict__ bin_y) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n_bins;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int b0 = bin_start[b], b1 = bin_start[b + 1];
+    for (int t = b0 + 1; t < b1; ++t) {
+      const float4 v = bin_y[t];
+      const int key = __float_as_int(v.w);
+      int u = t - 1;
+      while (u >= b0 && __float_as_int(bin_y[u].w) > key) {
+        bin_y[u + 1] = bin_y[u];
+        --u;
+      }
+      bin_y[u + 1] = v;
+    }
   }
 }
 
@@ -323,101 +383,115 @@ __device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, int
   return fp64_within(pos, i, j, st, n, rc2);
 }
 
-// Warp per center.  fill = 0: count exact neighbors; fill = 1: collect keys,
-// sort, and write the pair records at offsets[i].
+// Warp per center.  fill = 0: count exact neighbors; fill = 1: write the
+// pair records in enumeration order (cells in a fixed order, atoms in index
+// order within a cell: deterministic); fill = 2: the same, sorted by
+// (neighbor atom, image) first.
 __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
                             const int32_t* __restrict__ struct_of, int64_t N, float cutoff,
                             float rc2hi, float rc2lo, double rc2, const double* __restrict__ pos,
                             const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                            const GmpD4* __restrict__ atom_u, const int32_t* __restrict__ bin_start,
-                            const float4* __restrict__ bin_y, int64_t* __restrict__ counts,
-                            const int64_t* __restrict__ offsets, GmpPair* __restrict__ pairs,
-                            int max_keys, int32_t* __restrict__ maxm, uint32_t* __restrict__ err) {
+                            const int4* __restrict__ atom_rng, const float4* __restrict__ atom_y,
+                            const int32_t* __restrict__ bin_start, const float4* __restrict__ bin_y,
+                            int64_t* __restrict__ counts, const int64_t* __restrict__ offsets,
+                            GmpPair* __restrict__ pairs, int max_keys, int32_t* __restrict__ maxm,
+                            uint32_t* __restrict__ err) {
   extern __shared__ unsigned long long sh_keys[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= N) return;
   unsigned long long* keys = sh_keys + (size_t)wib * max_keys;
-  __shared__ int s_cnt[32];
-  if (lane == 0) s_cnt[wib] = 0;
-  __syncwarp();
 
   const int s = struct_of[i];
   const GmpStruct& st = S[s];
-  const GmpGrid g = G[s];
+  const GmpGrid& g = G[s];
+  int nb[3], per[3];
+  float ahi[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { nb[k] = g.nb[k]; per[k] = st.periodic[k]; }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ahi[k] = st.Ahi[k];
+  const int64_t bin_base = st.bin_base;
+  const float p2 = st.prescreen2, q2 = st.inside2;
   const float4 xhi = atom_xh[i], xli = atom_xl[i];
   int wi[3];
   gmp_unpack_shift(__float_as_int(xli.w), wi);
-  const GmpD4 ui4 = atom_u[i];
-  const double ui[3] = {ui4.x, ui4.y, ui4.z};
-  int lo[3], span[3];
-  for (int k = 0; k < 3; ++k) {
-    double a = (ui[k] - st.reach[k] - g.umin[k]) / g.binw[k];
-    double b = (ui[k] + st.reach[k] - g.umin[k]) / g.binw[k];
-    int l0 = (int)floor(a - 1e-7), h0 = (int)floor(b + 1e-7);
-    if (!st.periodic[k]) {
-      l0 = max(l0, 0);
-      h0 = min(h0, g.nb[k] - 1);
-    }
-    lo[k] = l0;
-    span[k] = max(h0 - l0 + 1, 0);
-  }
-  // wrapped FP32 position of the center
-  float yi[3];
-  for (int c = 0; c < 3; ++c)
-    yi[c] = (float)(ui[0] * st.A[c] + ui[1] * st.A[3 + c] + ui[2] * st.A[6 + c]);
-  const float p2 = st.prescreen2;
+  const int4 rg = atom_rng[i];
+  const int lo[3] = {rg.x, rg.y, rg.z};
+  const int span[3] = {rg.w & 1023, (rg.w >> 10) & 1023, (rg.w >> 20) & 1023};
+  const float4 yi4 = atom_y[i];
+  const float yi[3] = {yi4.x, yi4.y, yi4.z};
   const int total = span[0] * span[1] * span[2];
-  int count = 0;
-  for (int cidx = lane; cidx < total; cidx += 32) {
-    int c0 = cidx % span[0];
-    int c1 = (cidx / span[0]) % span[1];
-    int c2 = cidx / (span[0] * span[1]);
-    int bb[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
-    int m[3], bw[3];
-    for (int k = 0; k < 3; ++k) {
-      if (st.periodic[k]) {
-        m[k] = floor_div(bb[k], g.nb[k]);
-        bw[k] = bb[k] - m[k] * g.nb[k];
-      } else {
-        m[k] = 0;
-        bw[k] = bb[k];
+  int count = 0;   // per lane (count pass) / per warp (fill passes)
+  for (int r0 = 0; r0 < total; r0 += 32) {
+    const int cidx = r0 + lane;
+    int m[3] = {0, 0, 0};
+    int b0 = 0, b1 = 0;
+    float sh[3] = {0.0f, 0.0f, 0.0f};
+    if (cidx < total) {
+      const int c0 = cidx % span[0];
+      const int c1 = (cidx / span[0]) % span[1];
+      const int c2 = cidx / (span[0] * span[1]);
+      const int bb[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
+      int bw[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (per[k]) {
+          m[k] = floor_div(bb[k], nb[k]);
+          bw[k] = bb[k] - m[k] * nb[k];
+        } else {
+          bw[k] = bb[k];
+        }
       }
+      const int64_t bin = bin_base + bw[0] + (int64_t)nb[0] * (bw[1] + (int64_t)nb[1] * bw[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        sh[c] = (float)m[0] * ahi[c] + (float)m[1] * ahi[3 + c] + (float)m[2] * ahi[6 + c];
+      b0 = bin_start[bin];
+      b1 = bin_start[bin + 1];
     }
-    const int64_t bin = st.bin_base + bw[0] + (int64_t)g.nb[0] * (bw[1] + (int64_t)g.nb[1] * bw[2]);
-    float sh[3];
-    for (int c = 0; c < 3; ++c)
-      sh[c] = (float)m[0] * st.Ahi[c] + (float)m[1] * st.Ahi[3 + c] + (float)m[2] * st.Ahi[6 + c];
-    const int b0 = bin_start[bin], b1 = bin_start[bin + 1];
-    for (int slot = b0; slot < b1; ++slot) {
-      const float4 yj = bin_y[slot];
-      const float dx = (yj.x - yi[0]) + sh[0];
-      const float dy = (yj.y - yi[1]) + sh[1];
-      const float dz = (yj.z - yi[2]) + sh[2];
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 > p2) continue;
-      const int64_t j = __float_as_int(yj.w);
-      const float4 xhj = atom_xh[j], xlj = atom_xl[j];
-      int wj[3];
-      gmp_unpack_shift(__float_as_int(xlj.w), wj);
-      int n[3] = {m[0] + wi[0] - wj[0], m[1] + wi[1] - wj[1], m[2] + wi[2] - wj[2]};
-      if (!exact_accept(pos, i, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff)) continue;
-      if (abs(n[0]) >= 512 || abs(n[1]) >= 512 || abs(n[2]) >= 512) {
-        atomicOr(err, GMP_DEV_SHIFT_RANGE);  // reported after the count pass
-        continue;
+    // lockstep over the slots of this round's cells
+    const int len = __reduce_max_sync(0xffffffffu, b1 - b0);
+    for (int t = 0; t < len; ++t) {
+      const int slot = b0 + t;
+      bool acc = false;
+      unsigned long long key = 0;
+      if (slot < b1) {
+        const float4 yj = bin_y[slot];
+        const float dx = (yj.x - yi[0]) + sh[0];
+        const float dy = (yj.y - yi[1]) + sh[1];
+        const float dz = (yj.z - yi[2]) + sh[2];
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 <= p2) {
+          const int64_t j = __float_as_int(yj.w);
+          int wj[3];
+          gmp_unpack_shift(__float_as_int(__ldg(&atom_xl[j].w)), wj);
+          int n[3] = {m[0] + wi[0] - wj[0], m[1] + wi[1] - wj[1], m[2] + wi[2] - wj[2]};
+          acc = true;
+          if (r2 >= q2) {  // boundary shell: exact decision
+            const float4 xhj = atom_xh[j], xlj = atom_xl[j];
+            acc = exact_accept(pos, i, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff);
+          }
+          if (acc && (abs(n[0]) >= 512 || abs(n[1]) >= 512 || abs(n[2]) >= 512)) {
+            atomicOr(err, GMP_DEV_SHIFT_RANGE);  // reported after the count pass
+            acc = false;
+          }
+          if (acc) key = sort_key(j, n);
+        }
       }
-      if (fill) {
-        int slot_k = atomicAdd(&s_cnt[wib], 1);
-        if (slot_k < max_keys)
-          keys[slot_k] = sort_key(j, n);
+      if (!fill) {
+        count += acc ? 1 : 0;
+      } else {
+        const unsigned mask = __ballot_sync(0xffffffffu, acc);
+        const int slot_k = count + __popc(mask & ((1u << lane) - 1u));
+        if (acc && slot_k < max_keys) keys[slot_k] = key;
+        count += __popc(mask);
       }
-      ++count;
     }
   }
-  // warp total
-  for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
   if (!fill) {
+    for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if (lane == 0) {
       counts[i] = count;
       atomicMax(maxm, count);
@@ -425,34 +499,36 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
     return;
   }
   __syncwarp();
-  const int M = s_cnt[wib];
+  const int M = count;
   const int64_t base = offsets[i];
   if (M != (int)(offsets[i + 1] - base) || M > max_keys) {
     if (lane == 0) atomicOr(err, GMP_DEV_TOO_MANY_NEIGHBORS);
     return;
   }
-  // bitonic sort of the M keys (padded to a power of two with ~0)
-  int P2 = 1;
-  while (P2 < M) P2 <<= 1;
-  for (int t = M + lane; t < P2; t += 32) keys[t] = ~0ull;
-  __syncwarp();
-  for (int k = 2; k <= P2; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int t = lane; t < P2; t += 32) {
-        int partner = t ^ jj;
-        if (partner > t) {
-          unsigned long long a = keys[t], b = keys[partner];
-          bool up = (t & k) == 0;
-          if ((a > b) == up) {
-            keys[t] = b;
-            keys[partner] = a;
+  if (fill == 2) {
+    // bitonic sort of the M keys (padded to a power of two with ~0)
+    int P2 = 1;
+    while (P2 < M) P2 <<= 1;
+    for (int t = M + lane; t < P2; t += 32) keys[t] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= P2; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int t = lane; t < P2; t += 32) {
+          int partner = t ^ jj;
+          if (partner > t) {
+            unsigned long long a = keys[t], b = keys[partner];
+            bool up = (t & k) == 0;
+            if ((a > b) == up) {
+              keys[t] = b;
+              keys[partner] = a;
+            }
           }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
-  // records (recompute the same double-float displacement)
+  // records: the double-float displacement, rounded to FP32
   for (int t = lane; t < M; t += 32) {
     const unsigned long long key = keys[t];
     const int64_t j = (int64_t)(key >> 30);
@@ -539,12 +615,9 @@ cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struc
 cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
                             const int32_t* d_struct_of, int64_t N, int64_t n_bins,
                             const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
-                            int32_t* bin_cursor, int32_t* bin_atoms, float4* bin_y,
-                            const float4* atom_xh, const float4* atom_xl, const GmpD4* atom_u,
-                            void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
+                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y,
+                            const GmpD4* atom_u, void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
                             int sm_count, int64_t* launches) {
-  (void)atom_xh;
-  (void)atom_xl;
   (void)scan_tmp_bytes;
   cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * n_bins, stream);
   if (e != cudaSuccess) return e;
@@ -558,13 +631,18 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
   k_bin_scatter<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, atom_bin,
                                                                 bin_start, bin_cursor, atom_u, bin_y);
   ++*launches;
+  k_bin_sort<<<grid_for(n_bins, 256, sm_count), 256, 0, stream>>>(n_bins, bin_start, bin_y);
+  ++*launches;
+  k_ranges<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, d_struct_of, N, atom_u, atom_rng,
+                                                           atom_y);
+  ++*launches;
   return cudaGetLastError();
 }
 
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const int32_t* d_struct_of, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const GmpD4* atom_u, const int32_t* bin_start,
+                                     const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
                                      cudaStream_t stream, int sm_count, int64_t* launches) {
@@ -586,7 +664,7 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
   const unsigned blocks = (unsigned)((N + warps - 1) / warps);
   k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, d_struct_of, N,
                                                     (float)cutoff, rc2hi, rc2lo, rc2, pos, atom_xh,
-                                                    atom_xl, atom_u, bin_start, bin_y, counts,
+                                                    atom_xl, atom_rng, atom_y, bin_start, bin_y, counts,
                                                     offsets, pairs, max_keys, d_maxm, d_err);
   ++*launches;
   return cudaGetLastError();

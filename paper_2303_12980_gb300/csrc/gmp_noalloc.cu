@@ -41,12 +41,14 @@ struct Layout {
   static constexpr size_t bcursor = bcount + align256(4 * kMaxBins);
   static constexpr size_t bstart = bcursor + align256(4 * kMaxBins);
   static constexpr size_t by = bstart + align256(4 * (kMaxBins + 1));
-  static constexpr size_t scan = by + align256(16 * kNoAllocMaxAtoms);
+  static constexpr size_t rng = by + align256(16 * kNoAllocMaxAtoms);
+  static constexpr size_t ay = rng + align256(16 * kNoAllocMaxAtoms);
+  static constexpr size_t scan = ay + align256(16 * kNoAllocMaxAtoms);
   static constexpr size_t scan_bytes = 16 * 1024;
   static constexpr size_t total = scan + scan_bytes;
 };
 
-// The scratch itself (about 4 MB).  Host code must not use this name as an
+// The scratch itself (about 5 MB).  Host code must not use this name as an
 // address: it is only a host-side stand-in; the device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[Layout::total];
@@ -162,6 +164,8 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
   int32_t* d_bcursor = reinterpret_cast<int32_t*>(base + Layout::bcursor);
   int32_t* d_bstart = reinterpret_cast<int32_t*>(base + Layout::bstart);
   float4* d_by = reinterpret_cast<float4*>(base + Layout::by);
+  int4* d_rng = reinterpret_cast<int4*>(base + Layout::rng);
+  float4* d_ay = reinterpret_cast<float4*>(base + Layout::ay);
   void* d_scan = base + Layout::scan;
   if (gmp_scan_tmp_bytes(n_bins) > Layout::scan_bytes) return report(GMP_ERR_CAPACITY, "scan workspace too small");
 
@@ -175,11 +179,12 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
     e = gmp_launch_neighbors_prepare(d_st, 1, d_struct_of, n_atoms, cutoff, pos, d_species, 1, d_grid, d_xh, d_xl,
                                      d_u, d_bin, d_bbox, d_err, st, sm_count, &launches);
   if (e == cudaSuccess)
-    e = gmp_launch_bins(d_st, d_grid, d_struct_of, n_atoms, n_bins, d_bin, d_bcount, d_bstart, d_bcursor, nullptr,
-                        d_by, d_xh, d_xl, d_u, d_scan, Layout::scan_bytes, st, sm_count, &launches);
+    e = gmp_launch_bins(d_st, d_grid, d_struct_of, n_atoms, n_bins, d_bin, d_bcount, d_bstart, d_bcursor, d_rng,
+                        d_ay, d_by, d_u, d_scan, Layout::scan_bytes, st, sm_count, &launches);
   if (e == cudaSuccess)
-    e = gmp_launch_neighbor_pass(0, d_st, d_grid, d_struct_of, n_atoms, cutoff, pos, d_xh, d_xl, d_u, d_bstart, d_by,
-                                 counts, nullptr, nullptr, 0, d_maxm, d_err, st, sm_count, &launches);
+    e = gmp_launch_neighbor_pass(0, d_st, d_grid, d_struct_of, n_atoms, cutoff, pos, d_xh, d_xl, d_rng, d_ay,
+                                 d_bstart, d_by, counts, nullptr, nullptr, 0, d_maxm, d_err, st, sm_count,
+                                 &launches);
   uint32_t w = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d_err, sizeof(w), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
