@@ -105,9 +105,17 @@ def work_model(w, pairs: int):
     counts = np.bincount(w.species, minlength=w.n_elements)
     K = float(np.dot(counts, w.n_gauss) / counts.sum())
     fma_fwd = ns * K * (1 + n_l) + ns * C + 2 * C
-    fma = 3.5 * fma_fwd * pairs
     ex2 = 2 * ns * K * pairs
-    return {"fma_per_pair_fwd": fma_fwd, "flop_step": 2.0 * fma, "ex2_step": ex2}
+    return {"fma_per_pair_fwd": fma_fwd, "flop_fwd": 2.0 * fma_fwd * pairs,
+            "flop_bwd": 2.0 * 2.5 * fma_fwd * pairs, "flop_step": 2.0 * 3.5 * fma_fwd * pairs, "ex2_step": ex2}
+
+
+# DRAM bytes per neighbor pair of the forward and backward kernels, from one
+# ncu capture of fcc_slab32k (same instantiation as the default workload;
+# dram__bytes_read.sum + dram__bytes_write.sum over 4.64 M pairs), scaled by
+# the pairs of the run.  Update together with profiles/ when the kernels change.
+TRAFFIC_PER_PAIR = {"forward": (147.111424e6 + 79.203072e6) / 4.6425e6,
+                    "backward": (265.485056e6 + 4.201984e6) / 4.6425e6}
 
 
 # ------------------------------------------------------------------ our arm
@@ -172,13 +180,19 @@ def run_ours(args, rank, world, local_rank):
     ms_max = float(tmax.item())
     value = world * args.steps * N * F_ / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (fused forward + VJP), timed live by
-    # CUDA events on the launching stream inside the library
-    comp_ms, comp_n = prof["compute"]
-    nbr_ms, nbr_n = prof["neighbors"]
+    # roofline of the dominant kernel, timed live by CUDA events on the
+    # launching stream inside the library (one forward and one backward
+    # launch per step for a <= 16-sigma probe set)
+    stage = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sm_count * 128 * 2 * 2070e6 / 1e12   # FP32 FMA lanes x 2 FLOP x max SM clock
-    achieved = wm["flop_step"] / (comp_ms / comp_n * 1e-3) / 1e12 if comp_n else None
+    kern = {"forward": {"ms": stage["features"], "algorithmic_flop": wm["flop_fwd"]},
+            "backward": {"ms": stage["backward"], "algorithmic_flop": wm["flop_bwd"]}}
+    for v in kern.values():
+        v["tflops"] = v["algorithmic_flop"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] else None
+        v["frac"] = v["tflops"] / peak if v["tflops"] else None
+    dom = max(kern, key=lambda k: kern[k]["ms"] or 0.0)
+    achieved = kern[dom]["tflops"]
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -213,13 +227,12 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "roofline": {"bound": "alu", "kernel": "k_vjp (fused forward + VJP)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None,
+                     "traffic": TRAFFIC_PER_PAIR.get(dom, 0) * pairs if dom in TRAFFIC_PER_PAIR else None,
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
-                     "algorithmic_flop_per_step": wm["flop_step"], "ex2_per_step": wm["ex2_step"],
-                     "kernel_ms": comp_ms / comp_n if comp_n else None,
-                     "neighbor_stage_ms": nbr_ms / nbr_n if nbr_n else None},
+                     "kernels": kern, "ex2_per_step": wm["ex2_step"],
+                     "stage_ms": stage},
         "wall_s_timed": wall,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -114,7 +114,7 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t *atom
  * If the total nnz exceeds `cap`, nothing but *nnz_out is written and
  * GMP_ERR_CAPACITY is returned; call again with cap >= *nnz_out.
  * nnz_out is a host pointer; this call synchronises `stream`. */
-gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
                                   const double *pos, const double *cell, const uint8_t *pbc,
                                   const int32_t *species, float *features, int64_t *jac_off,
                                   int32_t *jac_j, float *jac, int64_t cap, int64_t *nnz_out,
@@ -125,7 +125,7 @@ gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t 
  * self pair included, decided in FP64 exactly as that expression reads
  * (left to right, no FMA).  nbr_off [N+1] int64; nbr_j [cap] int32;
  * nbr_shift [cap, 3] int32 (n1, n2, n3); each row ordered by (j, n1, n2, n3).
- * Capacity semantics as in gmp_featurize_jacobian. */
+ * Capacity semantics as in gmp_featurize_grad. */
 gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
                          const double *pos, const double *cell, const uint8_t *pbc,
                          const int32_t *species, int64_t *nbr_off, int32_t *nbr_j,
@@ -169,10 +169,12 @@ int64_t gmp_kernel_launches(gmp_handle h);
 /* Stage timing (diagnostics, not part of the method).  With enable != 0 the
  * featurize calls record CUDA events on the caller's stream around
  *   stage 0: neighbor search (binning, count, fill),
- *   stage 1: the feature / VJP / Jacobian compute kernels;
+ *   stage 1: the feature kernel (forward, or Jacobian),
+ *   stage 2: the backward kernel of gmp_featurize_vjp,
+ *   stage 3: FP64 refinement of ill-conditioned features and output copies;
  * gmp_profile_read synchronises those events and writes, per stage, the
  * summed milliseconds and the number of stage executions since the last
- * read (arrays of length n_stages <= 2), then clears the counters. */
+ * read (arrays of length n_stages <= 4), then clears the counters. */
 gmp_status gmp_profile(gmp_handle h, int enable);
 gmp_status gmp_profile_read(gmp_handle h, double *ms, int64_t *count, int n_stages);
 

@@ -27,7 +27,7 @@ GMP_OK = 0
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp",
-           "gmp_featurize_jacobian", "gmp_neighbors", "gmp_sync", "gmp_profile", "gmp_profile_read",
+           "gmp_featurize_grad", "gmp_neighbors", "gmp_sync", "gmp_profile", "gmp_profile_read",
            "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
 
 _lib = None
@@ -71,7 +71,7 @@ def load_library(path: str = LIB_PATH):
         common = [vp, i32, vp, vp, vp, vp, vp]
         L.gmp_featurize.argtypes = common + [vp, vp]
         L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
-        L.gmp_featurize_jacobian.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_featurize_grad.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_sync.argtypes = [vp, vp, C.c_double]
         L.gmp_profile.argtypes = [vp, C.c_int]
@@ -237,7 +237,7 @@ class GMPFeaturizer:
                                               _ptr(gp), _stream_ptr(stream, on_dev)))
         return feat, gp
 
-    def featurize_jacobian(self, pos, species, atom_off, cell, pbc, stream=None):
+    def featurize_grad(self, pos, species, atom_off, cell, pbc, stream=None):
         """(features [N,F], jac_off [N+1] int64, jac_j [nnz] int32, jac [nnz,F,3] float32):
         jac[r] = d features[i] / d pos[jac_j[r]] for r in jac_off[i]:jac_off[i+1]."""
         torch = _torch()
@@ -247,7 +247,7 @@ class GMPFeaturizer:
         feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos)
         joff = self._alloc((N + 1,), torch.int64, on_dev, pos)
         nnz = C.c_int64()
-        st = self._L.gmp_featurize_jacobian(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+        st = self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
                                             pbc.ctypes.data, _ptr(species), _ptr(feat), _ptr(joff), None, None,
                                             0, C.byref(nnz), _stream_ptr(stream, on_dev))
         if st not in (GMP_OK, 4):
@@ -255,7 +255,7 @@ class GMPFeaturizer:
         cap = int(nnz.value)
         jj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
         jac = self._alloc((max(cap, 1), self.num_features, 3), torch.float32, on_dev, pos)
-        self._check(self._L.gmp_featurize_jacobian(self._h, off.size - 1, off.ctypes.data, _ptr(pos),
+        self._check(self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos),
                                                    cell.ctypes.data, pbc.ctypes.data, _ptr(species), _ptr(feat),
                                                    _ptr(joff), _ptr(jj), _ptr(jac), cap, C.byref(nnz),
                                                    _stream_ptr(stream, on_dev)))
@@ -287,11 +287,13 @@ class GMPFeaturizer:
         self._check(self._L.gmp_profile(self._h, int(enable)))
 
     def profile_read(self):
-        """{'neighbors': (ms, count), 'compute': (ms, count)} since the last read."""
-        ms = (C.c_double * 2)()
-        cnt = (C.c_int64 * 2)()
-        self._check(self._L.gmp_profile_read(self._h, ms, cnt, 2))
-        return {"neighbors": (ms[0], cnt[0]), "compute": (ms[1], cnt[1])}
+        """{stage: (ms, count)} since the last read, stages 'neighbors',
+        'features' (forward / Jacobian kernel), 'backward', 'refine'."""
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int64 * 4)()
+        self._check(self._L.gmp_profile_read(self._h, ms, cnt, 4))
+        names = ("neighbors", "features", "backward", "refine")
+        return {n: (ms[k], cnt[k]) for k, n in enumerate(names)}
 
     def sync(self, stream=None, timeout_s: float = 0.0):
         torch = _torch()

@@ -87,8 +87,9 @@ struct gmp_ctx {
   cudaEvent_t ev = nullptr;
   // stage timing
   bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev[2];  // start/stop pairs per stage
-  size_t prof_used[2] = {0, 0};
+  static constexpr int kStages = 4;     // neighbors, features kernel, backward kernel, refine/finish
+  std::vector<cudaEvent_t> prof_ev[kStages];  // start/stop pairs per stage
+  size_t prof_used[kStages] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -626,8 +627,10 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
     GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_FORWARD, h->passes[g].NS, K, st, h->sm_count, &h->launches),
            "forward");
   }
-  if ((r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 1, false, st), "profile");
+  GMP_CK(prof_mark(h, 3, true, st), "profile");
+  if ((r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 3, false, st), "profile");
   if (io.host) {
     GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
     GMP_CK(cudaStreamSynchronize(st), "sync");
@@ -664,7 +667,6 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
   GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
   if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 1, true, st), "profile");
   for (size_t g = 0; g < h->passes.size(); ++g) {
     const PassData& pd = h->passes[g];
     // forward kernel (features + moments), then the backward kernel reading
@@ -679,16 +681,21 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     gmpk::KParams K = base_params(h, pd, (int)g, N);
     K.features = fout;
     K.mu_out = h->mu.as<float>();
+    GMP_CK(prof_mark(h, 1, true, st), "profile");
     GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, st, h->sm_count, &h->launches), "forward");
+    GMP_CK(prof_mark(h, 1, false, st), "profile");
     K.features = nullptr;
     K.flags = nullptr;
     K.grad_feat = gf;
     K.grad_acc = h->grad_acc.as<double>();
+    GMP_CK(prof_mark(h, 2, true, st), "profile");
     GMP_CK(launch_compute(pd.L, GMP_KIND_BACKWARD, pd.NS, K, st, h->sm_count, &h->launches), "backward");
+    GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
+  GMP_CK(prof_mark(h, 3, true, st), "profile");
   if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 1, false, st), "profile");
   GMP_CK(gmp_launch_grad_finish(N, h->grad_acc.as<double>(), gp, st, &h->launches), "grad finish");
+  GMP_CK(prof_mark(h, 3, false, st), "profile");
   if (io.host) {
     if (features)
       GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
@@ -698,7 +705,7 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
   return GMP_OK;
 }
 
-gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
                                   const double* cell, const uint8_t* pbc, const int32_t* species, float* features,
                                   int64_t* jac_off, int32_t* jac_j, float* jac, int64_t cap, int64_t* nnz_out,
                                   void* stream) {
@@ -750,8 +757,10 @@ gmp_status gmp_featurize_jacobian(gmp_handle h, int32_t n_struct, const int64_t*
     GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_JACOBIAN, h->passes[g].NS, K, st, h->sm_count, &h->launches),
            "jacobian");
   }
-  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 1, false, st), "profile");
+  GMP_CK(prof_mark(h, 3, true, st), "profile");
+  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  GMP_CK(prof_mark(h, 3, false, st), "profile");
   const cudaMemcpyKind k_off = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (N + 1), k_off, st), "copy jac_off");
   if (io.host) {
@@ -839,12 +848,12 @@ int64_t gmp_kernel_launches(gmp_handle h) { return h ? h->launches : 0; }
 gmp_status gmp_profile(gmp_handle h, int enable) {
   if (!h) return GMP_ERR_INVALID_ARG;
   h->profiling = enable != 0;
-  h->prof_used[0] = h->prof_used[1] = 0;
+  for (int s = 0; s < gmp_ctx::kStages; ++s) h->prof_used[s] = 0;
   return GMP_OK;
 }
 
 gmp_status gmp_profile_read(gmp_handle h, double* ms, int64_t* count, int n_stages) {
-  if (!h || !ms || !count || n_stages < 1 || n_stages > 2) return GMP_ERR_INVALID_ARG;
+  if (!h || !ms || !count || n_stages < 1 || n_stages > gmp_ctx::kStages) return GMP_ERR_INVALID_ARG;
   for (int s = 0; s < n_stages; ++s) {
     double tot = 0.0;
     for (size_t u = 0; u + 1 < h->prof_used[s] + 1 && u < h->prof_used[s]; u += 2) {

@@ -254,11 +254,19 @@ def fcc_slab262k(seed: int = 1004, reps=(32, 32, 64)) -> Workload:
                    [0, 1, 2, 3, 4, 5, 6], np.geomspace(0.05, 1.5, 16), 8.0)
 
 
+def fcc_slab32k(seed: int = 1004) -> Workload:
+    """The alloy slab at 1/8 size (16x16x32 conventional cells, 32,768
+    atoms), same probes; the small case for kernel profiling."""
+    w = fcc_slab262k(seed=seed, reps=(16, 16, 32))
+    return w.replace(name="fcc_slab32k")
+
+
 WORKLOADS = {
     "random64_box": random64_box,
     "fcc4096": fcc4096,
     "batched10k": batched10k,
     "fcc_slab262k": fcc_slab262k,
+    "fcc_slab32k": fcc_slab32k,
 }
 
 

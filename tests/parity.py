@@ -23,7 +23,11 @@ _report = {}
 
 def feature_errors(f_gpu, f_ref, f_abs, tau=FEAT_TAU):
     f_gpu = np.asarray(f_gpu, np.float64)
-    err = np.abs(f_gpu - f_ref) / np.maximum(np.abs(f_ref), tau * f_abs)
+    num = np.abs(f_gpu - f_ref)
+    den = np.maximum(np.abs(f_ref), tau * f_abs)
+    # an exactly zero feature with a zero scale (e.g. l >= 1 of an isolated
+    # atom) must come out exactly zero
+    err = np.where(num == 0.0, 0.0, num / np.where(den > 0.0, den, 1e-300))
     return err.max(axis=0)
 
 
@@ -32,7 +36,7 @@ def grad_errors(g_gpu, g_ref, g_abs, tau=GRAD_TAU):
     g_gpu = np.asarray(g_gpu, np.float64)
     num = np.linalg.norm(g_gpu - g_ref, axis=-1)
     den = np.maximum(np.linalg.norm(g_ref, axis=-1), tau * g_abs)
-    return num / den
+    return np.where(num == 0.0, 0.0, num / np.where(den > 0.0, den, 1e-300))
 
 
 def record(name, **vals):

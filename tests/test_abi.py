@@ -14,7 +14,7 @@ def _declared():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for n in ("gmp_create", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_jacobian",
+    for n in ("gmp_create", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_grad",
               "gmp_neighbors", "gmp_sync", "gmp_last_error", "gmp_destroy"):
         assert n in names
 

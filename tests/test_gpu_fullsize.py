@@ -1,0 +1,106 @@
+"""Full-size workloads on the GPU, checked on sampled outputs the FP64 oracle
+can compute one by one: the 262,144-atom FCC alloy slab (orders 0-6, 16
+sigmas) and the 10,000-structure batch of periodic boxes and clusters."""
+import numpy as np
+import pytest
+
+from paper_2303_12980_gb300 import synth
+
+from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors, record
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def _w(name):
+    if name not in _cache:
+        _cache[name] = synth.workload(name)
+    return _cache[name]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    from paper_2303_12980_gb300 import build
+    build.build()
+    return t
+
+
+@pytest.mark.parametrize("name,n_centers,n_atoms", [("fcc_slab262k", 192, 6), ("batched10k", 384, 12)])
+def test_full_size_sampled(torch, oracle_mod, name, n_centers, n_atoms):
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    w = _w(name)
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=2024)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    centers = synth.subset_centers(w.n_atoms, n_centers, seed=31)
+    ref, fabs = oracle_mod.features(w, centers, want_abs=True)
+    ferr = feature_errors(feat.cpu().numpy()[centers], ref, fabs)
+    atoms = synth.subset_centers(w.n_atoms, n_atoms, seed=32)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    record(f"fullsize/{name}", features_max_rel_err=ferr.max(), vjp_max_rel_err=gerr.max(),
+           centers=n_centers, atoms=n_atoms)
+    assert ferr.max() <= FEAT_TOL, ferr.max()
+    assert gerr.max() <= GRAD_TOL, gerr.max()
+    # neighbor counts of the sampled centers equal the oracle's
+    noff, _, _ = F.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+    cnt = (noff[1:] - noff[:-1]).cpu().numpy()[centers]
+    ooff, _, _, _ = oracle_mod.neighbors(w, centers)
+    assert np.array_equal(cnt, np.diff(ooff))
+
+
+def test_edge_cases(torch, oracle_mod):
+    """Empty structure in a batch, a single isolated atom, a structure with
+    a triclinic cell and mixed periodicity, positions far outside the cell."""
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    base = synth.workload("random64_box")
+    rng = np.random.default_rng(5)
+    tri = np.array([[7.0, 0.0, 0.0], [2.5, 6.5, 0.0], [1.0, 1.5, 8.0]])
+    p_tri = rng.uniform(0, 1, (20, 3)) @ tri + rng.integers(-3, 4, (20, 3)) @ tri  # outside the cell
+    p_one = np.array([[0.3, -0.2, 0.1]])
+    pos = np.concatenate([base.positions[:10], p_one, p_tri])
+    species = np.concatenate([base.species[:10], [1], rng.integers(0, 2, 20)]).astype(np.int32)
+    atom_off = np.array([0, 10, 10, 11, 31], np.int64)          # structure 1 is empty
+    cells = np.stack([base.cells[0], np.zeros((3, 3)), np.zeros((3, 3)), tri])
+    pbc = np.array([[1, 1, 1], [0, 0, 0], [0, 0, 0], [1, 0, 1]], np.uint8)
+    w = base.replace(positions=pos, species=species, atom_off=atom_off, cells=cells, pbc=pbc,
+                     orders=[-1, 0, 1, 2, 3])
+    F = GMPFeaturizer.from_workload(w)
+    f = F.featurize(torch.from_numpy(pos).cuda(), torch.from_numpy(species).cuda(), atom_off, cells, pbc)
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    err = feature_errors(f.cpu().numpy(), ref, fabs)
+    assert err.max() <= FEAT_TOL, err.max()
+    noff, nj, nsh = F.neighbors(torch.from_numpy(pos).cuda(), torch.from_numpy(species).cuda(),
+                                atom_off, cells, pbc)
+    ooff, oj, osh, _ = oracle_mod.neighbors(w)
+    assert np.array_equal(noff.cpu().numpy(), ooff)
+    assert np.array_equal(nj.cpu().numpy(), oj)
+    assert np.array_equal(nsh.cpu().numpy(), osh)
+
+
+def test_invalid_inputs_are_reported(torch):
+    from paper_2303_12980_gb300.binding import GMPError, GMPFeaturizer
+    w = synth.workload("random64_box")
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    bad_sp = torch.from_numpy(w.species).cuda().clone()
+    bad_sp[3] = 7  # only 2 elements
+    with pytest.raises(GMPError, match="species"):
+        F.featurize(pos, bad_sp, w.atom_off, w.cells, w.pbc)
+    with pytest.raises(GMPError, match="singular"):
+        F.featurize(pos, torch.from_numpy(w.species).cuda(), w.atom_off, np.zeros((1, 3, 3)), w.pbc)
+    nan_pos = pos.clone()
+    nan_pos[5, 1] = float("nan")
+    with pytest.raises(GMPError, match="non-finite"):
+        F.featurize(nan_pos, torch.from_numpy(w.species).cuda(), w.atom_off, w.cells, w.pbc)
+    # the handle stays usable after reported errors
+    f = F.featurize(pos, torch.from_numpy(w.species).cuda(), w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(f).all()

@@ -130,7 +130,7 @@ def test_jacobian_parity(torch, oracle_mod, name, n_centers):
     w = wl(name)
     pos, sp = _dev(torch, w)
     F = _featurizer(w)
-    feat, joff, jj, jac = F.featurize_jacobian(pos, sp, w.atom_off, w.cells, w.pbc)
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
     torch.cuda.synchronize()
     joff, jj, jac = joff.cpu().numpy(), jj.cpu().numpy(), jac.cpu().numpy()
     centers = synth.subset_centers(w.n_atoms, n_centers, seed=9)
