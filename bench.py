@@ -122,7 +122,7 @@ TRAFFIC_PER_PAIR = {"forward": (147.111424e6 + 79.203072e6) / 4.6425e6,
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
-    from paper_2303_12980_gb300 import build as B, synth
+    from paper_2303_12980_gb300 import build as B, dist_util, synth
     B.build()
     from paper_2303_12980_gb300.binding import GMPFeaturizer
 
@@ -174,11 +174,8 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * args.steps * N * F_ / (ms_max * 1e-3)
+    ms_max, units = dist_util.reduce_timing(ms, args.steps * N * F_, device=dev)
+    value = units / (ms_max * 1e-3)
 
     # roofline of the dominant kernel, timed live by CUDA events on the
     # launching stream inside the library (one forward and one backward
@@ -208,10 +205,8 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(ke):
             Fz.featurize_vjp(pos_h, sp_h, w.atom_off, w.cells, w.pbc, g_h, out=(feat_h, gp_h))
         te = (time.perf_counter() - t0) / ke
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * N * F_ / float(tt.item()), "unit": UNIT,
+        te_max, e_units = dist_util.reduce_timing(te * 1e3, N * F_, device=dev)
+        e2e = {"value": e_units / (te_max * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(N * 3 * 8 + N * 4 + N * F_ * 4),
                "d2h_bytes_per_step": int(N * F_ * 4 + N * 3 * 4)}
 
