@@ -142,6 +142,8 @@ def run_ours(args, rank, world, local_rank):
     def step():
         Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
 
+    tuning = Fz.tune(pos, sp, w.atom_off, w.cells, w.pbc, reps=2) if not args.no_tune else None
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -229,11 +231,60 @@ def run_ours(args, rank, world, local_rank):
                      "kernels": kern, "ex2_per_step": wm["ex2_step"],
                      "stage_ms": stage},
         "wall_s_timed": wall,
+        "tuning": tuning,
     }
+    if rank == 0 and args.batched:
+        out["batched"] = batched_comparison(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], acc = cpu_baseline(w, feat, gp, g_np, budget_s=args.cpu_budget)
         out["accuracy"] = acc
     return out
+
+
+def batched_comparison(args):
+    """10,000 uneven structures (batched10k, features + VJP): one batched
+    call, its CUDA-graph replay, and the plain one-structure-per-call loop,
+    same kernels and accuracy."""
+    import torch
+    from paper_2303_12980_gb300 import synth
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    w = synth.workload("batched10k")
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(w.positions).to(dev)
+    sp = torch.from_numpy(w.species).to(dev)
+    g = torch.from_numpy(synth.upstream_gradient(w.n_atoms, w.n_features, seed=7)).to(dev)
+    feat = torch.empty((w.n_atoms, w.n_features), device=dev)
+    gp = torch.empty((w.n_atoms, 3), device=dev)
+    units = w.n_atoms * w.n_features
+    s = torch.cuda.Stream()
+    res = {"workload": "batched10k", "structures": w.n_struct, "atoms": w.n_atoms}
+    with torch.cuda.stream(s):
+        Fz = GMPFeaturizer.from_workload(w)
+        res["tuning"] = Fz.tune(pos, sp, w.atom_off, w.cells, w.pbc, reps=2)
+        for mode in ("eager", "graph"):
+            Fz.set_graph(mode == "graph")
+            for _ in range(3):
+                Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
+            s.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
+            s.synchronize()
+            dt = (time.perf_counter() - t0) / 5
+            res[mode] = {"ms": dt * 1e3, "value": units / dt}
+        Fz.set_graph(False)
+        off = w.atom_off
+        t0 = time.perf_counter()
+        for k in range(w.n_struct):
+            a, b = int(off[k]), int(off[k + 1])
+            Fz.featurize_vjp(pos[a:b], sp[a:b], np.array([0, b - a]), w.cells[k:k + 1], w.pbc[k:k + 1],
+                             g[a:b], out=(feat[a:b], gp[a:b]))
+        s.synchronize()
+        dt = time.perf_counter() - t0
+        res["per_structure"] = {"ms": dt * 1e3, "value": units / dt,
+                                "note": "one gmp_featurize_vjp call per structure (plain path)"}
+    res["unit"] = UNIT
+    return res
 
 
 def _oracle_sample(w, centers):
@@ -313,6 +364,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="add the 10,000-structure batched / graph / per-structure comparison")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     args = ap.parse_args()
     if args.warmup < 3:

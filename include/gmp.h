@@ -156,6 +156,38 @@ gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double *pos, const
                                        const uint8_t *pbc, double cutoff, int64_t *counts,
                                        void *stream);
 
+/* CUDA-graph mode (default off).  When on, a gmp_featurize /
+ * gmp_featurize_vjp call with device buffers on a non-default stream first
+ * runs eagerly, then captures its whole device sequence (binning, neighbor
+ * passes, compute kernels, refinement) into a CUDA graph whose neighbor
+ * capacities carry 12.5% headroom over the eager run; the next calls with
+ * the same buffers, stream and batch description replay the graph and
+ * synchronise the stream once.  A batch that outgrows the captured
+ * capacities is detected on the device; that call then re-runs eagerly and
+ * recaptures, so results are always complete.  Any other call on the handle
+ * invalidates the graph. */
+gmp_status gmp_set_graph(gmp_handle h, int enable);
+
+/* Autotuner (not part of the method): builds the neighbor lists of the given
+ * batch, then times on it (CUDA events, `reps` launches after a warm-up)
+ * the candidate launch shapes of each compute kernel -- forward tile of 16
+ * or 32 pairs x 4/8/16 warps per CTA, backward 4/8 warps, the fused
+ * forward+backward VJP kernel 4/8 warps versus the forward + backward pair
+ * -- and keeps the fastest in the handle for later calls.  Synchronises
+ * `stream`; writes the number of neighbor pairs to *pairs_out (host, may be
+ * NULL).  Inputs as in gmp_featurize. */
+gmp_status gmp_tune(gmp_handle h, int32_t n_struct, const int64_t *atom_off, const double *pos,
+                    const double *cell, const uint8_t *pbc, const int32_t *species, int32_t reps,
+                    int64_t *pairs_out, void *stream);
+
+/* The handle's launch shapes as 6 int32 per sigma pass (forward tile,
+ * forward warps, backward warps, fused-VJP flag, fused warps, Jacobian
+ * warps; 0 warps = largest that fits), for persisting tuning results.
+ * gmp_tuning_get needs n >= 6 * passes (GMP_ERR_CAPACITY otherwise);
+ * gmp_tuning_set needs exactly that many values in range. */
+gmp_status gmp_tuning_get(gmp_handle h, int32_t *values, int32_t n);
+gmp_status gmp_tuning_set(gmp_handle h, const int32_t *values, int32_t n);
+
 /* Wait for `stream` with a timeout (seconds, <= 0: wait forever) by polling
  * an event; returns GMP_ERR_TIMEOUT if the work has not finished. */
 gmp_status gmp_sync(gmp_handle h, void *stream, double timeout_s);

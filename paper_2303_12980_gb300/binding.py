@@ -27,8 +27,11 @@ GMP_OK = 0
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp",
-           "gmp_featurize_grad", "gmp_neighbors", "gmp_sync", "gmp_profile", "gmp_profile_read",
+           "gmp_featurize_grad", "gmp_neighbors", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
+           "gmp_sync", "gmp_profile", "gmp_profile_read",
            "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
+TUNING_CACHE = os.environ.get("GMP_TUNING_CACHE",
+                              os.path.join(os.path.expanduser("~"), ".cache", "gmp_gb300", "tuning.json"))
 
 _lib = None
 _lock = threading.Lock()
@@ -73,6 +76,10 @@ def load_library(path: str = LIB_PATH):
         L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
         L.gmp_featurize_grad.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_set_graph.argtypes = [vp, C.c_int]
+        L.gmp_tune.argtypes = common + [i32, C.POINTER(i64), vp]
+        L.gmp_tuning_get.argtypes = [vp, C.POINTER(i32), i32]
+        L.gmp_tuning_set.argtypes = [vp, C.POINTER(i32), i32]
         L.gmp_sync.argtypes = [vp, vp, C.c_double]
         L.gmp_profile.argtypes = [vp, C.c_int]
         L.gmp_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), C.c_int]
@@ -294,6 +301,71 @@ class GMPFeaturizer:
         self._check(self._L.gmp_profile_read(self._h, ms, cnt, 4))
         names = ("neighbors", "features", "backward", "refine")
         return {n: (ms[k], cnt[k]) for k, n in enumerate(names)}
+
+    def set_graph(self, enable: bool = True):
+        """CUDA-graph replay of repeated calls on the same buffers and a
+        non-default stream (gmp_set_graph)."""
+        self._check(self._L.gmp_set_graph(self._h, int(enable)))
+
+    # ---------------------------------------------------------------- tuning
+    def tuning_key(self, atom_off) -> str:
+        """Signature of a problem for the tuning cache: probe set, tables
+        and the batch's size class."""
+        off = np.asarray(atom_off)
+        N, S = int(off[-1]), off.size - 1
+        ng = tuple(int(x) for x in self._keep["n_gauss"])
+        return (f"o{self.orders}_s{len(self.sigmas)}_g{max(ng)}x{len(ng)}_rc{self.cutoff:g}"
+                f"_N{int(np.log2(max(N, 1)))}_S{int(np.log2(max(S, 1)))}")
+
+    def tuning(self):
+        n = 6 * 64
+        buf = (C.c_int32 * n)()
+        st = self._L.gmp_tuning_get(self._h, buf, n)
+        self._check(st)
+        vals = list(buf)
+        npass = max(1, (len(self.sigmas) + 15) // 16) if any(o >= 0 for o in self.orders) else 1
+        return vals[:6 * npass]
+
+    def set_tuning(self, values):
+        arr = (C.c_int32 * len(values))(*[int(v) for v in values])
+        self._check(self._L.gmp_tuning_set(self._h, arr, len(values)))
+
+    def tune(self, pos, species, atom_off, cell, pbc, reps: int = 3, cache: bool = True, stream=None):
+        """Pick the fastest launch shapes on this batch (gmp_tune), reusing
+        and updating a JSON cache keyed by tuning_key()."""
+        import json
+        key = self.tuning_key(atom_off)
+        if cache and os.path.exists(TUNING_CACHE):
+            try:
+                with open(TUNING_CACHE) as f:
+                    known = json.load(f)
+                if key in known:
+                    self.set_tuning(known[key])
+                    return {"key": key, "values": known[key], "cached": True}
+            except (OSError, ValueError, GMPError):
+                pass
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        pairs = C.c_int64()
+        self._check(self._L.gmp_tune(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                     pbc.ctypes.data, _ptr(species), int(reps), C.byref(pairs),
+                                     _stream_ptr(stream, on_dev)))
+        vals = self.tuning()
+        if cache:
+            try:
+                os.makedirs(os.path.dirname(TUNING_CACHE), exist_ok=True)
+                known = {}
+                if os.path.exists(TUNING_CACHE):
+                    with open(TUNING_CACHE) as f:
+                        known = json.load(f)
+                known[key] = vals
+                tmp = TUNING_CACHE + f".tmp{os.getpid()}"
+                with open(tmp, "w") as f:
+                    json.dump(known, f, indent=1)
+                os.replace(tmp, TUNING_CACHE)
+            except (OSError, ValueError):
+                pass
+        return {"key": key, "values": vals, "cached": False, "pairs": int(pairs.value)}
 
     def sync(self, stream=None, timeout_s: float = 0.0):
         torch = _torch()

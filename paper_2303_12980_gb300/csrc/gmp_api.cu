@@ -45,6 +45,12 @@ struct PassData {
   int L;
   int NS;
   DevBuf rad;
+  // launch shapes (defaults until gmp_tune / gmp_tuning_set)
+  GmpShape fwd{16, 0};
+  GmpShape bwd{16, 0};
+  GmpShape fused{16, 0};
+  GmpShape jac{16, 0};
+  int vjp_fused = 0;  // 1: one fused forward+backward kernel instead of two
 };
 
 }  // namespace
@@ -85,6 +91,15 @@ struct gmp_ctx {
   std::string err;
   int64_t launches = 0;
   cudaEvent_t ev = nullptr;
+  // CUDA-graph replay of whole calls (gmp_set_graph)
+  bool graph_on = false;
+  bool graph_valid = false;
+  bool capturing = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<uintptr_t> graph_key;
+  int64_t cap_pairs = 0;   // capacities baked into the captured graph
+  int cap_keys = 0;
+  int64_t struct_gen = 0;  // bumped whenever the batch description changes
   // stage timing
   bool profiling = false;
   static constexpr int kStages = 4;     // neighbors, features kernel, backward kernel, refine/finish
@@ -115,16 +130,16 @@ gmp_status cuda_fail(gmp_ctx* h, cudaError_t e, const char* where) {
 
 int pad_sigmas(int n) { return n <= 4 ? 4 : (n <= 8 ? 8 : 16); }
 
-cudaError_t launch_compute(int L, int kind, int ns, const gmpk::KParams& K, cudaStream_t st, int sm,
-                           int64_t* launches) {
+cudaError_t launch_compute(int L, int kind, int ns, const gmpk::KParams& K, GmpShape shape, cudaStream_t st,
+                           int sm, int64_t* launches) {
   switch (L) {
-    case 0: return gmp_launch_compute_L0(kind, ns, K, st, sm, launches);
-    case 1: return gmp_launch_compute_L1(kind, ns, K, st, sm, launches);
-    case 2: return gmp_launch_compute_L2(kind, ns, K, st, sm, launches);
-    case 3: return gmp_launch_compute_L3(kind, ns, K, st, sm, launches);
-    case 4: return gmp_launch_compute_L4(kind, ns, K, st, sm, launches);
-    case 5: return gmp_launch_compute_L5(kind, ns, K, st, sm, launches);
-    case 6: return gmp_launch_compute_L6(kind, ns, K, st, sm, launches);
+    case 0: return gmp_launch_compute_L0(kind, ns, K, shape, st, sm, launches);
+    case 1: return gmp_launch_compute_L1(kind, ns, K, shape, st, sm, launches);
+    case 2: return gmp_launch_compute_L2(kind, ns, K, shape, st, sm, launches);
+    case 3: return gmp_launch_compute_L3(kind, ns, K, shape, st, sm, launches);
+    case 4: return gmp_launch_compute_L4(kind, ns, K, shape, st, sm, launches);
+    case 5: return gmp_launch_compute_L5(kind, ns, K, shape, st, sm, launches);
+    case 6: return gmp_launch_compute_L6(kind, ns, K, shape, st, sm, launches);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -221,6 +236,7 @@ gmp_status upload_structures(gmp_ctx* h, int32_t S, const int64_t* atom_off, con
   if (N > 0) GMP_CK(gmp_launch_struct_of(h->atom_off.as<int64_t>(), S, h->struct_of.as<int32_t>(), st, &h->launches), "struct_of");
   // the copies above read host memory asynchronously: wait before returning
   GMP_CK(cudaStreamSynchronize(st), "upload sync");
+  ++h->struct_gen;
   h->last_off.assign(atom_off, atom_off + S + 1);
   h->last_cell.assign(cell, cell + 9 * S);
   h->last_pbc.assign(pbc, pbc + 3 * S);
@@ -240,7 +256,7 @@ gmp_status decode_device_error(gmp_ctx* h, uint32_t w) {
 
 // Records a start (begin = true) or stop event of `stage` on `st`.
 cudaError_t prof_mark(gmp_ctx* h, int stage, bool begin, cudaStream_t st) {
-  if (!h->profiling) return cudaSuccess;
+  if (!h->profiling || h->capturing) return cudaSuccess;
   auto& v = h->prof_ev[stage];
   size_t& u = h->prof_used[stage];
   if (begin && u + 2 > v.size()) {
@@ -259,8 +275,9 @@ cudaError_t prof_mark(gmp_ctx* h, int stage, bool begin, cudaStream_t st) {
 // Binning + exact neighbor lists into h->pairs / h->nbr_off.  Synchronises
 // `st` once (to size the pair buffer).
 gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
-                           int64_t N, cudaStream_t st, bool sorted) {
+                           int64_t N, cudaStream_t st, bool sorted, bool capture = false) {
   int64_t* L = &h->launches;
+  if (!capture) h->graph_valid = false;  // buffers may move: a captured graph is stale
   GMP_CK(prof_mark(h, 0, true, st), "profile");
   uint32_t* d_err = h->scalars.as<uint32_t>();
   int32_t* d_maxm = reinterpret_cast<int32_t*>(d_err + 1);
@@ -296,10 +313,22 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
                                   N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                                   h->atom_rng.as<int4>(), h->atom_y.as<float4>(), h->bin_start.as<int32_t>(),
-                                  h->bin_y.as<float4>(), h->counts.as<int64_t>(), nullptr, nullptr, 0, d_maxm, d_err,
-                                  st, h->sm_count, L),
+                                  h->bin_y.as<float4>(), h->counts.as<int64_t>(), nullptr, nullptr, 0, 0, d_maxm,
+                                  d_err, st, h->sm_count, L),
          "neighbor count");
   GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), N, h->scan_tmp.p, st, L), "scan");
+  if (capture) {
+    // capacities fixed at capture time; the fill and compute kernels skip
+    // (and flag) centers beyond them
+    GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(),
+                                    h->struct_of.as<int32_t>(), N, h->cutoff, pos, h->atom_xh.as<float4>(),
+                                    h->atom_xl.as<float4>(), h->atom_rng.as<int4>(), h->atom_y.as<float4>(),
+                                    h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), nullptr,
+                                    h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->cap_pairs, h->cap_keys,
+                                    d_maxm, d_err, st, h->sm_count, L),
+           "neighbor fill");
+    return GMP_OK;
+  }
   GMP_CK(cudaMemcpyAsync(h->h_small, h->nbr_off.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read P");
   GMP_CK(cudaMemcpyAsync(h->h_small + 1, d_err, 8, cudaMemcpyDeviceToHost, st), "read err");
   GMP_CK(cudaStreamSynchronize(st), "neighbor sync");
@@ -320,8 +349,8 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
                                   h->struct_of.as<int32_t>(), N, h->cutoff, pos, h->atom_xh.as<float4>(),
                                   h->atom_xl.as<float4>(), h->atom_rng.as<int4>(), h->atom_y.as<float4>(),
                                   h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
-                                  nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), keys, d_maxm, d_err, st,
-                                  h->sm_count, L),
+                                  nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->P, keys, d_maxm,
+                                  d_err, st, h->sm_count, L),
          "neighbor fill");
   GMP_CK(prof_mark(h, 0, false, st), "profile");
   return GMP_OK;
@@ -344,6 +373,7 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   K.flags = h->flagq.as<unsigned long long>();
   K.flag_count = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3);
   K.flag_cap = flag_capacity(N);
+  K.pair_cap = h->capturing ? h->cap_pairs : h->P;
   K.sig0 = 16 * pass_index;
   K.flag_tau = kFlagTau;
   return K;
@@ -403,6 +433,64 @@ gmp_status common_checks(gmp_ctx* h, int32_t S, const int64_t* atom_off, const d
   if (r != GMP_OK) return r;
   N = atom_off[S];
   if (N > 0 && (!pos || !species)) return fail(h, GMP_ERR_INVALID_ARG, "pos and species are required");
+  return GMP_OK;
+}
+
+// Replays the captured graph of a call with this key.  Returns
+// GMP_ERR_CAPACITY (with the graph dropped) when there is no matching graph
+// or the batch outgrew the captured capacities: the caller then runs the
+// call eagerly, which re-measures and recaptures.
+gmp_status replay_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStream_t st) {
+  if (!h->graph_valid || key != h->graph_key) return GMP_ERR_CAPACITY;
+  uint32_t* d_err = h->scalars.as<uint32_t>();
+  GMP_CK(cudaGraphLaunch(h->graph_exec, st), "graph launch");
+  GMP_CK(cudaMemcpyAsync(h->h_small + 1, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "read err");
+  GMP_CK(cudaStreamSynchronize(st), "graph sync");
+  const uint32_t w = (uint32_t)(h->h_small[1] & 0xffffffffu);
+  if (!w) return GMP_OK;
+  GMP_CK(cudaMemsetAsync(d_err, 0, 4, st), "clear err");
+  if (w & GMP_DEV_CAPACITY) {
+    h->graph_valid = false;
+    return GMP_ERR_CAPACITY;
+  }
+  return decode_device_error(h, w);
+}
+
+// Captures `seq(true)` (the call's device work without host synchronisation)
+// into a CUDA graph for later replays; capacities get 12.5% headroom over
+// the eager run that just finished.
+template <typename Seq>
+gmp_status capture_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStream_t st, Seq& seq) {
+  if (!st) return GMP_OK;  // the legacy default stream cannot be captured
+  h->cap_pairs = h->P + h->P / 8 + 4096;
+  int keys = 32;
+  while (keys < h->max_m + h->max_m / 8 + 8) keys <<= 1;
+  if ((size_t)keys * 8 > 200 * 1024) return GMP_OK;  // too large for a fixed capacity: stay eager
+  h->cap_keys = keys;
+  GMP_CK(h->pairs.ensure(sizeof(GmpPair) * h->cap_pairs), "pairs");
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  GMP_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture");
+  h->capturing = true;
+  gmp_status r = seq(true);
+  h->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (r != GMP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  const cudaError_t e2 = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    h->graph_exec = nullptr;
+    return cuda_fail(h, e2, "graph instantiate");
+  }
+  h->graph_key = key;
+  h->graph_valid = true;
   return GMP_OK;
 }
 
@@ -618,19 +706,30 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
   } else if (!is_device_ptr(features)) {
     return fail(h, GMP_ERR_INVALID_ARG, "features must be a device pointer when inputs are");
   }
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, false)) != GMP_OK) return r;
-  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 1, true, st), "profile");
-  for (size_t g = 0; g < h->passes.size(); ++g) {
-    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
-    K.features = feat;
-    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_FORWARD, h->passes[g].NS, K, st, h->sm_count, &h->launches),
-           "forward");
-  }
-  GMP_CK(prof_mark(h, 1, false, st), "profile");
-  GMP_CK(prof_mark(h, 3, true, st), "profile");
-  if ((r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 3, false, st), "profile");
+  const bool use_graph = h->graph_on && !io.host;
+  const std::vector<uintptr_t> key = {0, (uintptr_t)io.pos, (uintptr_t)io.species, (uintptr_t)feat, (uintptr_t)st,
+                                      (uintptr_t)N, (uintptr_t)n_struct, (uintptr_t)h->struct_gen};
+  if (use_graph && (r = replay_graph(h, key, st)) != GMP_ERR_CAPACITY) return r;
+  auto seq = [&](bool capture) -> gmp_status {
+    gmp_status q = build_neighbors(h, n_struct, io.pos, io.species, N, st, false, capture);
+    if (q != GMP_OK) return q;
+    if ((q = begin_compute(h, N, st)) != GMP_OK) return q;
+    GMP_CK(prof_mark(h, 1, true, st), "profile");
+    for (size_t g = 0; g < h->passes.size(); ++g) {
+      gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
+      K.features = feat;
+      GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_FORWARD, h->passes[g].NS, K, h->passes[g].fwd, st,
+                            h->sm_count, &h->launches),
+             "forward");
+    }
+    GMP_CK(prof_mark(h, 1, false, st), "profile");
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+    return GMP_OK;
+  };
+  if ((r = seq(false)) != GMP_OK) return r;
+  if (use_graph && (r = capture_graph(h, key, st, seq)) != GMP_OK) return r;
   if (io.host) {
     GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
     GMP_CK(cudaStreamSynchronize(st), "sync");
@@ -663,39 +762,56 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     GMP_CK(h->stage_gradp.ensure(sizeof(float) * N * 3), "stage grad_pos");
     gp = h->stage_gradp.as<float>();
   }
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, false)) != GMP_OK) return r;
+  const bool use_graph = h->graph_on && !io.host;
+  const std::vector<uintptr_t> key = {1, (uintptr_t)io.pos, (uintptr_t)io.species, (uintptr_t)gf, (uintptr_t)feat,
+                                      (uintptr_t)gp, (uintptr_t)st, (uintptr_t)N, (uintptr_t)n_struct,
+                                      (uintptr_t)h->struct_gen};
+  if (use_graph && (r = replay_graph(h, key, st)) != GMP_ERR_CAPACITY) return r;
+  // buffers first (no allocation may happen while a graph is captured)
   GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
+  for (const PassData& pd : h->passes)
+    GMP_CK(h->mu.ensure(sizeof(float) * (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1)), "moments");
+  if (!feat) GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
+  auto seq = [&](bool capture) -> gmp_status {
+  gmp_status q = build_neighbors(h, n_struct, io.pos, io.species, N, st, false, capture);
+  if (q != GMP_OK) return q;
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
-  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
+  if ((q = begin_compute(h, N, st)) != GMP_OK) return q;
   for (size_t g = 0; g < h->passes.size(); ++g) {
     const PassData& pd = h->passes[g];
     // forward kernel (features + moments), then the backward kernel reading
-    // the moments: two lean kernels instead of one fused kernel
-    const size_t mu_floats = (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1);
-    GMP_CK(h->mu.ensure(sizeof(float) * mu_floats), "moments");
-    float* fout = feat;
-    if (!fout) {
-      GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
-      fout = h->stage_feat.as<float>();
-    }
+    // the moments (or one fused kernel, if the autotuner chose it)
+    float* fout = feat ? feat : h->stage_feat.as<float>();
     gmpk::KParams K = base_params(h, pd, (int)g, N);
     K.features = fout;
+    if (pd.vjp_fused) {
+      K.grad_feat = gf;
+      K.grad_acc = h->grad_acc.as<double>();
+      GMP_CK(prof_mark(h, 2, true, st), "profile");
+      GMP_CK(launch_compute(pd.L, GMP_KIND_VJP, pd.NS, K, pd.fused, st, h->sm_count, &h->launches), "vjp");
+      GMP_CK(prof_mark(h, 2, false, st), "profile");
+      continue;
+    }
     K.mu_out = h->mu.as<float>();
     GMP_CK(prof_mark(h, 1, true, st), "profile");
-    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, st, h->sm_count, &h->launches), "forward");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
     GMP_CK(prof_mark(h, 1, false, st), "profile");
     K.features = nullptr;
     K.flags = nullptr;
     K.grad_feat = gf;
     K.grad_acc = h->grad_acc.as<double>();
     GMP_CK(prof_mark(h, 2, true, st), "profile");
-    GMP_CK(launch_compute(pd.L, GMP_KIND_BACKWARD, pd.NS, K, st, h->sm_count, &h->launches), "backward");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_BACKWARD, pd.NS, K, pd.bwd, st, h->sm_count, &h->launches), "backward");
     GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
   GMP_CK(prof_mark(h, 3, true, st), "profile");
-  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  if (feat && (q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
   GMP_CK(gmp_launch_grad_finish(N, h->grad_acc.as<double>(), gp, st, &h->launches), "grad finish");
   GMP_CK(prof_mark(h, 3, false, st), "profile");
+  return GMP_OK;
+  };
+  if ((r = seq(false)) != GMP_OK) return r;
+  if (use_graph && (r = capture_graph(h, key, st, seq)) != GMP_OK) return r;
   if (io.host) {
     if (features)
       GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
@@ -754,7 +870,8 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
     K.jac_off = joff;
     K.jac_j = jj;
     K.jac = jd;
-    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_JACOBIAN, h->passes[g].NS, K, st, h->sm_count, &h->launches),
+    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_JACOBIAN, h->passes[g].NS, K, h->passes[g].jac, st, h->sm_count,
+                          &h->launches),
            "jacobian");
   }
   GMP_CK(prof_mark(h, 1, false, st), "profile");
@@ -809,6 +926,140 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t* atom_off
     GMP_CK(cudaStreamSynchronize(st), "sync");
     tj.release();
     ts.release();
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_tune(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                    const double* cell, const uint8_t* pbc, const int32_t* species, int32_t reps,
+                    int64_t* pairs_out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (pairs_out) *pairs_out = 0;
+  if (N == 0) return GMP_OK;
+  if (reps < 1) reps = 1;
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, false)) != GMP_OK) return r;
+  if (pairs_out) *pairs_out = h->P;
+  GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "tune features");
+  GMP_CK(h->stage_gradf.ensure(sizeof(float) * N * h->F), "tune grad");
+  GMP_CK(cudaMemsetAsync(h->stage_gradf.p, 0, sizeof(float) * N * h->F, st), "tune grad zero");
+  GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
+  cudaEvent_t e0, e1;
+  GMP_CK(cudaEventCreate(&e0), "event");
+  GMP_CK(cudaEventCreate(&e1), "event");
+  auto timed = [&](int kind, const PassData& pd, const gmpk::KParams& K, GmpShape shape, float* ms) -> cudaError_t {
+    cudaError_t e = launch_compute(pd.L, kind, pd.NS, K, shape, st, h->sm_count, &h->launches);  // warm-up
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
+    for (int k = 0; k < reps; ++k)
+      if ((e = launch_compute(pd.L, kind, pd.NS, K, shape, st, h->sm_count, &h->launches)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    if ((e = cudaEventElapsedTime(ms, e0, e1)) != cudaSuccess) return e;
+    *ms /= reps;
+    return cudaSuccess;
+  };
+  gmp_status out = GMP_OK;
+  for (size_t g = 0; g < h->passes.size() && out == GMP_OK; ++g) {
+    PassData& pd = h->passes[g];
+    const size_t mu_floats = (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1);
+    if (h->mu.ensure(sizeof(float) * mu_floats) != cudaSuccess ||
+        (out = begin_compute(h, N, st)) != GMP_OK) {
+      if (out == GMP_OK) out = fail(h, GMP_ERR_OOM, "tune buffers");
+      break;
+    }
+    gmpk::KParams K = base_params(h, pd, (int)g, N);
+    K.flags = nullptr;
+    K.features = h->stage_feat.as<float>();
+    K.mu_out = h->mu.as<float>();
+    float best_f = 1e30f, t = 0.0f;
+    GmpShape fwd_best = pd.fwd;
+    for (int tile : {16, 32})
+      for (int warps : {4, 8, 16}) {
+        cudaError_t e = timed(GMP_KIND_FORWARD, pd, K, GmpShape{tile, warps}, &t);
+        if (e != cudaSuccess) { out = cuda_fail(h, e, "tune forward"); break; }
+        if (t < best_f) { best_f = t; fwd_best = GmpShape{tile, warps}; }
+      }
+    if (out != GMP_OK) break;
+    // moments for the backward candidates
+    if (cudaError_t e = launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, fwd_best, st, h->sm_count, &h->launches)) {
+      out = cuda_fail(h, e, "tune forward");
+      break;
+    }
+    gmpk::KParams Kb = K;
+    Kb.features = nullptr;
+    Kb.grad_feat = h->stage_gradf.as<float>();
+    Kb.grad_acc = h->grad_acc.as<double>();
+    float best_b = 1e30f;
+    GmpShape bwd_best = pd.bwd;
+    for (int warps : {4, 8}) {
+      cudaError_t e = timed(GMP_KIND_BACKWARD, pd, Kb, GmpShape{16, warps}, &t);
+      if (e != cudaSuccess) { out = cuda_fail(h, e, "tune backward"); break; }
+      if (t < best_b) { best_b = t; bwd_best = GmpShape{16, warps}; }
+    }
+    if (out != GMP_OK) break;
+    gmpk::KParams Kv = Kb;
+    Kv.features = h->stage_feat.as<float>();
+    Kv.mu_out = nullptr;
+    float best_v = 1e30f;
+    GmpShape fused_best = pd.fused;
+    for (int warps : {4, 8}) {
+      cudaError_t e = timed(GMP_KIND_VJP, pd, Kv, GmpShape{16, warps}, &t);
+      if (e != cudaSuccess) { out = cuda_fail(h, e, "tune fused"); break; }
+      if (t < best_v) { best_v = t; fused_best = GmpShape{16, warps}; }
+    }
+    if (out != GMP_OK) break;
+    pd.fwd = fwd_best;
+    pd.bwd = bwd_best;
+    pd.fused = fused_best;
+    pd.vjp_fused = best_v < best_f + best_b ? 1 : 0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return out;
+}
+
+gmp_status gmp_set_graph(gmp_handle h, int enable) {
+  if (!h) return GMP_ERR_INVALID_ARG;
+  h->graph_on = enable != 0;
+  h->graph_valid = false;
+  return GMP_OK;
+}
+
+gmp_status gmp_tuning_get(gmp_handle h, int32_t* values, int32_t n) {
+  if (!h || !values) return GMP_ERR_INVALID_ARG;
+  const int need = 6 * (int)h->passes.size();
+  if (n < need) return fail(h, GMP_ERR_CAPACITY, "tuning record needs " + std::to_string(need) + " values");
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    const PassData& pd = h->passes[g];
+    int32_t* v = values + 6 * g;
+    v[0] = pd.fwd.tile; v[1] = pd.fwd.warps; v[2] = pd.bwd.warps;
+    v[3] = pd.vjp_fused; v[4] = pd.fused.warps; v[5] = pd.jac.warps;
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_tuning_set(gmp_handle h, const int32_t* values, int32_t n) {
+  if (!h || !values) return GMP_ERR_INVALID_ARG;
+  if (n != 6 * (int)h->passes.size()) return fail(h, GMP_ERR_INVALID_ARG, "tuning record has the wrong length");
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    const int32_t* v = values + 6 * g;
+    if ((v[0] != 16 && v[0] != 32) || v[1] < 0 || v[1] > 16 || v[2] < 0 || v[2] > 16 || (v[3] != 0 && v[3] != 1) ||
+        v[4] < 0 || v[4] > 16 || v[5] < 0 || v[5] > 16)
+      return fail(h, GMP_ERR_INVALID_ARG, "tuning record out of range");
+  }
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    PassData& pd = h->passes[g];
+    const int32_t* v = values + 6 * g;
+    pd.fwd = GmpShape{v[0], v[1]};
+    pd.bwd = GmpShape{16, v[2]};
+    pd.vjp_fused = v[3];
+    pd.fused = GmpShape{16, v[4]};
+    pd.jac = GmpShape{16, v[5]};
   }
   return GMP_OK;
 }
@@ -879,6 +1130,7 @@ void gmp_destroy(gmp_handle h) {
                     &h->jac_counts, &h->stage_pos, &h->stage_species, &h->stage_feat, &h->stage_gradf,
                     &h->stage_gradp};
   for (DevBuf* b : bufs) b->release();
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->h_small) cudaFreeHost(h->h_small);
   for (auto& v : h->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);

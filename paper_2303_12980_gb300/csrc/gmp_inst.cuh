@@ -7,26 +7,32 @@
 
 namespace gmpk {
 
-template <int L, int NS>
+template <int L, int NS, int TILE>
 size_t smem_bytes(const GmpPass& P, int warps) {
-  return sizeof(float) * (table_floats(P.n_el, NS, P.kmax) + (size_t)warps * Shape<L, NS>::WARP_FLOATS);
+  return sizeof(float) * (table_floats(P.n_el, NS, P.kmax) + (size_t)warps * Shape<L, NS, TILE>::WARP_FLOATS);
 }
 
+// shape.tile: 16 or 32 pairs per forward tile; shape.warps: warps per CTA
+// (0 = as many as the launch bounds and 227 KB of shared memory allow).
 template <int L, int NS>
-cudaError_t launch(int kind, const KParams& K, cudaStream_t st, int sm_count, int64_t* launches) {
-  void (*fn)(KParams) = kind == GMP_KIND_FORWARD    ? k_forward<L, NS>
+cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, int sm_count,
+                   int64_t* launches) {
+  const int tile = (kind == GMP_KIND_FORWARD && shape.tile == 32) ? 32 : 16;
+  void (*fn)(KParams) = kind == GMP_KIND_FORWARD    ? (tile == 32 ? k_forward<L, NS, 32> : k_forward<L, NS, 16>)
                         : kind == GMP_KIND_VJP      ? k_vjp<L, NS>
                         : kind == GMP_KIND_BACKWARD ? k_backward<L, NS>
                                                     : k_jacobian<L, NS>;
-  // as many warps per CTA as the kernel allows (launch bounds) and 227 KB of
-  // shared memory fit
+  auto smem_of = [&](int w) {
+    return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w) : smem_bytes<L, NS, 16>(K.pass, w);
+  };
   cudaFuncAttributes fa;
   cudaError_t ea = cudaFuncGetAttributes(&fa, fn);
   if (ea != cudaSuccess) return ea;
   int warps = fa.maxThreadsPerBlock / 32;
   if (warps > 16) warps = 16;
-  while (warps > 1 && smem_bytes<L, NS>(K.pass, warps) > 227 * 1024) --warps;
-  const size_t smem = smem_bytes<L, NS>(K.pass, warps);
+  if (shape.warps > 0 && shape.warps < warps) warps = shape.warps;
+  while (warps > 1 && smem_of(warps) > 227 * 1024) --warps;
+  const size_t smem = smem_of(warps);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -47,13 +53,13 @@ cudaError_t launch(int kind, const KParams& K, cudaStream_t st, int sm_count, in
 
 }  // namespace gmpk
 
-#define GMP_DEFINE_LAUNCHER(LV)                                                                 \
-  cudaError_t gmp_launch_compute_L##LV(int kind, int ns, const gmpk::KParams& K, cudaStream_t st, \
-                                      int sm_count, int64_t* launches) {                       \
-    switch (ns) {                                                                               \
-      case 4: return gmpk::launch<LV, 4>(kind, K, st, sm_count, launches);                      \
-      case 8: return gmpk::launch<LV, 8>(kind, K, st, sm_count, launches);                      \
-      case 16: return gmpk::launch<LV, 16>(kind, K, st, sm_count, launches);                    \
-      default: return cudaErrorInvalidValue;                                                    \
-    }                                                                                           \
+#define GMP_DEFINE_LAUNCHER(LV)                                                                      \
+  cudaError_t gmp_launch_compute_L##LV(int kind, int ns, const gmpk::KParams& K, GmpShape shape,      \
+                                      cudaStream_t st, int sm_count, int64_t* launches) {             \
+    switch (ns) {                                                                                    \
+      case 4: return gmpk::launch<LV, 4>(kind, K, shape, st, sm_count, launches);                    \
+      case 8: return gmpk::launch<LV, 8>(kind, K, shape, st, sm_count, launches);                    \
+      case 16: return gmpk::launch<LV, 16>(kind, K, shape, st, sm_count, launches);                  \
+      default: return cudaErrorInvalidValue;                                                         \
+    }                                                                                                \
   }

@@ -180,8 +180,8 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
                                      const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
-                                     GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
-                                     cudaStream_t stream, int sm_count, int64_t* launches);
+                                     GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
 cudaError_t gmp_launch_forward(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
                                const GmpPair* pairs, float* features, float* mu_out,
                                int32_t* work_counter, cudaStream_t stream, int sm_count,

@@ -72,7 +72,7 @@ __host__ __device__ constexpr int odd4(int n) {
   return 4 * q;
 }
 
-template <int L, int NS>
+template <int L, int NS, int TILE_ = 16>
 struct Shape {
   static constexpr int NIND = (L + 1) * (L + 1);   // independent components, orders 0..L
   static constexpr int NIND1 = (L + 2) * (L + 2);  // ... orders 0..L+1
@@ -83,8 +83,9 @@ struct Shape {
   static constexpr int RL4 = (L + 1 + 3) / 4 * 4;  // r^l, l = 0..L, after the S chunks
   static constexpr int RSTR = odd4((L + 1) * NS);
   static constexpr int SSTR = odd4(NCH * 4 + RL4);
-  static constexpr int TILE = 16;                  // pairs staged per tile (2 lanes per pair)
+  static constexpr int TILE = TILE_;               // pairs staged per tile: 16 (2 lanes per pair) or 32
   static constexpr int FOLD = 16;                  // pairs per FP32 partial before the TwoSum fold
+  static_assert(TILE_ == 16 || TILE_ == 32, "tile of 16 or 32 pairs");
   static constexpr int NINDP = (NIND + 3) / 4 * 4; // padded row of per-sigma vectors
   static constexpr int WARP_FLOATS = TILE * RSTR + TILE * SSTR;
   static_assert(NS * NIND + NS * (L + 1) <= TILE * RSTR, "moments and bounds must fit the R tile");
@@ -121,6 +122,7 @@ struct KParams {
   unsigned long long* flags;  // packed (center, order, sigma, column)
   int32_t* flag_count;
   int64_t flag_cap;
+  int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
   float flag_tau;             // flag when f < flag_tau * C_l l! (2l-1)!! B^2
 };
@@ -198,10 +200,7 @@ __device__ __forceinline__ float density_term(const float* __restrict__ dens_e, 
 }
 
 // Shared memory: tables first (radial then density), then one region per warp.
-template <int L, int NS>
-__host__ __device__ constexpr size_t warp_region_floats() {
-  return (size_t)Shape<L, NS>::WARP_FLOATS;
-}
+
 
 __host__ __device__ inline size_t table_floats(int n_el, int NS, int kmax) {
   return (size_t)n_el * rad_elem_stride(NS, kmax) + (size_t)n_el * dens_elem_stride(kmax);
@@ -231,7 +230,7 @@ __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_r
 // compensated pair) in Mu[s * NIND + k] and the conditioning bound
 // B_{l,s} = sum_pairs |R_{l,s}| r^l in Mu[NS * NIND + s * (L+1) + l]
 // (warp-private shared memory), and returns the density (all lanes).
-template <int L, int NS>
+template <int L, int NS, int TILE = 16>
 __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens,
                                                const GmpPair* __restrict__ pairs, int64_t p0,
@@ -240,7 +239,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
                                                const int (&it_sb)[Shape<L, NS>::Q],
                                                const int (&it_ch)[Shape<L, NS>::Q],
                                                const bool (&it_ok)[Shape<L, NS>::Q]) {
-  using SH = Shape<L, NS>;
+  using SH = Shape<L, NS, TILE>;
   const int lane = threadIdx.x & 31;
   float hi[SH::Q][16], lo[SH::Q][16];
 #pragma unroll
@@ -254,9 +253,10 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
 #pragma unroll
     for (int u = 0; u < 4; ++u) bnd[q][u] = 0.0f;
 
-  const int half = lane >> 4;         // phase 1: two lanes per pair
-  const int pl = lane & 15;
-  constexpr int SG_LO = (SH::NSB + 1) / 2;  // sigma groups of half 0: [0, SG_LO)
+  constexpr int LPP = 32 / TILE;      // phase 1: lanes per pair (2 or 1)
+  const int half = LPP == 2 ? (lane >> 4) : 0;
+  const int pl = LPP == 2 ? (lane & 15) : lane;
+  constexpr int SG_LO = LPP == 2 ? (SH::NSB + 1) / 2 : SH::NSB;  // sigma groups of half 0: [0, SG_LO)
   const int sg0 = half ? SG_LO : 0, sg1 = half ? SH::NSB : SG_LO;
   for (int base = 0; base < M; base += SH::TILE) {
     const int np = min(SH::TILE, M - base);
@@ -282,7 +282,8 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
           v.w = (k0 + 3 < kend) ? S[(k0 + 3 < kend) ? k0 + 3 : k0] : 0.0f;
           *reinterpret_cast<float4*>(srow + 4 * c) = v;
         });
-      } else {  // r^l for the conditioning bound
+      }
+      if (LPP == 1 || half == 1) {  // r^l for the conditioning bound
         const float r = __fsqrt_rn(r2h);
         float rl[SH::RL4];
         rl[0] = 1.0f;
@@ -426,9 +427,9 @@ __device__ __forceinline__ void write_features(const KParams& K, int64_t i, cons
 }
 
 // ------------------------------------------------------------------------
-template <int L, int NS>
+template <int L, int NS, int TILE>
 __global__ void __launch_bounds__(512) k_forward(KParams K) {
-  using SH = Shape<L, NS>;
+  using SH = Shape<L, NS, TILE>;
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
@@ -445,8 +446,10 @@ __global__ void __launch_bounds__(512) k_forward(KParams K) {
   setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_off[i];
+    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
     const int M = (int)(K.nbr_off[i + 1] - p0);
-    const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
+    const float rho = forward_sweep<L, NS, TILE>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch,
+                                                 it_ok);
     write_features<L, NS>(K, i, Mu, rho);
     if (K.mu_out) {
       float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
@@ -597,6 +600,7 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_off[i];
+    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
     const int M = (int)(K.nbr_off[i + 1] - p0);
     const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
     const float* grow = K.grad_feat + i * P.F;
@@ -623,6 +627,7 @@ __global__ void __launch_bounds__(256) k_backward(KParams K) {
   float* Lam = Mu + SH::TILE * SH::RSTR;
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_off[i];
+    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
     const int M = (int)(K.nbr_off[i + 1] - p0);
     const float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
     for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
@@ -662,6 +667,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   constexpr int QF = (8 * 16 + 1 + 31) / 32;  // features per lane (<= 8 orders x 16 sigmas + density)
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_off[i];
+    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
     const int M = (int)(K.nbr_off[i + 1] - p0);
     const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
     const int nf = P.n_ord * P.nsig;

@@ -13,9 +13,15 @@ namespace gmpk {
 struct KParams;
 }
 
+// Launch shape of a compute kernel (chosen by the autotuner or defaults).
+struct GmpShape {
+  int tile;   // forward tile: 16 pairs (two lanes per pair) or 32 (one lane per pair)
+  int warps;  // warps per CTA, 0 = largest that fits
+};
+
 #define GMP_DECLARE_LAUNCHER(LV)                                                                \
-  cudaError_t gmp_launch_compute_L##LV(int kind, int ns, const gmpk::KParams& K, cudaStream_t st, \
-                                      int sm_count, int64_t* launches);
+  cudaError_t gmp_launch_compute_L##LV(int kind, int ns, const gmpk::KParams& K, GmpShape shape,  \
+                                      cudaStream_t st, int sm_count, int64_t* launches);
 GMP_DECLARE_LAUNCHER(0)
 GMP_DECLARE_LAUNCHER(1)
 GMP_DECLARE_LAUNCHER(2)

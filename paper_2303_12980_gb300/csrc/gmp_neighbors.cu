@@ -394,8 +394,8 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
                             const int4* __restrict__ atom_rng, const float4* __restrict__ atom_y,
                             const int32_t* __restrict__ bin_start, const float4* __restrict__ bin_y,
                             int64_t* __restrict__ counts, const int64_t* __restrict__ offsets,
-                            GmpPair* __restrict__ pairs, int max_keys, int32_t* __restrict__ maxm,
-                            uint32_t* __restrict__ err) {
+                            GmpPair* __restrict__ pairs, int64_t pair_cap, int max_keys,
+                            int32_t* __restrict__ maxm, uint32_t* __restrict__ err) {
   extern __shared__ unsigned long long sh_keys[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -501,7 +501,11 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
   __syncwarp();
   const int M = count;
   const int64_t base = offsets[i];
-  if (M != (int)(offsets[i + 1] - base) || M > max_keys) {
+  if (offsets[i + 1] > pair_cap || M > max_keys) {  // capacities fixed in advance (graph replay)
+    if (lane == 0) atomicOr(err, GMP_DEV_CAPACITY);
+    return;
+  }
+  if (M != (int)(offsets[i + 1] - base)) {
     if (lane == 0) atomicOr(err, GMP_DEV_TOO_MANY_NEIGHBORS);
     return;
   }
@@ -644,8 +648,8 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
                                      const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
-                                     GmpPair* pairs, int max_keys, int32_t* d_maxm, uint32_t* d_err,
-                                     cudaStream_t stream, int sm_count, int64_t* launches) {
+                                     GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
   (void)sm_count;
   const double rc2 = cutoff * cutoff;
   const float rc2hi = (float)rc2;
@@ -665,7 +669,7 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
   k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, d_struct_of, N,
                                                     (float)cutoff, rc2hi, rc2lo, rc2, pos, atom_xh,
                                                     atom_xl, atom_rng, atom_y, bin_start, bin_y, counts,
-                                                    offsets, pairs, max_keys, d_maxm, d_err);
+                                                    offsets, pairs, pair_cap, max_keys, d_maxm, d_err);
   ++*launches;
   return cudaGetLastError();
 }

@@ -183,7 +183,7 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
                         d_ay, d_by, d_u, d_scan, Layout::scan_bytes, st, sm_count, &launches);
   if (e == cudaSuccess)
     e = gmp_launch_neighbor_pass(0, d_st, d_grid, d_struct_of, n_atoms, cutoff, pos, d_xh, d_xl, d_rng, d_ay,
-                                 d_bstart, d_by, counts, nullptr, nullptr, 0, d_maxm, d_err, st, sm_count,
+                                 d_bstart, d_by, counts, nullptr, nullptr, 0, 0, d_maxm, d_err, st, sm_count,
                                  &launches);
   uint32_t w = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d_err, sizeof(w), cudaMemcpyDeviceToHost, st);

@@ -177,3 +177,29 @@ def test_deterministic(torch):
     b = F.featurize(pos, sp, w.atom_off, w.cells, w.pbc)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_graph_replay_matches_eager(torch):
+    """Graph mode: replays on the same buffers give the eager results, follow
+    in-place position updates, and fall back eagerly when the batch outgrows
+    the captured neighbor capacity."""
+    w = wl("batched300")
+    F_eager = _featurizer(w)
+    F_graph = _featurizer(w)
+    F_graph.set_graph(True)
+    s = torch.cuda.Stream()
+    pos, sp = _dev(torch, w)
+    g = torch.from_numpy(synth.upstream_gradient(w.n_atoms, w.n_features, seed=4)).cuda()
+    feat = torch.empty((w.n_atoms, w.n_features), device="cuda")
+    gp = torch.empty((w.n_atoms, 3), device="cuda")
+    with torch.cuda.stream(s):
+        for step in range(4):
+            if step == 2:   # small in-place move: same buffers, graph replay
+                pos += 0.01 * torch.randn_like(pos)
+            if step == 3:   # compress the clusters (cells unchanged): more neighbors than captured
+                pos *= 0.8
+            F_graph.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
+            fe, ge = F_eager.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g)
+            s.synchronize()
+            assert torch.equal(feat, fe), step
+            assert torch.equal(gp, ge), step
