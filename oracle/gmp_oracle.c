@@ -264,8 +264,17 @@ typedef struct {
  * ascending).  Image bounds per periodic axis k: with b_k the k-th column
  * of inv(cell) and df = frac_j - frac_i, any image within rc satisfies
  * |df_k + n_k| <= rc |b_k|; the loop takes one extra image on each side. */
+static int64_t list_neighbors_at(const oracle_problem *P, int s, const double *xi, opair **out,
+                                 int64_t *cap);
+
 static int64_t list_neighbors(const oracle_problem *P, int64_t i, opair **out, int64_t *cap) {
-  int s = struct_of(P, i);
+  return list_neighbors_at(P, struct_of(P, i), P->pos + 3 * i, out, cap);
+}
+
+/* The same enumeration around an arbitrary point xi of structure s (the
+ * center need not be an atom): d = (x_j - xi) + ((n1 a1 + n2 a2) + n3 a3). */
+static int64_t list_neighbors_at(const oracle_problem *P, int s, const double *xi, opair **out,
+                                 int64_t *cap) {
   const double *A = P->cell + 9 * s;
   const uint8_t *pb = P->pbc + 3 * s;
   int periodic = pb[0] || pb[1] || pb[2];
@@ -279,7 +288,6 @@ static int64_t list_neighbors(const oracle_problem *P, int64_t i, opair **out, i
     }
   }
   const double rc2 = P->cutoff * P->cutoff;
-  const double *xi = P->pos + 3 * i;
   double fi[3];
   for (int k = 0; k < 3; ++k) fi[k] = xi[0] * Ai[k] + xi[1] * Ai[3 + k] + xi[2] * Ai[6 + k];
   int64_t cnt = 0;
@@ -483,8 +491,25 @@ static void pair_terms(const octx *X, int e, const double d[3], double *t, doubl
 /* feat[t*F + f]: features; fabs[t*F + f] (optional): the same reduction
  * applied to the sums of |per-pair contribution| (the cancellation-free
  * scale of each feature); mu (optional): [n_centers, ncol] moments. */
+static int features_impl(const oracle_problem *P, int64_t n_centers, const int64_t *centers,
+                         const double *points, const int32_t *point_struct, double *feat,
+                         double *fabs_out, double *mu_out);
+
 int oracle_features(const oracle_problem *P, int64_t n_centers, const int64_t *centers,
                     double *feat, double *fabs_out, double *mu_out) {
+  return features_impl(P, n_centers, centers, NULL, NULL, feat, fabs_out, mu_out);
+}
+
+/* Features at reference points (PAPER Overview: features "at any set of
+ * reference points" of a structure): points [n,3], point_struct [n]. */
+int oracle_point_features(const oracle_problem *P, int64_t n_points, const double *points,
+                          const int32_t *point_struct, double *feat, double *fabs_out) {
+  return features_impl(P, n_points, NULL, points, point_struct, feat, fabs_out, NULL);
+}
+
+static int features_impl(const oracle_problem *P, int64_t n_centers, const int64_t *centers,
+                         const double *points, const int32_t *point_struct, double *feat,
+                         double *fabs_out, double *mu_out) {
   octx X;
   if (ctx_init(&X, P)) return -1;
   int bad = 0;
@@ -497,7 +522,8 @@ int oracle_features(const oracle_problem *P, int64_t n_centers, const int64_t *c
     double *t = (double *)calloc((size_t)X.ncol + 1, sizeof(double));
 #pragma omp for schedule(dynamic, 1)
     for (int64_t ti = 0; ti < n_centers; ++ti) {
-      int64_t m = list_neighbors(P, centers[ti], &buf, &cap);
+      int64_t m = points ? list_neighbors_at(P, point_struct[ti], points + 3 * ti, &buf, &cap)
+                         : list_neighbors(P, centers[ti], &buf, &cap);
       if (m < 0) { bad = 1; continue; }
       memset(mu, 0, sizeof(double) * X.ncol);
       memset(ab, 0, sizeof(double) * X.ncol);

@@ -75,6 +75,7 @@ def lib():
             L.oracle_neighbor_counts.argtypes = [P, C.c_int64, vp, vp]
             L.oracle_neighbor_lists.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             L.oracle_features.argtypes = [P, C.c_int64, vp, vp, vp, vp]
+            L.oracle_point_features.argtypes = [P, C.c_int64, vp, vp, vp, vp]
             L.oracle_jacobian_counts.argtypes = [P, C.c_int64, vp, vp]
             L.oracle_jacobian_rows.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             _lib = L
@@ -181,6 +182,19 @@ def features(w, centers=None, want_abs=False, want_mu=False):
     if want_mu:
         out.append(mu)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def point_features(w, points, point_struct, want_abs=False):
+    """FP64 features at reference points [n,3] of structures point_struct [n]."""
+    P = Problem(w)
+    pts = np.ascontiguousarray(points, np.float64)
+    ps = np.ascontiguousarray(point_struct, np.int32)
+    f = np.zeros((ps.size, P.F), np.float64)
+    fa = np.zeros((ps.size, P.F), np.float64) if want_abs else None
+    if lib().oracle_point_features(C.byref(P.s), ps.size, pts.ctypes.data, ps.ctypes.data, f.ctypes.data,
+                                   fa.ctypes.data if want_abs else None):
+        raise ValueError("oracle_point_features failed")
+    return (f, fa) if want_abs else f
 
 
 def jacobian_rows(w, centers=None, want_abs=False):

@@ -324,3 +324,79 @@ def test_jacobian_translation_sum_rule(oracle_mod):
     for t in range(10):
         blk = jac[joff[t]:joff[t + 1]]
         assert np.all(np.abs(blk.sum(0)) <= 1e-11 * np.abs(blk).sum(0).max())
+
+
+# ------------------------------------------------------------ reference points
+def test_point_features_match_3d_quadrature(oracle_mod):
+    # probes centred on a point that is not an atom: each moment is the
+    # defining overlap integral on a grid around the point, the feature the
+    # weighted sum of squares l!/(a!b!c!) mu_abc^2 over all components
+    pos = np.array([[0.0, 0.0, 0.0], [0.9, -0.6, 0.5], [-0.5, 0.8, -0.7]])
+    coef, expo = [0.7, 0.4], [1.6, 0.6]
+    sig = 0.55
+    p = np.array([0.35, 0.2, -0.15])
+    w = _cluster(pos, [0, 0, 0], [-1, 0, 1, 2, 3], [sig], coef, expo, [2])
+    f = oracle_mod.point_features(w, p[None, :], [0])[0]
+    h = 0.05
+    g = np.arange(-5.0, 5.0 + h / 2, h)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    beta = 1.0 / (2 * sig * sig)
+    Ns = (2 * math.pi * sig * sig) ** -1.5
+    rho = np.zeros_like(X)
+    for q in pos - p:
+        R2 = (X - q[0]) ** 2 + (Y - q[1]) ** 2 + (Z - q[2]) ** 2
+        for c, a in zip(coef, expo):
+            rho += c * np.exp(-a * R2)
+    base = Ns * np.exp(-beta * (X * X + Y * Y + Z * Z)) * rho * h ** 3
+    dens = sum(c * math.exp(-a * float(np.sum((q - p) ** 2))) for q in pos for c, a in zip(coef, expo))
+    assert abs(f[0] - dens) <= 1e-13 * dens
+    for col, l in enumerate([0, 1, 2, 3], start=1):
+        want = scale = 0.0
+        for (a, b, c) in oracle_mod.components(l):
+            P = oracle_mod.mcsh_poly(a, b, c)
+            S = sum(k * X ** pp * Y ** qq * Z ** ss for (pp, qq, ss), k in P.items())
+            wt = math.factorial(l) / (math.factorial(a) * math.factorial(b) * math.factorial(c))
+            mu = float(np.sum(S * base))
+            mu_abs = float(np.sum(np.abs(S) * base))
+            want += wt * mu * mu
+            scale += wt * mu_abs * mu_abs
+        assert abs(f[col] - want) <= 1e-8 * scale, (l, f[col], want)
+
+
+def test_point_density_matches_brute_force_images(oracle_mod):
+    # order -1 at points anywhere (inside, outside, far outside the cell):
+    # the density of every atom image within the cutoff, images enumerated
+    # by brute force
+    w = synth.workload("random64_box").replace(orders=[-1])
+    rng = np.random.default_rng(11)
+    pts = rng.uniform(-12.0, 22.0, (24, 3))
+    f = oracle_mod.point_features(w, pts, np.zeros(24, np.int32))[:, 0]
+    A = w.cells[0]
+    go = w.gauss_off
+    rc2 = w.cutoff * w.cutoff
+    for t, p in enumerate(pts):
+        rho = 0.0
+        for n1 in range(-4, 5):
+            for n2 in range(-4, 5):
+                for n3 in range(-4, 5):
+                    shift = (n1 * A[0] + n2 * A[1]) + n3 * A[2]
+                    D = (w.positions - p) + shift
+                    r2 = (D[:, 0] * D[:, 0] + D[:, 1] * D[:, 1]) + D[:, 2] * D[:, 2]
+                    for jj in np.nonzero(r2 < rc2)[0]:
+                        e = w.species[jj]
+                        rho += sum(w.gauss_coef[k] * math.exp(-w.gauss_exp[k] * r2[jj]) for k in range(go[e], go[e + 1]))
+        assert abs(f[t] - rho) <= 1e-12 * abs(rho), (t, f[t], rho)
+
+
+def test_point_features_special_points(oracle_mod):
+    # a point on an atom has that atom's features; a point beyond the cutoff
+    # of every atom of a cluster has zero features
+    w = synth.batched10k(n_struct=6)
+    atoms = np.array([0, int(w.atom_off[3]) + 1, int(w.atom_off[5])])
+    ps = np.searchsorted(w.atom_off, atoms, side="right") - 1
+    fa = oracle_mod.features(w, atoms)
+    fp = oracle_mod.point_features(w, w.positions[atoms], ps)
+    assert np.array_equal(fa, fp)
+    cl = next(s for s in range(w.n_struct) if not w.pbc[s].any())
+    far = w.positions[w.atom_off[cl]:w.atom_off[cl + 1]].max(0) + w.cutoff + 0.01
+    assert np.all(oracle_mod.point_features(w, far[None, :], [cl]) == 0.0)
