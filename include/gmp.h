@@ -75,8 +75,14 @@ typedef struct {
   const int32_t *orders;      /* each in {-1, 0, 1, ..., 6}, no repeats         */
   int32_t n_sigmas;           /* >= 1 when any order >= 0                       */
   const double *sigmas;       /* each > 0, Angstrom                             */
-  double cutoff;              /* > 0, Angstrom; hard cutoff |d| < cutoff        */
+  double cutoff;              /* Angstrom; hard cutoff |d| < cutoff.  <= 0:
+                                 derived from overlap_threshold (below)        */
   uint32_t flags;             /* GMP_FLAG_*                                     */
+  double overlap_threshold;   /* used when cutoff <= 0 (Examples: "overlap_threshold",
+                                 "the desired accuracy of the features"): the
+                                 cutoff is the smallest radius beyond which every
+                                 single-primitive contribution to any moment is
+                                 below this value (see gmp_cutoff)             */
 } gmp_params;
 
 /* Create a handle on CUDA device `device`: validates `params`, copies the
@@ -87,6 +93,17 @@ gmp_status gmp_create(const gmp_params *params, int device, gmp_handle *out);
 
 /* Number of features per atom F = (#orders >= 0) * n_sigmas + (#order -1). */
 gmp_status gmp_num_features(gmp_handle h, int32_t *F);
+
+/* The cutoff in use (Angstrom).  When it was derived from overlap_threshold
+ * t (PAPER Examples: the cutoff "will be inferred by the overlap_threshold
+ * setting"), it is the largest r at which some single-primitive bound still
+ * exceeds t:
+ *   order l >= 0, sigma s, primitive (c, alpha), g = alpha + 1/(2 s^2):
+ *     |c| N_s (pi/g)^(3/2) (alpha/g)^l sqrt(l! (2l-1)!!) r^l exp(-(alpha/(2 s^2 g)) r^2)
+ *     (the largest overlap of that primitive with any MCSH component of the
+ *     probe, since |S_c(d)| <= sqrt(l!(2l-1)!!) |d|^l);
+ *   order -1: |c| exp(-alpha r^2). */
+gmp_status gmp_cutoff(gmp_handle h, double *cutoff);
 
 /* Features of every atom (Examples: entry["features"]).
  * features [N, F] float32, order-major: column (o, s) = o * n_sigmas + s for
@@ -119,6 +136,25 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t *ato
                                   const int32_t *species, float *features, int64_t *jac_off,
                                   int32_t *jac_j, float *jac, int64_t cap, int64_t *nnz_out,
                                   void *stream);
+
+/* Features at reference points (PAPER Overview: the features can be
+ * computed at arbitrary reference points of a structure, not only at its
+ * atoms).  The probes are centred on each point; the neighbor set is every
+ * atom image of the point's structure with |(x_j - p) + n1 a1 + n2 a2 + n3 a3|
+ * < cutoff, decided in FP64 exactly as gmp_neighbors does for atoms (a point
+ * that coincides with an atom gets that atom's features).
+ *   point_off [S+1] int64 HOST array: structure s owns points
+ *     point_off[s] .. point_off[s+1]-1 (point_off[0] = 0);
+ *   points [n_points, 3] float64 raw Cartesian (any position, inside the
+ *     cell or not; periodic axes wrap as for atoms);
+ *   features [n_points, F] float32 out, columns as in gmp_featurize.
+ * points and features follow pos (device or host; with no atoms at all the
+ * features are zero).  A structure may own points and no atoms, or atoms and
+ * no points.  Synchronises `stream` once (to size the neighbor buffer). */
+gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                                const double *pos, const double *cell, const uint8_t *pbc,
+                                const int32_t *species, const int64_t *point_off,
+                                const double *points, float *features, void *stream);
 
 /* Exact neighbor images (for checking; the featurize calls build their own).
  * Pairs (i, j, n) with |(x_j - x_i) + n1 a1 + n2 a2 + n3 a3| < cutoff, the

@@ -27,7 +27,7 @@ GMP_OK = 0
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp",
-           "gmp_featurize_grad", "gmp_neighbors", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
+           "gmp_featurize_grad", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
            "gmp_sync", "gmp_profile", "gmp_profile_read",
            "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
 TUNING_CACHE = os.environ.get("GMP_TUNING_CACHE",
@@ -55,6 +55,7 @@ class _Params(C.Structure):
         ("sigmas", C.c_void_p),
         ("cutoff", C.c_double),
         ("flags", C.c_uint32),
+        ("overlap_threshold", C.c_double),
     ]
 
 
@@ -76,7 +77,9 @@ def load_library(path: str = LIB_PATH):
         L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
         L.gmp_featurize_grad.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_featurize_points.argtypes = common + [vp, vp, vp, vp]
         L.gmp_set_graph.argtypes = [vp, C.c_int]
+        L.gmp_cutoff.argtypes = [vp, C.POINTER(C.c_double)]
         L.gmp_tune.argtypes = common + [i32, C.POINTER(i64), vp]
         L.gmp_tuning_get.argtypes = [vp, C.POINTER(i32), i32]
         L.gmp_tuning_set.argtypes = [vp, C.POINTER(i32), i32]
@@ -125,11 +128,11 @@ class GMPFeaturizer:
     """
 
     def __init__(self, orders, sigmas, cutoff, n_gauss, gauss_coef, gauss_exp, device: int = 0,
-                 flags: int = 0):
+                 flags: int = 0, overlap_threshold: float = 1e-16):
         self._L = load_library()
         self.orders = [int(o) for o in orders]
         self.sigmas = [float(s) for s in sigmas]
-        self.cutoff = float(cutoff)
+        self.cutoff = float(cutoff) if cutoff else 0.0
         self.device = int(device)
         self._keep = dict(
             n_gauss=np.ascontiguousarray(n_gauss, np.int32),
@@ -143,12 +146,15 @@ class GMPFeaturizer:
                     gauss_coef=k["coef"].ctypes.data, gauss_exp=k["expo"].ctypes.data,
                     n_orders=len(self.orders), orders=k["orders"].ctypes.data,
                     n_sigmas=len(self.sigmas), sigmas=k["sigmas"].ctypes.data,
-                    cutoff=self.cutoff, flags=int(flags))
+                    cutoff=self.cutoff, flags=int(flags), overlap_threshold=float(overlap_threshold))
         h = C.c_void_p()
         st = self._L.gmp_create(C.byref(p), self.device, C.byref(h))
         if st != GMP_OK:
             raise GMPError(st, "gmp_create rejected the parameters (see stderr)")
         self._h = h
+        rc = C.c_double()
+        self._check(self._L.gmp_cutoff(self._h, C.byref(rc)))
+        self.cutoff = float(rc.value)  # derived from overlap_threshold when cutoff was not given
         F = C.c_int32()
         self._check(self._L.gmp_num_features(self._h, C.byref(F)))
         self.num_features = int(F.value)
@@ -267,6 +273,32 @@ class GMPFeaturizer:
                                                    _ptr(joff), _ptr(jj), _ptr(jac), cap, C.byref(nnz),
                                                    _stream_ptr(stream, on_dev)))
         return feat, joff, jj[:cap], jac[:cap]
+
+    def featurize_points(self, pos, species, atom_off, cell, pbc, points, point_off, stream=None):
+        """Features [n_points, F] float32 with the probes centred on reference
+        points (float64 [n_points, 3], same device as pos); structure s owns
+        points point_off[s]:point_off[s+1]."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        poff = np.ascontiguousarray(point_off, np.int64)
+        if poff.size != off.size:
+            raise ValueError("point_off needs one entry per structure plus one")
+        if isinstance(points, torch.Tensor):
+            if points.dtype != torch.float64 or not points.is_contiguous() or points.is_cuda != on_dev:
+                raise ValueError("points must be a contiguous float64 tensor on the same device as pos")
+            if not on_dev:
+                points = points.numpy()
+        else:
+            points = np.ascontiguousarray(points, np.float64)
+        NP = int(poff[-1])
+        if tuple(points.shape) != (NP, 3):
+            raise ValueError("points must be [point_off[-1], 3]")
+        feat = self._alloc((NP, self.num_features), torch.float32, on_dev, pos)
+        self._check(self._L.gmp_featurize_points(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                                 pbc.ctypes.data, _ptr(species), poff.ctypes.data, _ptr(points),
+                                                 _ptr(feat), _stream_ptr(stream, on_dev)))
+        return feat
 
     def neighbors(self, pos, species, atom_off, cell, pbc, stream=None):
         """Exact neighbor images: (nbr_off [N+1], nbr_j [P], nbr_shift [P,3])."""

@@ -84,6 +84,7 @@ struct gmp_ctx {
   DevBuf ktab;   // FP64 radial constants [n_el][n_sigmas][kmax][3] for the refinement kernel
   DevBuf flagq;  // queued ill-conditioned features
   DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp;
+  DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
   int64_t P = 0;  // pairs of the last neighbor build
   int max_m = 0;
   // pinned host scratch for small readbacks
@@ -173,6 +174,51 @@ bool inv3(const double* A, double* Ai) {
 
 // Validates the batch description and uploads per-structure data when it
 // changed since the previous call.
+// Largest r where term(r) > t, for term(r) = a r^l exp(-b r^2) (a, b > 0):
+// increasing up to r* = sqrt(l / (2b)), decreasing beyond; bisection on
+// the decreasing branch.
+double term_radius(double a, int l, double b, double t) {
+  auto term = [&](double r) { return a * std::pow(r, l) * std::exp(-b * r * r); };
+  const double rstar = l > 0 ? std::sqrt(l / (2.0 * b)) : 0.0;
+  if (term(rstar) <= t) return 0.0;
+  double lo = rstar, hi = std::max(2.0 * rstar, 1.0);
+  while (term(hi) > t) hi *= 2.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-12 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    (term(mid) > t ? lo : hi) = mid;
+  }
+  return hi;
+}
+
+// Cutoff from the overlap threshold t (largest radius of any single
+// primitive's bound above t; see gmp_cutoff in gmp.h).
+double derived_cutoff(const gmp_ctx& h, double t) {
+  double rc = 0.0;
+  int64_t off = 0;
+  for (int e = 0; e < h.n_el; ++e) {
+    for (int q = 0; q < h.n_gauss[e]; ++q) {
+      const double a = h.alpha[off + q], c = std::fabs(h.coef[off + q]);
+      for (int l : h.orders) {
+        if (l < 0) {
+          rc = std::max(rc, term_radius(c, 0, a, t));
+          continue;
+        }
+        double lf = 1.0, df = 1.0;
+        for (int k = 2; k <= l; ++k) lf *= k;
+        for (int k = 2 * l - 1; k > 1; k -= 2) df *= k;
+        for (double sig : h.sigmas) {
+          const double beta = 1.0 / (2.0 * sig * sig), g = a + beta;
+          const double amp = c * std::pow(2.0 * M_PI * sig * sig, -1.5) * std::pow(M_PI / g, 1.5) *
+                             std::pow(a / g, l) * std::sqrt(lf * df);
+          rc = std::max(rc, term_radius(amp, l, a * beta / g, t));
+        }
+      }
+    }
+    off += h.n_gauss[e];
+  }
+  return rc;
+}
+
 gmp_status upload_structures(gmp_ctx* h, int32_t S, const int64_t* atom_off, const double* cell,
                              const uint8_t* pbc, cudaStream_t st) {
   if (S < 1 || !atom_off) return fail(h, GMP_ERR_INVALID_ARG, "n_struct must be >= 1 with atom_off");
@@ -272,18 +318,11 @@ cudaError_t prof_mark(gmp_ctx* h, int stage, bool begin, cudaStream_t st) {
   return r;
 }
 
-// Binning + exact neighbor lists into h->pairs / h->nbr_off.  Synchronises
-// `st` once (to size the pair buffer).
-gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
-                           int64_t N, cudaStream_t st, bool sorted, bool capture = false) {
+// Checks, fractional coordinates and the cell-list bins of the N atoms.
+gmp_status bin_atoms(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species, int64_t N,
+                     int64_t n_centers, cudaStream_t st) {
   int64_t* L = &h->launches;
-  if (!capture) h->graph_valid = false;  // buffers may move: a captured graph is stale
-  GMP_CK(prof_mark(h, 0, true, st), "profile");
   uint32_t* d_err = h->scalars.as<uint32_t>();
-  int32_t* d_maxm = reinterpret_cast<int32_t*>(d_err + 1);
-  // the error word is cleared after it is read (below), so a condition
-  // raised after the read of the previous call is reported here
-  GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
   GMP_CK(h->atom_xh.ensure(sizeof(float4) * N), "atom_xh");
   GMP_CK(h->atom_xl.ensure(sizeof(float4) * N), "atom_xl");
   GMP_CK(h->atom_u.ensure(sizeof(GmpD4) * N), "atom_u");
@@ -294,9 +333,9 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   GMP_CK(h->bin_cursor.ensure(sizeof(int32_t) * h->n_bins), "bin_cursor");
   GMP_CK(h->bin_start.ensure(sizeof(int32_t) * (h->n_bins + 1)), "bin_start");
   GMP_CK(h->bin_y.ensure(sizeof(float4) * N), "bin_y");
-  GMP_CK(h->counts.ensure(sizeof(int64_t) * N), "counts");
-  GMP_CK(h->nbr_off.ensure(sizeof(int64_t) * (N + 1)), "nbr_off");
-  const int64_t scan_n = std::max<int64_t>(N, h->n_bins);
+  GMP_CK(h->counts.ensure(sizeof(int64_t) * n_centers), "counts");
+  GMP_CK(h->nbr_off.ensure(sizeof(int64_t) * (n_centers + 1)), "nbr_off");
+  const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(N, n_centers), h->n_bins);
   GMP_CK(h->scan_tmp.ensure(gmp_scan_tmp_bytes(scan_n)), "scan_tmp");
 
   GMP_CK(gmp_launch_neighbors_prepare(h->structs.as<GmpStruct>(), S, h->struct_of.as<int32_t>(), N, h->cutoff,
@@ -310,26 +349,38 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
                          h->atom_y.as<float4>(), h->bin_y.as<float4>(), h->atom_u.as<GmpD4>(), h->scan_tmp.p,
                          h->scan_tmp.bytes, st, h->sm_count, L),
          "bins");
-  GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(),
-                                  N, h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                                  h->atom_rng.as<int4>(), h->atom_y.as<float4>(), h->bin_start.as<int32_t>(),
+  return GMP_OK;
+}
+
+// Exact neighbor lists of the NC centers C over the binned atoms into
+// h->pairs / h->nbr_off.  Synchronises `st` once (to size the pair buffer)
+// unless capturing.
+gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const double* pos, cudaStream_t st,
+                          bool sorted, bool capture) {
+  int64_t* L = &h->launches;
+  uint32_t* d_err = h->scalars.as<uint32_t>();
+  int32_t* d_maxm = reinterpret_cast<int32_t*>(d_err + 1);
+  // the error word is cleared after it is read (below), so a condition
+  // raised after the read of the previous call is reported here
+  GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
+  GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
+                                  h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
                                   h->bin_y.as<float4>(), h->counts.as<int64_t>(), nullptr, nullptr, 0, 0, d_maxm,
                                   d_err, st, h->sm_count, L),
          "neighbor count");
-  GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), N, h->scan_tmp.p, st, L), "scan");
+  GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), NC, h->scan_tmp.p, st, L), "scan");
   if (capture) {
     // capacities fixed at capture time; the fill and compute kernels skip
     // (and flag) centers beyond them
-    GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(),
-                                    h->struct_of.as<int32_t>(), N, h->cutoff, pos, h->atom_xh.as<float4>(),
-                                    h->atom_xl.as<float4>(), h->atom_rng.as<int4>(), h->atom_y.as<float4>(),
+    GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
+                                    h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                                     h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), nullptr,
                                     h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->cap_pairs, h->cap_keys,
                                     d_maxm, d_err, st, h->sm_count, L),
            "neighbor fill");
     return GMP_OK;
   }
-  GMP_CK(cudaMemcpyAsync(h->h_small, h->nbr_off.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read P");
+  GMP_CK(cudaMemcpyAsync(h->h_small, h->nbr_off.as<int64_t>() + NC, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read P");
   GMP_CK(cudaMemcpyAsync(h->h_small + 1, d_err, 8, cudaMemcpyDeviceToHost, st), "read err");
   GMP_CK(cudaStreamSynchronize(st), "neighbor sync");
   const uint32_t w = (uint32_t)(h->h_small[1] & 0xffffffffu);
@@ -345,13 +396,26 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   if ((size_t)keys * 8 > 200 * 1024)
     return fail(h, GMP_ERR_CAPACITY, "a center has " + std::to_string(maxm) + " neighbor images (limit 25600)");
   GMP_CK(h->pairs.ensure(sizeof(GmpPair) * (h->P > 0 ? h->P : 1)), "pairs");
-  GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(),
-                                  h->struct_of.as<int32_t>(), N, h->cutoff, pos, h->atom_xh.as<float4>(),
-                                  h->atom_xl.as<float4>(), h->atom_rng.as<int4>(), h->atom_y.as<float4>(),
+  GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
+                                  h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                                   h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
                                   nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->P, keys, d_maxm,
                                   d_err, st, h->sm_count, L),
          "neighbor fill");
+  return GMP_OK;
+}
+
+// Binning + exact neighbor lists of every atom into h->pairs / h->nbr_off.
+// Synchronises `st` once (to size the pair buffer) unless capturing.
+gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
+                           int64_t N, cudaStream_t st, bool sorted, bool capture = false) {
+  if (!capture) h->graph_valid = false;  // buffers may move: a captured graph is stale
+  GMP_CK(prof_mark(h, 0, true, st), "profile");
+  gmp_status r = bin_atoms(h, S, pos, species, N, N, st);
+  if (r != GMP_OK) return r;
+  const GmpCenters C{h->struct_of.as<int32_t>(), pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
+                     h->atom_rng.as<int4>(), h->atom_y.as<float4>()};
+  if ((r = neighbor_lists(h, C, N, pos, st, sorted, capture)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 0, false, st), "profile");
   return GMP_OK;
 }
@@ -387,10 +451,13 @@ gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
 }
 
 // FP64 recomputation of the queued features.
-gmp_status refine(gmp_ctx* h, int64_t N, const double* pos, float* features, cudaStream_t st) {
+// Centers are the atoms unless center_pos / center_struct give reference points.
+gmp_status refine(gmp_ctx* h, int64_t N, const double* pos, float* features, cudaStream_t st,
+                  const double* center_pos = nullptr, const int32_t* center_struct = nullptr) {
   GMP_CK(gmp_launch_refine(h->flagq.as<unsigned long long>(),
                            reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3), flag_capacity(N),
-                           features, h->F, pos, h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
+                           features, h->F, pos, center_pos ? center_pos : pos,
+                           center_struct ? center_struct : h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
                            h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->ktab.as<double>(),
                            (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->scalars.as<uint32_t>(),
                            h->sm_count, st, &h->launches),
@@ -510,7 +577,9 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
   };
   if (p->n_elements < 1 || !p->n_gauss || !p->gauss_coef || !p->gauss_exp) return bad("density tables missing");
   if (p->n_orders < 1 || p->n_orders > 8 || !p->orders) return bad("orders: 1..8 entries required");
-  if (!(p->cutoff > 0.0) || !std::isfinite(p->cutoff)) return bad("cutoff must be > 0");
+  if (!std::isfinite(p->cutoff)) return bad("cutoff must be finite");
+  if (!(p->cutoff > 0.0) && !(p->overlap_threshold > 0.0 && std::isfinite(p->overlap_threshold)))
+    return bad("cutoff <= 0 needs overlap_threshold > 0");
   h->n_el = p->n_elements;
   int64_t tot = 0;
   for (int e = 0; e < p->n_elements; ++e) {
@@ -544,7 +613,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     }
   }
   if (h->sigmas.size() > 1024) return bad("at most 1024 sigmas");
-  h->cutoff = p->cutoff;
+  h->cutoff = p->cutoff > 0.0 ? p->cutoff : derived_cutoff(*h, p->overlap_threshold);
+  if (!(h->cutoff > 0.0)) return bad("overlap_threshold leaves no neighbor within reach (cutoff 0)");
   h->flags = p->flags;
   const int nsig = (int)h->sigmas.size();
   h->F = (dens ? 1 : 0);
@@ -679,6 +749,12 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
   if (cudaMallocHost((void**)&h->h_small, 64) != cudaSuccess) { cudaGetLastError(); return bad("pinned alloc failed"); }
   if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return bad("event"); }
   *out = h;
+  return GMP_OK;
+}
+
+gmp_status gmp_cutoff(gmp_handle h, double* cutoff) {
+  if (!h || !cutoff) return GMP_ERR_INVALID_ARG;
+  *cutoff = h->cutoff;
   return GMP_OK;
 }
 
@@ -887,6 +963,79 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
     GMP_CK(cudaStreamSynchronize(st), "sync");
     tmp_jac.release();
     tmp_jj.release();
+  }
+  return GMP_OK;
+}
+
+gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                                const double* cell, const uint8_t* pbc, const int32_t* species,
+                                const int64_t* point_off, const double* points, float* features, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (!point_off || point_off[0] != 0) return fail(h, GMP_ERR_INVALID_ARG, "point_off with point_off[0] = 0 is required");
+  for (int s = 0; s < n_struct; ++s)
+    if (point_off[s + 1] < point_off[s]) return fail(h, GMP_ERR_INVALID_ARG, "point_off must be non-decreasing");
+  const int64_t NP = point_off[n_struct];
+  if (NP > (int64_t)INT32_MAX / 2) return fail(h, GMP_ERR_INVALID_ARG, "too many points");
+  if (NP == 0) return GMP_OK;
+  if (!points || !features) return fail(h, GMP_ERR_INVALID_ARG, "points and features are required");
+  const bool host = !is_device_ptr(points);
+  if (host != !is_device_ptr(features)) return fail(h, GMP_ERR_INVALID_ARG, "points and features must both be device or both host pointers");
+  if (N > 0 && host != !is_device_ptr(pos)) return fail(h, GMP_ERR_INVALID_ARG, "points and pos must both be device or both host pointers");
+  h->graph_valid = false;  // shares the neighbor buffers with the graph-captured calls
+  Io io;
+  if (N > 0 && (r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  const double* pts = points;
+  float* feat = features;
+  if (host) {
+    GMP_CK(h->stage_pts.ensure(sizeof(double) * 3 * NP), "stage points");
+    GMP_CK(cudaMemcpyAsync(h->stage_pts.p, points, sizeof(double) * 3 * NP, cudaMemcpyHostToDevice, st), "h2d points");
+    pts = h->stage_pts.as<double>();
+    GMP_CK(h->stage_feat.ensure(sizeof(float) * NP * h->F), "stage features");
+    feat = h->stage_feat.as<float>();
+  }
+  if (N == 0) {
+    GMP_CK(cudaMemsetAsync(feat, 0, sizeof(float) * NP * h->F, st), "zero features");
+  } else {
+    GMP_CK(h->pt_off.ensure(sizeof(int64_t) * (n_struct + 1)), "point_off");
+    GMP_CK(h->pt_struct.ensure(sizeof(int32_t) * NP), "point struct");
+    GMP_CK(h->pt_xh.ensure(sizeof(float4) * NP), "point xh");
+    GMP_CK(h->pt_xl.ensure(sizeof(float4) * NP), "point xl");
+    GMP_CK(h->pt_rng.ensure(sizeof(int4) * NP), "point ranges");
+    GMP_CK(h->pt_y.ensure(sizeof(float4) * NP), "point y");
+    GMP_CK(cudaMemcpyAsync(h->pt_off.p, point_off, sizeof(int64_t) * (n_struct + 1), cudaMemcpyHostToDevice, st),
+           "upload point_off");
+    GMP_CK(gmp_launch_struct_of(h->pt_off.as<int64_t>(), n_struct, h->pt_struct.as<int32_t>(), st, &h->launches),
+           "point struct");
+    GMP_CK(prof_mark(h, 0, true, st), "profile");
+    if ((r = bin_atoms(h, n_struct, io.pos, io.species, N, NP, st)) != GMP_OK) return r;
+    GMP_CK(gmp_launch_point_prepare(h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->pt_struct.as<int32_t>(), NP,
+                                    pts, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(), h->pt_rng.as<int4>(),
+                                    h->pt_y.as<float4>(), h->scalars.as<uint32_t>(), st, h->sm_count, &h->launches),
+           "point prepare");
+    const GmpCenters C{h->pt_struct.as<int32_t>(), pts, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(),
+                       h->pt_rng.as<int4>(), h->pt_y.as<float4>()};
+    if ((r = neighbor_lists(h, C, NP, io.pos, st, false, false)) != GMP_OK) return r;
+    GMP_CK(prof_mark(h, 0, false, st), "profile");
+    if ((r = begin_compute(h, NP, st)) != GMP_OK) return r;
+    GMP_CK(prof_mark(h, 1, true, st), "profile");
+    for (size_t g = 0; g < h->passes.size(); ++g) {
+      gmpk::KParams K = base_params(h, h->passes[g], (int)g, NP);
+      K.features = feat;
+      GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_FORWARD, h->passes[g].NS, K, h->passes[g].fwd, st,
+                            h->sm_count, &h->launches),
+             "forward");
+    }
+    GMP_CK(prof_mark(h, 1, false, st), "profile");
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((r = refine(h, NP, io.pos, feat, st, pts, h->pt_struct.as<int32_t>())) != GMP_OK) return r;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+  }
+  if (host) {
+    GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * NP * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
+    GMP_CK(cudaStreamSynchronize(st), "sync");
   }
   return GMP_OK;
 }

@@ -173,34 +173,42 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
 size_t gmp_scan_tmp_bytes(int64_t n);
 cudaError_t gmp_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp,
                                    cudaStream_t stream, int64_t* launches);
+// The points that neighbor lists are built around: the atoms themselves or
+// reference points (gmp_featurize_points).  Per center: structure id, FP64
+// position [3], double-float split (xl.w = packed wrap of the fractional
+// coordinates), scanned bin range and wrapped FP32 position (k_ranges).
+struct GmpCenters {
+  const int32_t* sid;
+  const double* pos;
+  const float4* xh;
+  const float4* xl;
+  const int4* rng;
+  const float4* y;
+};
+// Per reference point: the GmpCenters fields above from its FP64 position
+// and structure (after the atom grid of each structure is built).
+cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* d_grid,
+                                     const int32_t* point_struct, int64_t n_points, const double* points,
+                                     float4* pt_xh, float4* pt_xl, int4* pt_rng, float4* pt_y,
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
 // fill: 0 = count only, 1 = records in enumeration order (deterministic),
-// 2 = records sorted by (neighbor atom, image)
+// 2 = records sorted by (neighbor atom, image).  Centers C [N]; neighbors
+// are the binned atoms (pos, atom_xh, atom_xl).
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
-                                     const int32_t* d_struct_of, int64_t N, double cutoff,
+                                     const GmpCenters& C, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
+                                     const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
-cudaError_t gmp_launch_forward(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
-                               const GmpPair* pairs, float* features, float* mu_out,
-                               int32_t* work_counter, cudaStream_t stream, int sm_count,
-                               int64_t* launches);
-cudaError_t gmp_launch_vjp(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
-                           const GmpPair* pairs, const float* grad_feat, float* features,
-                           double* grad_acc, int32_t* work_counter, cudaStream_t stream,
-                           int sm_count, int64_t* launches);
-cudaError_t gmp_launch_jacobian(const GmpPass& pass, int64_t N, const int64_t* nbr_off,
-                                const GmpPair* pairs, const int64_t* jac_off, int32_t* jac_j,
-                                float* jac, float* features, int32_t* work_counter,
-                                cudaStream_t stream, int sm_count, int64_t* launches);
 cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
                                       int64_t* counts, cudaStream_t stream, int sm_count,
                                       int64_t* launches);
 cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,
                                    cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
-                              float* features, int F, const double* pos, const int32_t* struct_of,
+                              float* features, int F, const double* pos, const double* center_pos,
+                              const int32_t* center_struct,
                               const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
                               const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
                               cudaStream_t stream, int64_t* launches);

@@ -163,6 +163,7 @@ __device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kma
       R[u][l] = 0.0f;
       if (DERIV) Rd[u][l] = 0.0f;
     }
+#pragma unroll 2
   for (int q = 0; q < kmax; ++q) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -175,11 +176,11 @@ __device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kma
         A[4] = a1.x; A[5] = a1.y; A[6] = a1.z; A[7] = a1.w;
       }
       const float E = gmp_exp_neg(h.x, h.y, r2h, r2l);
-      const float mb = -h.z;
+      const float Ed = __fmul_rn(-h.z, E);  // d exp(-b r^2) / d r^2
 #pragma unroll
       for (int l = 0; l <= L; ++l) {
         R[u][l] = __fmaf_rn(A[l], E, R[u][l]);
-        if (DERIV) Rd[u][l] = __fmaf_rn(mb, __fmul_rn(A[l], E), Rd[u][l]);
+        if (DERIV) Rd[u][l] = __fmaf_rn(A[l], Ed, Rd[u][l]);
       }
     }
   }

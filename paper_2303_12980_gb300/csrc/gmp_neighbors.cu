@@ -156,12 +156,16 @@ __global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
   // and FP32 r^2 < (rc - 2 delta)^2 (1 - 2^-20) means |d| < rc, both by a
   // margin far above the FP64 rounding of the defining expression; only the
   // shell in between needs the exact test.
+  // Centers need not be atoms (reference points): along a non-periodic axis
+  // a center scans some bin only if its coordinate lies within reach + one
+  // bin width of the atoms' range, which the bound on |y| covers.
   double Y = 0.0, Sh = 0.0;
   for (int c = 0; c < 3; ++c) {
     double yc = 0.0, sc = 0.0;
     for (int k = 0; k < 3; ++k) {
       double a = fabs(st.A[3 * k + c]);
-      double uk = fmax(fabs(g.umin[k]), fabs(umax[k])) + 1.0;
+      double uk = fmax(fabs(g.umin[k]), fabs(umax[k])) + 1.0 +
+                  (st.periodic[k] ? 0.0 : st.reach[k] + 2.0 * g.binw[k]);
       yc += uk * a;
       sc += (ceil(st.reach[k]) + 2.0) * a;
     }
@@ -220,6 +224,33 @@ __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __
   }
 }
 
+// Bins a center at wrapped fractional coordinates u can reach, and its
+// wrapped FP32 position.
+__device__ __forceinline__ void center_range(const GmpStruct& st, const GmpGrid& g, const double* u,
+                                             int4& rng_out, float4& y_out) {
+  int lo[3], span[3];
+  for (int k = 0; k < 3; ++k) {
+    const double lo_f = (u[k] - st.reach[k] - g.umin[k]) * g.inv_binw[k];
+    const double hi_f = (u[k] + st.reach[k] - g.umin[k]) * g.inv_binw[k];
+    int l0, h0;
+    if (st.periodic[k]) {
+      l0 = (int)floor(lo_f - 1e-7);
+      h0 = (int)floor(hi_f + 1e-7);
+    } else {
+      // a reference point may lie far outside the atoms' range: clamp in
+      // FP64 before converting (an empty range comes out as h0 < l0)
+      l0 = (int)fmin(fmax(floor(lo_f - 1e-7), 0.0), (double)g.nb[k]);
+      h0 = (int)fmax(fmin(floor(hi_f + 1e-7), (double)(g.nb[k] - 1)), -1.0);
+    }
+    lo[k] = l0;
+    span[k] = max(h0 - l0 + 1, 0);
+  }
+  float y[3];
+  for (int c = 0; c < 3; ++c) y[c] = (float)(u[0] * st.A[c] + u[1] * st.A[3 + c] + u[2] * st.A[6 + c]);
+  rng_out = make_int4(lo[0], lo[1], lo[2], span[0] | (span[1] << 10) | (span[2] << 20));
+  y_out = make_float4(y[0], y[1], y[2], 0.0f);
+}
+
 // Per atom: the bins its cutoff sphere can touch, lo[k] .. lo[k]+span[k]-1
 // (periodic axes unwrapped), and its wrapped FP32 position.  Once per atom,
 // so the neighbor kernels need no FP64 set-up.  atom_u is overwritten with
@@ -234,22 +265,49 @@ __global__ void k_ranges(const GmpStruct* __restrict__ S, const GmpGrid* __restr
     const GmpGrid& g = G[s];
     const GmpD4 u4 = atom_u[a];
     const double u[3] = {u4.x, u4.y, u4.z};
-    int lo[3], span[3];
-    for (int k = 0; k < 3; ++k) {
-      const double lo_f = (u[k] - st.reach[k] - g.umin[k]) * g.inv_binw[k];
-      const double hi_f = (u[k] + st.reach[k] - g.umin[k]) * g.inv_binw[k];
-      int l0 = (int)floor(lo_f - 1e-7), h0 = (int)floor(hi_f + 1e-7);
-      if (!st.periodic[k]) {
-        l0 = max(l0, 0);
-        h0 = min(h0, g.nb[k] - 1);
-      }
-      lo[k] = l0;
-      span[k] = max(h0 - l0 + 1, 0);
+    center_range(st, g, u, atom_rng[a], atom_y[a]);
+  }
+}
+
+// Per reference point: the checks, wrap and double-float split of
+// k_prepare and the bin range of k_ranges, in the structure's atom grid.
+__global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
+                                const int32_t* __restrict__ point_struct, int64_t n, const double* __restrict__ pts,
+                                float4* __restrict__ pt_xh, float4* __restrict__ pt_xl, int4* __restrict__ pt_rng,
+                                float4* __restrict__ pt_y, uint32_t* __restrict__ err) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int s = point_struct[a];
+    const GmpStruct& st = S[s];
+    double x[3] = {pts[3 * a], pts[3 * a + 1], pts[3 * a + 2]};
+    if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+      atomicOr(err, GMP_DEV_NONFINITE);
+      x[0] = x[1] = x[2] = 0.0;
     }
-    float y[3];
-    for (int c = 0; c < 3; ++c) y[c] = (float)(u[0] * st.A[c] + u[1] * st.A[3 + c] + u[2] * st.A[6 + c]);
-    atom_rng[a] = make_int4(lo[0], lo[1], lo[2], span[0] | (span[1] << 10) | (span[2] << 20));
-    atom_y[a] = make_float4(y[0], y[1], y[2], 0.0f);
+    double u[3];
+    int w[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
+      if (st.periodic[k]) {
+        double f = floor(u[k]);
+        if (fabs(f) > 500.0) {
+          atomicOr(err, GMP_DEV_SHIFT_RANGE);
+          f = 0.0;
+        }
+        w[k] = (int)f;
+        u[k] -= f;
+        if (u[k] >= 1.0) { u[k] -= 1.0; w[k] += 1; }
+        if (u[k] < 0.0) u[k] = 0.0;
+      }
+    }
+    float h[3], l[3];
+    for (int k = 0; k < 3; ++k) {
+      h[k] = (float)x[k];
+      l[k] = (float)(x[k] - (double)h[k]);
+    }
+    pt_xh[a] = make_float4(h[0], h[1], h[2], 0.0f);
+    pt_xl[a] = make_float4(l[0], l[1], l[2], __int_as_float(pack_wrap(w[0], w[1], w[2])));
+    center_range(st, G[s], u, pt_rng[a], pt_y[a]);
   }
 }
 
@@ -356,19 +414,19 @@ __device__ __forceinline__ void df_disp(const float4& xhi, const float4& xli, co
 }
 
 // The FP64 expression of the neighbor definition, evaluated exactly as written.
-__device__ __noinline__ bool fp64_within(const double* __restrict__ pos, int64_t i, int64_t j,
-                                         const GmpStruct& st, const int* n, double rc2) {
+__device__ __noinline__ bool fp64_within(const double* __restrict__ pos, const double* __restrict__ xi,
+                                         int64_t j, const GmpStruct& st, const int* n, double rc2) {
   double d[3];
   for (int c = 0; c < 3; ++c) {
     double sh = __dadd_rn(__dadd_rn(__dmul_rn((double)n[0], st.A[c]), __dmul_rn((double)n[1], st.A[3 + c])),
                           __dmul_rn((double)n[2], st.A[6 + c]));
-    d[c] = __dadd_rn(__dsub_rn(pos[3 * j + c], pos[3 * i + c]), sh);
+    d[c] = __dadd_rn(__dsub_rn(pos[3 * j + c], xi[c]), sh);
   }
   double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
   return r2 < rc2;
 }
 
-__device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, int64_t i, int64_t j,
+__device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, const double* __restrict__ xi, int64_t j,
                                              const float4& xhi, const float4& xli, const float4& xhj,
                                              const float4& xlj, const GmpStruct& st, const int* n,
                                              float rc2hi, float rc2lo, double rc2, float cutoff) {
@@ -380,7 +438,7 @@ __device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, int
   const float tol = ldexpf((mag + cutoff + 1.0f) * (cutoff + 1.0f) * 16.0f, -36);
   if (diff.hi < -tol) return true;
   if (diff.hi > tol) return false;
-  return fp64_within(pos, i, j, st, n, rc2);
+  return fp64_within(pos, xi, j, st, n, rc2);
 }
 
 // Warp per center.  fill = 0: count exact neighbors; fill = 1: write the
@@ -388,10 +446,9 @@ __device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, int
 // order within a cell: deterministic); fill = 2: the same, sorted by
 // (neighbor atom, image) first.
 __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
-                            const int32_t* __restrict__ struct_of, int64_t N, float cutoff,
+                            const GmpCenters C, int64_t N, float cutoff,
                             float rc2hi, float rc2lo, double rc2, const double* __restrict__ pos,
                             const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                            const int4* __restrict__ atom_rng, const float4* __restrict__ atom_y,
                             const int32_t* __restrict__ bin_start, const float4* __restrict__ bin_y,
                             int64_t* __restrict__ counts, const int64_t* __restrict__ offsets,
                             GmpPair* __restrict__ pairs, int64_t pair_cap, int max_keys,
@@ -403,7 +460,7 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
   if (i >= N) return;
   unsigned long long* keys = sh_keys + (size_t)wib * max_keys;
 
-  const int s = struct_of[i];
+  const int s = C.sid[i];
   const GmpStruct& st = S[s];
   const GmpGrid& g = G[s];
   int nb[3], per[3];
@@ -414,13 +471,14 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
   for (int k = 0; k < 9; ++k) ahi[k] = st.Ahi[k];
   const int64_t bin_base = st.bin_base;
   const float p2 = st.prescreen2, q2 = st.inside2;
-  const float4 xhi = atom_xh[i], xli = atom_xl[i];
+  const float4 xhi = C.xh[i], xli = C.xl[i];
+  const double* xi = C.pos + 3 * i;
   int wi[3];
   gmp_unpack_shift(__float_as_int(xli.w), wi);
-  const int4 rg = atom_rng[i];
+  const int4 rg = C.rng[i];
   const int lo[3] = {rg.x, rg.y, rg.z};
   const int span[3] = {rg.w & 1023, (rg.w >> 10) & 1023, (rg.w >> 20) & 1023};
-  const float4 yi4 = atom_y[i];
+  const float4 yi4 = C.y[i];
   const float yi[3] = {yi4.x, yi4.y, yi4.z};
   const int total = span[0] * span[1] * span[2];
   int count = 0;   // per lane (count pass) / per warp (fill passes)
@@ -471,7 +529,7 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
           acc = true;
           if (r2 >= q2) {  // boundary shell: exact decision
             const float4 xhj = atom_xh[j], xlj = atom_xl[j];
-            acc = exact_accept(pos, i, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff);
+            acc = exact_accept(pos, xi, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff);
           }
           if (acc && (abs(n[0]) >= 512 || abs(n[1]) >= 512 || abs(n[2]) >= 512)) {
             atomicOr(err, GMP_DEV_SHIFT_RANGE);  // reported after the count pass
@@ -643,10 +701,21 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
   return cudaGetLastError();
 }
 
+cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* d_grid,
+                                     const int32_t* point_struct, int64_t n_points, const double* points,
+                                     float4* pt_xh, float4* pt_xl, int4* pt_rng, float4* pt_y,
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
+  if (n_points <= 0) return cudaSuccess;
+  k_point_prepare<<<grid_for(n_points, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, point_struct, n_points,
+                                                                         points, pt_xh, pt_xl, pt_rng, pt_y, d_err);
+  ++*launches;
+  return cudaGetLastError();
+}
+
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
-                                     const int32_t* d_struct_of, int64_t N, double cutoff,
+                                     const GmpCenters& C, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const int4* atom_rng, const float4* atom_y, const int32_t* bin_start,
+                                     const int32_t* bin_start,
                                      const float4* bin_y, int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
@@ -666,9 +735,9 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
     }
   }
   const unsigned blocks = (unsigned)((N + warps - 1) / warps);
-  k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, d_struct_of, N,
+  k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, C, N,
                                                     (float)cutoff, rc2hi, rc2lo, rc2, pos, atom_xh,
-                                                    atom_xl, atom_rng, atom_y, bin_start, bin_y, counts,
+                                                    atom_xl, bin_start, bin_y, counts,
                                                     offsets, pairs, pair_cap, max_keys, d_maxm, d_err);
   ++*launches;
   return cudaGetLastError();

@@ -181,10 +181,10 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
   if (e == cudaSuccess)
     e = gmp_launch_bins(d_st, d_grid, d_struct_of, n_atoms, n_bins, d_bin, d_bcount, d_bstart, d_bcursor, d_rng,
                         d_ay, d_by, d_u, d_scan, Layout::scan_bytes, st, sm_count, &launches);
+  const GmpCenters centers{d_struct_of, pos, d_xh, d_xl, d_rng, d_ay};
   if (e == cudaSuccess)
-    e = gmp_launch_neighbor_pass(0, d_st, d_grid, d_struct_of, n_atoms, cutoff, pos, d_xh, d_xl, d_rng, d_ay,
-                                 d_bstart, d_by, counts, nullptr, nullptr, 0, 0, d_maxm, d_err, st, sm_count,
-                                 &launches);
+    e = gmp_launch_neighbor_pass(0, d_st, d_grid, centers, n_atoms, cutoff, pos, d_xh, d_xl, d_bstart, d_by,
+                                 counts, nullptr, nullptr, 0, 0, d_maxm, d_err, st, sm_count, &launches);
   uint32_t w = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d_err, sizeof(w), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -4,7 +4,8 @@
 // cancellation-free scale of its moments (near-symmetric environments make
 // l >= 1 moments cancel) loses relative accuracy in FP32 in proportion to
 // sqrt(scale / f).  The forward kernels queue such (center, order, sigma)
-// entries; this kernel recomputes each of them from the FP64 positions:
+// entries; this kernel recomputes each of them from the FP64 positions
+// (center_pos: the atoms, or the reference points of gmp_featurize_points):
 // the displacement by the neighbor definition's own FP64 expression, the
 // Gaussian overlap radial factor with FP64 exp, the MCSH components by the
 // same recurrences in double, and the invariant in double.
@@ -15,7 +16,8 @@ namespace {
 
 __global__ void k_refine(const unsigned long long* __restrict__ flags, const int32_t* __restrict__ count,
                          int64_t cap, float* __restrict__ features, int F, const double* __restrict__ pos,
-                         const int32_t* __restrict__ struct_of, const GmpStruct* __restrict__ S,
+                         const double* __restrict__ cpos, const int32_t* __restrict__ cstruct,
+                         const GmpStruct* __restrict__ S,
                          const int64_t* __restrict__ nbr_off, const GmpPair* __restrict__ pairs,
                          const double* __restrict__ ktab, int nsig_total, int kmax, uint32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
@@ -32,7 +34,7 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
     const int l = (int)((e >> 24) & 15);
     const int sig = (int)((e >> 12) & 4095);
     const int col = (int)(e & 4095);
-    const GmpStruct& st = S[struct_of[i]];
+    const GmpStruct& st = S[cstruct[i]];
     double mu[13];
     for (int k = 0; k < 13; ++k) mu[k] = 0.0;
     const int64_t p0 = nbr_off[i], p1 = nbr_off[i + 1];
@@ -44,7 +46,7 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
       for (int c = 0; c < 3; ++c) {
         const double sh = __dadd_rn(__dadd_rn(__dmul_rn((double)nn[0], st.A[c]), __dmul_rn((double)nn[1], st.A[3 + c])),
                                     __dmul_rn((double)nn[2], st.A[6 + c]));
-        d[c] = __dadd_rn(__dsub_rn(pos[3 * (int64_t)pr.j + c], pos[3 * i + c]), sh);
+        d[c] = __dadd_rn(__dsub_rn(pos[3 * (int64_t)pr.j + c], cpos[3 * i + c]), sh);
       }
       const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
       // radial factor: sum_q Kd (alpha/gamma)^l exp(-(alpha beta / gamma) r^2)
@@ -68,11 +70,11 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
 }  // namespace
 
 cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
-                              float* features, int F, const double* pos, const int32_t* struct_of,
-                              const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
+                              float* features, int F, const double* pos, const double* center_pos,
+                              const int32_t* center_struct, const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
                               const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
                               cudaStream_t stream, int64_t* launches) {
-  k_refine<<<sm_count * 4, 256, 0, stream>>>(flags, count, cap, features, F, pos, struct_of, structs, nbr_off,
+  k_refine<<<sm_count * 4, 256, 0, stream>>>(flags, count, cap, features, F, pos, center_pos, center_struct, structs, nbr_off,
                                              pairs, ktab, nsig_total, kmax, err);
   ++*launches;
   return cudaGetLastError();

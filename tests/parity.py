@@ -7,6 +7,13 @@ Tolerances (floating point; neighbor sets are compared bit for bit):
 F_abs / G_abs are the oracle's cancellation-free scales (the same reduction
 applied to sums of |per-pair contribution|).  See the design doc for how the
 floors follow from FP32 arithmetic.
+
+Both denominators are also floored at FP32_MIN_NORMAL = 2^-126: the outputs
+are FP32, and below the smallest normal FP32 number the format itself has
+fewer than 24 significant bits (subnormals) or none (below 2^-149), so no
+FP32 result can meet a relative bound there.  Such values arise for probes
+much narrower than the distance to the nearest atom (e.g. sigma = 0.05 A at a
+reference point 2 A from every atom, where features fall to 1e-48).
 """
 import json
 import os
@@ -17,6 +24,7 @@ FEAT_TOL = 1e-5
 FEAT_TAU = 1e-6
 GRAD_TOL = 1e-4
 GRAD_TAU = 1e-3
+FP32_MIN_NORMAL = 2.0 ** -126
 
 _report = {}
 
@@ -24,10 +32,8 @@ _report = {}
 def feature_errors(f_gpu, f_ref, f_abs, tau=FEAT_TAU):
     f_gpu = np.asarray(f_gpu, np.float64)
     num = np.abs(f_gpu - f_ref)
-    den = np.maximum(np.abs(f_ref), tau * f_abs)
-    # an exactly zero feature with a zero scale (e.g. l >= 1 of an isolated
-    # atom) must come out exactly zero
-    err = np.where(num == 0.0, 0.0, num / np.where(den > 0.0, den, 1e-300))
+    den = np.maximum(np.maximum(np.abs(f_ref), tau * f_abs), FP32_MIN_NORMAL)
+    err = num / den
     return err.max(axis=0)
 
 
@@ -35,8 +41,8 @@ def grad_errors(g_gpu, g_ref, g_abs, tau=GRAD_TAU):
     """Row-wise: Euclidean error of each 3-vector over max(|g_ref|, tau*g_abs)."""
     g_gpu = np.asarray(g_gpu, np.float64)
     num = np.linalg.norm(g_gpu - g_ref, axis=-1)
-    den = np.maximum(np.linalg.norm(g_ref, axis=-1), tau * g_abs)
-    return np.where(num == 0.0, 0.0, num / np.where(den > 0.0, den, 1e-300))
+    den = np.maximum(np.maximum(np.linalg.norm(g_ref, axis=-1), tau * g_abs), FP32_MIN_NORMAL)
+    return num / den
 
 
 def record(name, **vals):

@@ -203,3 +203,96 @@ def test_graph_replay_matches_eager(torch):
             s.synchronize()
             assert torch.equal(feat, fe), step
             assert torch.equal(gp, ge), step
+
+
+def _cutoff_by_grid(w, t):
+    """Largest r on a 1e-4 A grid where some single-primitive bound exceeds
+    the overlap threshold t (direct evaluation; compare gmp_cutoff)."""
+    import math
+    r = np.arange(1e-4, 80.0, 1e-4)
+    best = 0.0
+    go = w.gauss_off
+    for e in range(w.n_elements):
+        for k in range(go[e], go[e + 1]):
+            a, c = w.gauss_exp[k], abs(w.gauss_coef[k])
+            for l in w.orders:
+                if l < 0:
+                    val = c * np.exp(-a * r * r)
+                    idx = np.nonzero(val > t)[0]
+                    best = max(best, r[idx[-1]] if idx.size else 0.0)
+                    continue
+                lf = math.factorial(l)
+                df = math.prod(range(2 * l - 1, 0, -2)) if l > 0 else 1
+                for s in w.sigmas:
+                    beta = 1 / (2 * s * s)
+                    g = a + beta
+                    amp = c * (2 * math.pi * s * s) ** -1.5 * (math.pi / g) ** 1.5 * (a / g) ** l * math.sqrt(lf * df)
+                    val = amp * r ** l * np.exp(-(a * beta / g) * r * r)
+                    idx = np.nonzero(val > t)[0]
+                    best = max(best, r[idx[-1]] if idx.size else 0.0)
+    return best
+
+
+def test_cutoff_from_overlap_threshold(torch, oracle_mod):
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    w = wl("random64_box").replace(orders=[-1, 0, 1, 2])
+    for t in (1e-8, 1e-12):
+        F = GMPFeaturizer(w.orders, w.sigmas, 0.0, w.n_gauss, w.gauss_coef, w.gauss_exp, overlap_threshold=t)
+        ref = _cutoff_by_grid(w, t)
+        assert abs(F.cutoff - ref) <= 2e-4, (t, F.cutoff, ref)
+    wc = w.replace(cutoff=F.cutoff)
+    pos, sp = _dev(torch, wc)
+    f = F.featurize(pos, sp, wc.atom_off, wc.cells, wc.pbc)
+    torch.cuda.synchronize()
+    fref, fabs = oracle_mod.features(wc, want_abs=True)
+    assert feature_errors(f.cpu().numpy(), fref, fabs).max() <= FEAT_TOL
+
+
+def _points_for(w, n_per, seed):
+    """Reference points per structure: on atoms, uniform in (and around) the
+    cell or the cluster's box, and a few far away."""
+    rng = np.random.default_rng(seed)
+    pts, off = [], [0]
+    for s in range(w.n_struct):
+        a0, a1 = int(w.atom_off[s]), int(w.atom_off[s + 1])
+        k = n_per if s % 7 != 3 else 0          # some structures own no points
+        if k:
+            if w.pbc[s].any():
+                lo, hi = np.zeros(3), np.ones(3)
+                P = rng.uniform(-0.6, 1.6, (k, 3)) @ w.cells[s]
+            else:
+                X = w.positions[a0:a1] if a1 > a0 else np.zeros((1, 3))
+                lo, hi = X.min(0) - 3.0, X.max(0) + 3.0
+                P = rng.uniform(lo, hi, (k, 3))
+            if a1 > a0:
+                P[0] = w.positions[rng.integers(a0, a1)]
+            P[-1] = P[-1] + 1e3 * (s % 2)            # far outside the structure
+            pts.append(P)
+        off.append(off[-1] + k)
+    return np.concatenate(pts), np.array(off, np.int64)
+
+
+@pytest.mark.parametrize("name,n_per", [("random64_box", 40), ("batched300", 5), ("slab_small", 64)])
+def test_point_features_parity(torch, oracle_mod, name, n_per):
+    w = wl(name)
+    pts, poff = _points_for(w, n_per, seed=17)
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    f = F.featurize_points(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(pts).cuda(), poff)
+    torch.cuda.synchronize()
+    pstruct = np.repeat(np.arange(w.n_struct), np.diff(poff))
+    ref, fabs = oracle_mod.point_features(w, pts, pstruct, want_abs=True)
+    err = feature_errors(f.cpu().numpy(), ref, fabs)
+    record(f"points/{name}", max_rel_err=err.max(), points=len(pts))
+    assert err.max() <= FEAT_TOL, (err.max(), np.argmax(err))
+    # a point on an atom reproduces that atom's features bit for bit (same
+    # neighbor enumeration, same kernels)
+    fa = F.featurize(pos, sp, w.atom_off, w.cells, w.pbc).cpu().numpy()
+    fp = f.cpu().numpy()
+    for s in range(w.n_struct):
+        if poff[s + 1] > poff[s] and w.atom_off[s + 1] > w.atom_off[s]:
+            a = np.nonzero((w.positions == pts[poff[s]]).all(1))[0][0]
+            assert np.array_equal(fp[poff[s]], fa[a]), (s, a)
+    # host buffers give the same result
+    fh = F.featurize_points(w.positions, w.species, w.atom_off, w.cells, w.pbc, pts, poff)
+    assert np.array_equal(np.asarray(fh), fp)
