@@ -651,6 +651,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     P.kmax = h->kmax;
     P.n_el = h->n_el;
     P.want_density = (g == 0 && dens) ? 1 : 0;
+    P.mixed_sign = 0;
+    for (double c : h->coef) P.mixed_sign |= (c < 0.0) ? 1 : 0;
     P.F = h->F;
     P.dens_col = -1;
     P.n_ord = 0;
@@ -664,7 +666,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       P.ord_col[P.n_ord] = col[o] + s0;
       ++P.n_ord;
     }
-    std::vector<float> tab((size_t)h->n_el * pd.NS * h->kmax * GMP_RAD_STRIDE, 0.0f);
+    const int RB = gmp_rad_block(L), NSB = pd.NS / 4;
+    std::vector<float> tab((size_t)h->n_el * NSB * h->kmax * RB * 4, 0.0f);
     int64_t off = 0;
     for (int e = 0; e < h->n_el; ++e) {
       for (int s = 0; s < ns; ++s) {
@@ -676,12 +679,13 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
           const double gam = a + beta;
           const double b = a * beta / gam;
           const double B = b * LOG2E;
-          float* ent = &tab[(((size_t)e * pd.NS + s) * h->kmax + q) * GMP_RAD_STRIDE];
-          ent[0] = (float)B;
-          ent[1] = (float)(B - (double)ent[0]);
-          ent[2] = (float)b;
+          float* blk = &tab[(((size_t)e * NSB + s / 4) * h->kmax + q) * RB * 4];
+          const int u = s % 4;
+          blk[u] = (float)B;
+          blk[4 + u] = (float)(B - (double)blk[u]);
+          blk[8 + u] = (float)b;
           const double K0 = c * Ns * std::pow(M_PI / gam, 1.5);
-          for (int l = 0; l < 8; ++l) ent[4 + l] = (float)(K0 * std::pow(a / gam, l));
+          for (int l = 0; l <= L; ++l) blk[4 * (3 + l) + u] = (float)(K0 * std::pow(a / gam, l));
         }
       }
       off += h->n_gauss[e];

@@ -9,7 +9,7 @@ namespace gmpk {
 
 template <int L, int NS, int TILE>
 size_t smem_bytes(const GmpPass& P, int warps) {
-  return sizeof(float) * (table_floats(P.n_el, NS, P.kmax) + (size_t)warps * Shape<L, NS, TILE>::WARP_FLOATS);
+  return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax) + (size_t)warps * Shape<L, NS, TILE>::WARP_FLOATS);
 }
 
 // shape.tile: 16 or 32 pairs per forward tile; shape.warps: warps per CTA

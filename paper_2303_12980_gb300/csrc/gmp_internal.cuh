@@ -64,12 +64,14 @@ __host__ __device__ inline void gmp_unpack_shift(int32_t s, int* n) {
   n[2] = ((s >> 20) & 1023) - 512;
 }
 
-// Radial table entry per (element, sigma, primitive): 12 floats.
+// Radial table block per (element, group of 4 sigmas, primitive): L + 4
+// float4s, each holding one quantity for the 4 sigmas of the group, so one
+// 16-byte shared-memory load serves four sigmas:
 //   [0] Bhi, [1] Blo : B = alpha*beta/gamma * log2(e) as a double-float
 //   [2] b            : alpha*beta/gamma (natural-log rate, for d/dr^2)
-//   [3] unused
-//   [4 + l] A_l      : c * N_sigma * (pi/gamma)^(3/2) * (alpha/gamma)^l, l = 0..7
-#define GMP_RAD_STRIDE 12
+//   [3 + l] A_l      : c * N_sigma * (pi/gamma)^(3/2) * (alpha/gamma)^l, l = 0..L
+// Blocks are ordered [element][sigma group][primitive].
+__host__ __device__ constexpr int gmp_rad_block(int L) { return L + 4; }
 // Density table entry per (element, primitive): Bhi, Blo, b, c with B = alpha*log2(e), b = alpha.
 #define GMP_DENS_STRIDE 4
 
@@ -81,12 +83,13 @@ struct GmpPass {
   int kmax;            // primitives per element (padded)
   int n_el;
   int want_density;    // order -1 requested
+  int mixed_sign;      // some density coefficient is negative (radial factors may be < 0)
   int F;               // total feature columns
   int n_ord;           // number of orders >= 0 written by this pass
   int ord_l[8];        // orders written
   int ord_col[8];      // feature column of (order, sigma 0) for this pass
   int dens_col;        // column of order -1 or -1
-  const float* rad;    // [n_el][nsig_pad][kmax][GMP_RAD_STRIDE]
+  const float* rad;    // [n_el][nsig_pad / 4][kmax][gmp_rad_block(lmax)] float4
   const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]
 };
 

@@ -58,6 +58,12 @@ __host__ __device__ constexpr int chunk_k0(int c) {
   while (c >= chunks_of_order(l)) { c -= chunks_of_order(l); ++l; }
   return l * l + 4 * c;
 }
+// chunk holding the last independent components of order l
+__host__ __device__ constexpr int last_chunk(int l) {
+  int c = 0;
+  for (int m = 0; m <= l; ++m) c += chunks_of_order(m);
+  return c - 1;
+}
 // order l of flat independent component k (k in [l^2, (l+1)^2))
 __host__ __device__ constexpr int order_of(int k) {
   int l = 0;
@@ -80,7 +86,7 @@ struct Shape {
   static constexpr int NCH = nchunks(L);
   static constexpr int NITEM = NSB * NCH;
   static constexpr int Q = (NITEM + 31) / 32;
-  static constexpr int RL4 = (L + 1 + 3) / 4 * 4;  // r^l, l = 0..L, after the S chunks
+  static constexpr int RL4 = (L + 1 + 3) / 4 * 4;  // r^l, l = 0..L, after the S chunks (mixed signs)
   static constexpr int RSTR = odd4((L + 1) * NS);
   static constexpr int SSTR = odd4(NCH * 4 + RL4);
   static constexpr int TILE = TILE_;               // pairs staged per tile: 16 (2 lanes per pair) or 32
@@ -94,8 +100,8 @@ struct Shape {
 
 // Per-element strides of the shared-memory tables: an odd number of float4s,
 // so lanes reading different elements hit different banks.
-__host__ __device__ inline int rad_elem_stride(int NS, int kmax) {
-  int q = NS * kmax * (GMP_RAD_STRIDE / 4);
+__host__ __device__ inline int rad_elem_stride(int L, int NS, int kmax) {
+  int q = (NS / 4) * kmax * gmp_rad_block(L);
   if ((q & 1) == 0) ++q;
   return 4 * q;
 }
@@ -153,9 +159,11 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
 }
 
 // Radial factors of one pair for a group of 4 sigmas: R[u][l] (and dR/dr^2).
+// Each 16-byte table load serves the four sigmas of the group.
 template <int L, int NS, bool DERIV>
 __device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                         float r2l, float (&R)[4][L + 1], float (&Rd)[4][L + 1]) {
+  constexpr int RB = gmp_rad_block(L);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -163,25 +171,56 @@ __device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kma
       R[u][l] = 0.0f;
       if (DERIV) Rd[u][l] = 0.0f;
     }
-#pragma unroll 2
+#pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4 bh = blk[0], bl = blk[1];
+    const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+    float E[4], Ed[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float* ent = tab_e + ((sg * 4 + u) * kmax + q) * GMP_RAD_STRIDE;
-      const float4 h = *reinterpret_cast<const float4*>(ent);
-      const float4 a0 = *reinterpret_cast<const float4*>(ent + 4);
-      float A[8] = {a0.x, a0.y, a0.z, a0.w, 0.f, 0.f, 0.f, 0.f};
-      if (L >= 4) {
-        const float4 a1 = *reinterpret_cast<const float4*>(ent + 8);
-        A[4] = a1.x; A[5] = a1.y; A[6] = a1.z; A[7] = a1.w;
-      }
-      const float E = gmp_exp_neg(h.x, h.y, r2h, r2l);
-      const float Ed = __fmul_rn(-h.z, E);  // d exp(-b r^2) / d r^2
+    for (int u = 0; u < 4; ++u) E[u] = gmp_exp_neg(bhv[u], blv[u], r2h, r2l);
+    if (DERIV) {
+      const float4 b = blk[2];
+      Ed[0] = __fmul_rn(-b.x, E[0]);  // d exp(-b r^2) / d r^2
+      Ed[1] = __fmul_rn(-b.y, E[1]);
+      Ed[2] = __fmul_rn(-b.z, E[2]);
+      Ed[3] = __fmul_rn(-b.w, E[3]);
+    }
 #pragma unroll
-      for (int l = 0; l <= L; ++l) {
-        R[u][l] = __fmaf_rn(A[l], E, R[u][l]);
-        if (DERIV) Rd[u][l] = __fmaf_rn(A[l], Ed, Rd[u][l]);
+    for (int l = 0; l <= L; ++l) {
+      const float4 a = blk[3 + l];
+      const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
+        if (DERIV) Rd[u][l] = __fmaf_rn(av[u], Ed[u], Rd[u][l]);
       }
+    }
+  }
+}
+
+// Radial factors of one pair for half a sigma group (sigmas 4 sg + 2 hp and
+// 4 sg + 2 hp + 1): the same arithmetic as radial4 with half its registers;
+// each 8-byte table load serves two sigmas.
+template <int L>
+__device__ __forceinline__ void radial2(const float* __restrict__ tab_e, int kmax, int sg, int hp, float r2h,
+                                        float r2l, float (&R)[2][L + 1]) {
+  constexpr int RB = gmp_rad_block(L);
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int l = 0; l <= L; ++l) R[u][l] = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < kmax; ++q) {
+    const float2* blk = reinterpret_cast<const float2*>(tab_e) + ((sg * kmax + q) * RB) * 2 + hp;
+    const float2 bh = blk[0], bl = blk[2];
+    const float E0 = gmp_exp_neg(bh.x, bl.x, r2h, r2l);
+    const float E1 = gmp_exp_neg(bh.y, bl.y, r2h, r2l);
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+      const float2 a = blk[2 * (3 + l)];
+      R[0][l] = __fmaf_rn(a.x, E0, R[0][l]);
+      R[1][l] = __fmaf_rn(a.y, E1, R[1][l]);
     }
   }
 }
@@ -203,15 +242,16 @@ __device__ __forceinline__ float density_term(const float* __restrict__ dens_e, 
 // Shared memory: tables first (radial then density), then one region per warp.
 
 
-__host__ __device__ inline size_t table_floats(int n_el, int NS, int kmax) {
-  return (size_t)n_el * rad_elem_stride(NS, kmax) + (size_t)n_el * dens_elem_stride(kmax);
+__host__ __device__ inline size_t table_floats(int n_el, int L, int NS, int kmax) {
+  return (size_t)n_el * rad_elem_stride(L, NS, kmax) + (size_t)n_el * dens_elem_stride(kmax);
 }
 
 // Copies the radial and density tables to shared memory, padding each
 // element's block to its bank-spreading stride.
+template <int L>
 __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_rad, float* s_dens) {
-  const int per = NS * P.kmax * (GMP_RAD_STRIDE / 4);  // float4s per element in global memory
-  const int es = rad_elem_stride(NS, P.kmax) / 4;
+  const int per = (NS / 4) * P.kmax * gmp_rad_block(L);  // float4s per element in global memory
+  const int es = rad_elem_stride(L, NS, P.kmax) / 4;
   for (int t = threadIdx.x; t < P.n_el * per; t += blockDim.x) {
     const int e = t / per, r = t - e * per;
     reinterpret_cast<float4*>(s_rad)[e * es + r] = __ldg(reinterpret_cast<const float4*>(P.rad) + t);
@@ -231,6 +271,10 @@ __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_r
 // compensated pair) in Mu[s * NIND + k] and the conditioning bound
 // B_{l,s} = sum_pairs |R_{l,s}| r^l in Mu[NS * NIND + s * (L+1) + l]
 // (warp-private shared memory), and returns the density (all lanes).
+// The last chunk of every order has a free fourth slot (2l+1 = 1 mod 4 or
+// 3 mod 4); with non-negative density coefficients (R >= 0) that slot of the
+// S row holds r^l, so the moment accumulator of the slot is B itself.  With
+// mixed signs the slot holds 0 and B is accumulated from |R| explicitly.
 template <int L, int NS, int TILE = 16>
 __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens,
@@ -248,11 +292,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
 #pragma unroll
     for (int v = 0; v < 16; ++v) { hi[q][v] = 0.0f; lo[q][v] = 0.0f; }
   float rho_hi = 0.0f, rho_lo = 0.0f;
-  float bnd[SH::Q][4];  // B_{l,s} partials (items holding the first chunk of an order)
-#pragma unroll
-  for (int q = 0; q < SH::Q; ++q)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) bnd[q][u] = 0.0f;
+  const bool mixed = P.mixed_sign != 0;
 
   constexpr int LPP = 32 / TILE;      // phase 1: lanes per pair (2 or 1)
   const int half = LPP == 2 ? (lane >> 4) : 0;
@@ -269,22 +309,37 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       int e, j;
       load_pair(pairs, p0 + base + pl, dx, dy, dz, r2h, r2l, e, j);
       float* srow = St + pl * SH::SSTR;
-      if (half == 0) {  // MCSH components
+      if (half == 0) {  // MCSH components; r^l in the free slot of each order's last chunk
         float S[SH::NIND];
         GmpMcsh<L>::eval(dx, dy, dz, r2h, S);
         static_for<SH::NCH>([&](auto cc) {
           constexpr int c = decltype(cc)::value;
           constexpr int k0 = chunk_k0(c);
           constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
-          float4 v;
-          v.x = S[k0];
-          v.y = (k0 + 1 < kend) ? S[(k0 + 1 < kend) ? k0 + 1 : k0] : 0.0f;
-          v.z = (k0 + 2 < kend) ? S[(k0 + 2 < kend) ? k0 + 2 : k0] : 0.0f;
-          v.w = (k0 + 3 < kend) ? S[(k0 + 3 < kend) ? k0 + 3 : k0] : 0.0f;
-          *reinterpret_cast<float4*>(srow + 4 * c) = v;
+          if constexpr (k0 + 4 < kend + 1 && k0 + 3 < kend) {  // full chunk
+            *reinterpret_cast<float4*>(srow + 4 * c) = make_float4(S[k0], S[k0 + 1], S[k0 + 2], S[k0 + 3]);
+          } else if constexpr (k0 + 1 == kend) {  // last chunk, one component: .y = 0
+            *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], 0.0f);
+          } else {  // last chunk, three components
+            *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], S[(k0 + 1 < kend) ? k0 + 1 : k0]);
+            srow[4 * c + 2] = S[(k0 + 2 < kend) ? k0 + 2 : k0];
+          }
         });
       }
-      if (LPP == 1 || half == 1) {  // r^l for the conditioning bound
+      if (LPP == 1 || half == 1) {  // free slots of the last chunks: r^l (0 with mixed signs)
+        const float r = __fsqrt_rn(r2h);
+        float rpow = mixed ? 0.0f : 1.0f;
+        static_for<L + 1>([&](auto ll) {
+          constexpr int l = decltype(ll)::value;
+          constexpr int c = last_chunk(l);
+          if constexpr (chunk_k0(c) + 1 == (l + 1) * (l + 1))
+            *reinterpret_cast<float2*>(srow + 4 * c + 2) = make_float2(0.0f, rpow);
+          else
+            srow[4 * c + 3] = rpow;
+          rpow = __fmul_rn(rpow, r);
+        });
+      }
+      if (mixed && (LPP == 1 || half == 1)) {  // r^l for the explicit |R| bound
         const float r = __fsqrt_rn(r2h);
         float rl[SH::RL4];
         rl[0] = 1.0f;
@@ -295,14 +350,17 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
           *reinterpret_cast<float4*>(srow + 4 * SH::NCH + 4 * c) =
               make_float4(rl[4 * c], rl[4 * c + 1], rl[4 * c + 2], rl[4 * c + 3]);
       }
-      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
       float* rrow = Rt + pl * SH::RSTR;
       for (int sg = sg0; sg < sg1; ++sg) {
-        float R[4][L + 1], Rd[4][L + 1];
-        radial4<L, NS, false>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
+#pragma unroll 1
+        for (int hp = 0; hp < 2; ++hp) {
+          float R[2][L + 1];
+          radial2<L>(tab_e, P.kmax, sg, hp, r2h, r2l, R);
 #pragma unroll
-        for (int l = 0; l <= L; ++l)
-          *reinterpret_cast<float4*>(rrow + l * NS + 4 * sg) = make_float4(R[0][l], R[1][l], R[2][l], R[3][l]);
+          for (int l = 0; l <= L; ++l)
+            *reinterpret_cast<float2*>(rrow + l * NS + 4 * sg + 2 * hp) = make_float2(R[0][l], R[1][l]);
+        }
       }
       if (P.want_density && half == 0) {
         const float t = density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, nullptr);
@@ -319,15 +377,16 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       if (!it_ok[q]) continue;
       const float* rp = Rt + it_l[q] * NS + 4 * it_sb[q];
       const float* sp = St + 4 * it_ch[q];
-      if (chunk_k0(it_ch[q]) == it_l[q] * it_l[q]) {  // first chunk of order l: bound B
+      if (mixed && chunk_k0(it_ch[q]) + 4 >= (it_l[q] + 1) * (it_l[q] + 1)) {
+        // last chunk of order l, mixed signs: B from |R| into the free slot
         const float* rlp = St + 4 * SH::NCH + it_l[q];
         for (int pp = 0; pp < np; ++pp) {
           const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
           const float rl = rlp[pp * SH::SSTR];
-          bnd[q][0] = __fmaf_rn(fabsf(r.x), rl, bnd[q][0]);
-          bnd[q][1] = __fmaf_rn(fabsf(r.y), rl, bnd[q][1]);
-          bnd[q][2] = __fmaf_rn(fabsf(r.z), rl, bnd[q][2]);
-          bnd[q][3] = __fmaf_rn(fabsf(r.w), rl, bnd[q][3]);
+          hi[q][3] = __fmaf_rn(fabsf(r.x), rl, hi[q][3]);
+          hi[q][7] = __fmaf_rn(fabsf(r.y), rl, hi[q][7]);
+          hi[q][11] = __fmaf_rn(fabsf(r.z), rl, hi[q][11]);
+          hi[q][15] = __fmaf_rn(fabsf(r.w), rl, hi[q][15]);
         }
       }
       for (int b0 = 0; b0 < np; b0 += SH::FOLD) {
@@ -368,9 +427,10 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (kbase + c < kend) Mu[(4 * it_sb[q] + u) * SH::NIND + kbase + c] = __fadd_rn(hi[q][4 * u + c], lo[q][4 * u + c]);
-    if (kbase == l * l)
+    if (kbase + 4 >= kend)  // last chunk: the free slot holds B
 #pragma unroll
-      for (int u = 0; u < 4; ++u) Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] = bnd[q][u];
+      for (int u = 0; u < 4; ++u)
+        Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] = __fadd_rn(hi[q][4 * u + 3], lo[q][4 * u + 3]);
   }
   // density: warp total
   float rho = __fadd_rn(rho_hi, rho_lo);
@@ -434,9 +494,9 @@ __global__ void __launch_bounds__(512) k_forward(KParams K) {
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables(P, NS, s_rad, s_dens);
+  load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
@@ -532,7 +592,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     float lam[SH::NIND], lamd[SH::NIND];
 #pragma unroll
     for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
-    const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+    const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 1], Rd[4][L + 1];
       radial4<L, NS, true>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
@@ -587,9 +647,9 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables(P, NS, s_rad, s_dens);
+  load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
@@ -619,9 +679,9 @@ __global__ void __launch_bounds__(256) k_backward(KParams K) {
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables(P, NS, s_rad, s_dens);
+  load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
@@ -653,9 +713,9 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables(P, NS, s_rad, s_dens);
+  load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
@@ -722,7 +782,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
       // radial factors of this pair for every sigma (all lanes need their own)
       float S1[SH::NIND1];
       GmpMcsh<L + 1>::eval(dx, dy, dz, r2h, S1);
-      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(NS, P.kmax);
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
         if (!f_ok[q]) continue;
@@ -735,11 +795,12 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           const int l = f_l[q], s = f_s[q];
           float R = 0.0f, Rd = 0.0f;
           for (int qq = 0; qq < P.kmax; ++qq) {
-            const float* ent = tab_e + (s * P.kmax + qq) * GMP_RAD_STRIDE;
-            const float E = gmp_exp_neg(ent[0], ent[1], r2h, r2l);
-            const float t = ent[4 + l] * E;
+            // slot v of the block holds quantity v for the 4 sigmas of the group
+            const float* ent = tab_e + ((s / 4) * P.kmax + qq) * gmp_rad_block(L) * 4 + (s % 4);
+            const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
+            const float t = ent[4 * (3 + l)] * E;
             R += t;
-            Rd = __fmaf_rn(-ent[2], t, Rd);
+            Rd = __fmaf_rn(-ent[8], t, Rd);
           }
           const float* lam = Lam + s * SH::NINDP;
           float Pv = 0.0f, V[3];
