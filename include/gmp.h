@@ -207,7 +207,7 @@ gmp_status gmp_set_graph(gmp_handle h, int enable);
 /* Autotuner (not part of the method): builds the neighbor lists of the given
  * batch, then times on it (CUDA events, `reps` launches after a warm-up)
  * the candidate launch shapes of each compute kernel -- forward tile of 16
- * or 32 pairs x 4/8/16 warps per CTA, backward 4/8 warps, the fused
+ * or 32 pairs x 4/8/16 warps per CTA, backward 4/6/12 warps, the fused
  * forward+backward VJP kernel 4/8 warps versus the forward + backward pair
  * -- and keeps the fastest in the handle for later calls.  Synchronises
  * `stream`; writes the number of neighbor pairs to *pairs_out (host, may be

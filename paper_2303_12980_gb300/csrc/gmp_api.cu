@@ -651,6 +651,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     P.kmax = h->kmax;
     P.n_el = h->n_el;
     P.want_density = (g == 0 && dens) ? 1 : 0;
+    for (int s = 0; s < 16; ++s)
+      P.nbeta[s] = s < ns ? (float)(-1.0 / (2.0 * h->sigmas[s0 + s] * h->sigmas[s0 + s])) : 0.0f;
     P.mixed_sign = 0;
     for (double c : h->coef) P.mixed_sign |= (c < 0.0) ? 1 : 0;
     P.F = h->F;
@@ -677,15 +679,13 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
         for (int q = 0; q < h->n_gauss[e]; ++q) {
           const double a = h->alpha[off + q], c = h->coef[off + q];
           const double gam = a + beta;
-          const double b = a * beta / gam;
-          const double B = b * LOG2E;
+          const double B = a * beta / gam * LOG2E;
           float* blk = &tab[(((size_t)e * NSB + s / 4) * h->kmax + q) * RB * 4];
           const int u = s % 4;
           blk[u] = (float)B;
           blk[4 + u] = (float)(B - (double)blk[u]);
-          blk[8 + u] = (float)b;
           const double K0 = c * Ns * std::pow(M_PI / gam, 1.5);
-          for (int l = 0; l <= L; ++l) blk[4 * (3 + l) + u] = (float)(K0 * std::pow(a / gam, l));
+          for (int l = 0; l <= L + 1; ++l) blk[4 * (2 + l) + u] = (float)(K0 * std::pow(a / gam, l));
         }
       }
       off += h->n_gauss[e];
@@ -1149,7 +1149,7 @@ gmp_status gmp_tune(gmp_handle h, int32_t n_struct, const int64_t* atom_off, con
     Kb.grad_acc = h->grad_acc.as<double>();
     float best_b = 1e30f;
     GmpShape bwd_best = pd.bwd;
-    for (int warps : {4, 8}) {
+    for (int warps : {4, 6, 12}) {
       cudaError_t e = timed(GMP_KIND_BACKWARD, pd, Kb, GmpShape{16, warps}, &t);
       if (e != cudaSuccess) { out = cuda_fail(h, e, "tune backward"); break; }
       if (t < best_b) { best_b = t; bwd_best = GmpShape{16, warps}; }

@@ -68,9 +68,10 @@ __host__ __device__ inline void gmp_unpack_shift(int32_t s, int* n) {
 // float4s, each holding one quantity for the 4 sigmas of the group, so one
 // 16-byte shared-memory load serves four sigmas:
 //   [0] Bhi, [1] Blo : B = alpha*beta/gamma * log2(e) as a double-float
-//   [2] b            : alpha*beta/gamma (natural-log rate, for d/dr^2)
-//   [3 + l] A_l      : c * N_sigma * (pi/gamma)^(3/2) * (alpha/gamma)^l, l = 0..L
-// Blocks are ordered [element][sigma group][primitive].
+//   [2 + l] A_l      : c * N_sigma * (pi/gamma)^(3/2) * (alpha/gamma)^l, l = 0..L+1
+// Blocks are ordered [element][sigma group][primitive].  Order L+1 serves
+// the derivative: since the exponent rate is alpha*beta/gamma = beta *
+// (alpha/gamma), d R_l / d r^2 = -beta R_{l+1} exactly.
 __host__ __device__ constexpr int gmp_rad_block(int L) { return L + 4; }
 // Density table entry per (element, primitive): Bhi, Blo, b, c with B = alpha*log2(e), b = alpha.
 #define GMP_DENS_STRIDE 4
@@ -90,6 +91,7 @@ struct GmpPass {
   int ord_col[8];      // feature column of (order, sigma 0) for this pass
   int dens_col;        // column of order -1 or -1
   const float* rad;    // [n_el][nsig_pad / 4][kmax][gmp_rad_block(lmax)] float4
+  float nbeta[16];     // -beta = -1/(2 sigma^2) per sigma of the pass (0 for padding)
   const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]
 };
 

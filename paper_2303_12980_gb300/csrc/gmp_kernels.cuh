@@ -158,43 +158,29 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
   j = __float_as_int(b.z);
 }
 
-// Radial factors of one pair for a group of 4 sigmas: R[u][l] (and dR/dr^2).
-// Each 16-byte table load serves the four sigmas of the group.
-template <int L, int NS, bool DERIV>
-__device__ __forceinline__ void radial4(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
-                                        float r2l, float (&R)[4][L + 1], float (&Rd)[4][L + 1]) {
+// Radial factors of one pair for a group of 4 sigmas, orders 0..L+1 (the
+// extra order gives the derivative: dR_l/dr^2 = -beta R_{l+1}).  Each
+// 16-byte table load serves the four sigmas of the group.
+template <int L>
+__device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+                                         float r2l, float (&R)[4][L + 2]) {
   constexpr int RB = gmp_rad_block(L);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int l = 0; l <= L; ++l) {
-      R[u][l] = 0.0f;
-      if (DERIV) Rd[u][l] = 0.0f;
-    }
+    for (int l = 0; l <= L + 1; ++l) R[u][l] = 0.0f;
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
     const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
     const float4 bh = blk[0], bl = blk[1];
-    const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
-    float E[4], Ed[4];
+    const float E[4] = {gmp_exp_neg(bh.x, bl.x, r2h, r2l), gmp_exp_neg(bh.y, bl.y, r2h, r2l),
+                        gmp_exp_neg(bh.z, bl.z, r2h, r2l), gmp_exp_neg(bh.w, bl.w, r2h, r2l)};
 #pragma unroll
-    for (int u = 0; u < 4; ++u) E[u] = gmp_exp_neg(bhv[u], blv[u], r2h, r2l);
-    if (DERIV) {
-      const float4 b = blk[2];
-      Ed[0] = __fmul_rn(-b.x, E[0]);  // d exp(-b r^2) / d r^2
-      Ed[1] = __fmul_rn(-b.y, E[1]);
-      Ed[2] = __fmul_rn(-b.z, E[2]);
-      Ed[3] = __fmul_rn(-b.w, E[3]);
-    }
-#pragma unroll
-    for (int l = 0; l <= L; ++l) {
-      const float4 a = blk[3 + l];
+    for (int l = 0; l <= L + 1; ++l) {
+      const float4 a = blk[2 + l];
       const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
-        if (DERIV) Rd[u][l] = __fmaf_rn(av[u], Ed[u], Rd[u][l]);
-      }
+      for (int u = 0; u < 4; ++u) R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
     }
   }
 }
@@ -218,7 +204,7 @@ __device__ __forceinline__ void radial2(const float* __restrict__ tab_e, int kma
     const float E1 = gmp_exp_neg(bh.y, bl.y, r2h, r2l);
 #pragma unroll
     for (int l = 0; l <= L; ++l) {
-      const float2 a = blk[2 * (3 + l)];
+      const float2 a = blk[2 * (2 + l)];
       R[0][l] = __fmaf_rn(a.x, E0, R[0][l]);
       R[1][l] = __fmaf_rn(a.y, E1, R[1][l]);
     }
@@ -594,10 +580,14 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
-      float R[4][L + 1], Rd[4][L + 1];
-      radial4<L, NS, true>(tab_e, P.kmax, sg, r2h, r2l, R, Rd);
+      float R[4][L + 2];
+      radial4d<L>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
+        const float nb = P.nbeta[4 * sg + u];
+        float Rd[L + 1];  // dR_l/dr^2 = -beta R_{l+1}
+#pragma unroll
+        for (int l = 0; l <= L; ++l) Rd[l] = __fmul_rn(nb, R[u][l + 1]);
         const float* lrow = Lam + (4 * sg + u) * SH::NINDP;
         static_for<SH::NINDP / 4>([&](auto cq) {
           constexpr int c4 = decltype(cq)::value;
@@ -608,7 +598,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
             if constexpr (k < SH::NIND) {
               constexpr int l = order_of(k);
               lam[k] = __fmaf_rn(lv[decltype(tt)::value], R[u][l], lam[k]);
-              lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[u][l], lamd[k]);
+              lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[l], lamd[k]);
             }
           });
         });
@@ -674,7 +664,7 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
 }
 
 template <int L, int NS>
-__global__ void __launch_bounds__(256) k_backward(KParams K) {
+__global__ void __launch_bounds__(384) k_backward(KParams K) {
   using SH = Shape<L, NS>;
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
@@ -738,6 +728,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
     adjoints<L, NS>(P, Mu, nullptr, Lam);
     // this lane's features
     int f_col[QF], f_l[QF], f_s[QF];
+    float f_nb[QF];  // -beta of the feature's sigma
     bool f_ok[QF];
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
@@ -751,6 +742,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
       } else {
         f_s[q] = 0; f_l[q] = -1; f_col[q] = P.dens_col;
       }
+      f_nb[q] = P.nbeta[f_s[q]];
     }
     float self[QF][3], acc[QF][3];
 #pragma unroll
@@ -793,15 +785,15 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           g[0] = 2.0f * drho * dx; g[1] = 2.0f * drho * dy; g[2] = 2.0f * drho * dz;
         } else {
           const int l = f_l[q], s = f_s[q];
-          float R = 0.0f, Rd = 0.0f;
+          float R = 0.0f, R1 = 0.0f;
           for (int qq = 0; qq < P.kmax; ++qq) {
             // slot v of the block holds quantity v for the 4 sigmas of the group
             const float* ent = tab_e + ((s / 4) * P.kmax + qq) * gmp_rad_block(L) * 4 + (s % 4);
             const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
-            const float t = ent[4 * (3 + l)] * E;
-            R += t;
-            Rd = __fmaf_rn(-ent[8], t, Rd);
+            R = __fmaf_rn(ent[4 * (2 + l)], E, R);
+            R1 = __fmaf_rn(ent[4 * (3 + l)], E, R1);
           }
+          const float Rd = f_nb[q] * R1;  // dR_l/dr^2 = -beta R_{l+1}
           const float* lam = Lam + s * SH::NINDP;
           float Pv = 0.0f, V[3];
           for (int k = l * l; k < (l + 1) * (l + 1); ++k) Pv = __fmaf_rn(lam[k], S1[k], Pv);

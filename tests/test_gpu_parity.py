@@ -296,3 +296,26 @@ def test_point_features_parity(torch, oracle_mod, name, n_per):
     # host buffers give the same result
     fh = F.featurize_points(w.positions, w.species, w.atom_off, w.cells, w.pbc, pts, poff)
     assert np.array_equal(np.asarray(fh), fp)
+
+
+def test_mixed_sign_density_tables(torch, oracle_mod):
+    """Density coefficients of both signs (radial factors may be negative):
+    features, refinement flags and the VJP against the oracle."""
+    w = wl("random64_box")
+    coef = np.array(w.gauss_coef, np.float64)
+    coef[1] *= -0.5
+    coef[6] *= -0.3
+    w = w.replace(gauss_coef=coef, orders=[-1, 0, 1, 2])
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=8)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    ferr = feature_errors(feat.cpu().numpy(), ref, fabs)
+    atoms = synth.subset_centers(w.n_atoms, 16, seed=3)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    record("mixed_sign/random64_box", features_max_rel_err=ferr.max(), vjp_max_rel_err=gerr.max())
+    assert ferr.max() <= FEAT_TOL, ferr.max()
+    assert gerr.max() <= GRAD_TOL, gerr.max()
