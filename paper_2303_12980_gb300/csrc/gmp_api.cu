@@ -77,7 +77,7 @@ struct gmp_ctx {
   int64_t n_bins = 0;
   // workspace
   DevBuf structs, grid, atom_off, struct_of, bbox, atom_xh, atom_xl, atom_u, atom_bin, atom_rng, atom_y;
-  DevBuf bin_count, bin_cursor, bin_start, bin_y, counts, nbr_off, scan_tmp, pairs;
+  DevBuf bin_count, bin_cursor, bin_start, bin_y, bin_je, counts, nbr_off, scan_tmp, pairs;
   DevBuf scalars;  // err word, maxm, counter
   DevBuf grad_acc, jac_counts;
   DevBuf mu;     // per-center moments between the forward and backward kernels
@@ -333,6 +333,7 @@ gmp_status bin_atoms(gmp_ctx* h, int32_t S, const double* pos, const int32_t* sp
   GMP_CK(h->bin_cursor.ensure(sizeof(int32_t) * h->n_bins), "bin_cursor");
   GMP_CK(h->bin_start.ensure(sizeof(int32_t) * (h->n_bins + 1)), "bin_start");
   GMP_CK(h->bin_y.ensure(sizeof(float4) * N), "bin_y");
+  GMP_CK(h->bin_je.ensure(sizeof(int2) * N), "bin_je");
   GMP_CK(h->counts.ensure(sizeof(int64_t) * n_centers), "counts");
   GMP_CK(h->nbr_off.ensure(sizeof(int64_t) * (n_centers + 1)), "nbr_off");
   const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(N, n_centers), h->n_bins);
@@ -346,8 +347,9 @@ gmp_status bin_atoms(gmp_ctx* h, int32_t S, const double* pos, const int32_t* sp
   GMP_CK(gmp_launch_bins(h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->struct_of.as<int32_t>(), N,
                          h->n_bins, h->atom_bin.as<int32_t>(), h->bin_count.as<int32_t>(),
                          h->bin_start.as<int32_t>(), h->bin_cursor.as<int32_t>(), h->atom_rng.as<int4>(),
-                         h->atom_y.as<float4>(), h->bin_y.as<float4>(), h->atom_u.as<GmpD4>(), h->scan_tmp.p,
-                         h->scan_tmp.bytes, st, h->sm_count, L),
+                         h->atom_y.as<float4>(), h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->atom_u.as<GmpD4>(),
+                         h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->scan_tmp.p, h->scan_tmp.bytes, st,
+                         h->sm_count, L),
          "bins");
   return GMP_OK;
 }
@@ -365,7 +367,8 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
   GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
   GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
                                   h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
-                                  h->bin_y.as<float4>(), h->counts.as<int64_t>(), nullptr, nullptr, 0, 0, d_maxm,
+                                  h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, h->counts.as<int64_t>(),
+                                  nullptr, nullptr, 0, 0, d_maxm,
                                   d_err, st, h->sm_count, L),
          "neighbor count");
   GMP_CK(gmp_exclusive_scan_i64(h->counts.as<int64_t>(), h->nbr_off.as<int64_t>(), NC, h->scan_tmp.p, st, L), "scan");
@@ -374,7 +377,7 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
     // (and flag) centers beyond them
     GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
                                     h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                                    h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), nullptr,
+                                    h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, nullptr,
                                     h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->cap_pairs, h->cap_keys,
                                     d_maxm, d_err, st, h->sm_count, L),
            "neighbor fill");
@@ -398,7 +401,7 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
   GMP_CK(h->pairs.ensure(sizeof(GmpPair) * (h->P > 0 ? h->P : 1)), "pairs");
   GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
                                   h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                                  h->bin_start.as<int32_t>(), h->bin_y.as<float4>(),
+                                  h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el,
                                   nullptr, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->P, keys, d_maxm,
                                   d_err, st, h->sm_count, L),
          "neighbor fill");

@@ -172,9 +172,9 @@ cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struc
 cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
                             const int32_t* d_struct_of, int64_t N, int64_t n_bins,
                             const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
-                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y,
-                            const GmpD4* atom_u, void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
-                            int sm_count, int64_t* launches);
+                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y, int2* bin_je,
+                            const GmpD4* atom_u, const float4* atom_xh, const float4* atom_xl, void* scan_tmp,
+                            size_t scan_tmp_bytes, cudaStream_t stream, int sm_count, int64_t* launches);
 size_t gmp_scan_tmp_bytes(int64_t n);
 cudaError_t gmp_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp,
                                    cudaStream_t stream, int64_t* launches);
@@ -202,8 +202,8 @@ cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* 
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const GmpCenters& C, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const int32_t* bin_start,
-                                     const float4* bin_y, int64_t* counts, const int64_t* offsets,
+                                     const int32_t* bin_start, const float4* bin_y, const int2* bin_je, int n_el,
+                                     int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
 cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,

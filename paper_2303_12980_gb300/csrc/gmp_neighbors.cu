@@ -14,8 +14,11 @@
 //      relative), which decides every case except a shell of relative width
 //      ~1e-9 around rc^2; inside that shell the FP64 expression above is
 //      evaluated exactly as written, so the set equals the FP64 one;
-//   4. each center's accepted (j, n) keys are sorted in shared memory, which
-//      makes every later sum over a center's neighbors deterministic.
+//   4. each center's accepted (j, n) records are written in a fixed order,
+//      which makes every later sum over a center's neighbors deterministic:
+//      grouped by neighbor species, enumeration order within a species
+//      (the feature kernels then read the same table rows across a tile),
+//      or sorted by (j, n) for the Jacobian and the neighbor-list output.
 #include "gmp_internal.cuh"
 
 #include <math.h>
@@ -206,10 +209,14 @@ __global__ void k_bin_assign(const GmpStruct* __restrict__ S, const GmpGrid* __r
   }
 }
 
+// Bin slots: bin_y = (wrapped FP32 position, packed wrap of the atom),
+// bin_je = (atom index, species).
 __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
                               int64_t N, const int32_t* __restrict__ atom_bin,
                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ bin_cursor,
-                              const GmpD4* __restrict__ atom_u, float4* __restrict__ bin_y) {
+                              const GmpD4* __restrict__ atom_u, const float4* __restrict__ atom_xh,
+                              const float4* __restrict__ atom_xl, float4* __restrict__ bin_y,
+                              int2* __restrict__ bin_je) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
        a += (int64_t)gridDim.x * blockDim.x) {
     const int s = struct_of[a];
@@ -220,7 +227,8 @@ __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __
     float y[3];
     for (int c = 0; c < 3; ++c)
       y[c] = (float)(u4.x * st.A[c] + u4.y * st.A[3 + c] + u4.z * st.A[6 + c]);
-    bin_y[slot] = make_float4(y[0], y[1], y[2], __int_as_float((int32_t)a));
+    bin_y[slot] = make_float4(y[0], y[1], y[2], atom_xl[a].w);
+    bin_je[slot] = make_int2((int32_t)a, __float_as_int(atom_xh[a].w));
   }
 }
 
@@ -313,19 +321,22 @@ __global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* 
 
 // Orders each bin's atoms by index (the scatter above fills bins in
 // arbitrary order), which makes neighbor enumeration deterministic.
-__global__ void k_bin_sort(int64_t n_bins, const int32_t* __restrict__ bin_start, float4* __restrict__ bin_y) {
+__global__ void k_bin_sort(int64_t n_bins, const int32_t* __restrict__ bin_start, float4* __restrict__ bin_y,
+                           int2* __restrict__ bin_je) {
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n_bins;
        b += (int64_t)gridDim.x * blockDim.x) {
     const int b0 = bin_start[b], b1 = bin_start[b + 1];
     for (int t = b0 + 1; t < b1; ++t) {
       const float4 v = bin_y[t];
-      const int key = __float_as_int(v.w);
+      const int2 je = bin_je[t];
       int u = t - 1;
-      while (u >= b0 && __float_as_int(bin_y[u].w) > key) {
+      while (u >= b0 && bin_je[u].x > je.x) {
         bin_y[u + 1] = bin_y[u];
+        bin_je[u + 1] = bin_je[u];
         --u;
       }
       bin_y[u + 1] = v;
+      bin_je[u + 1] = je;
     }
   }
 }
@@ -441,24 +452,36 @@ __device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, con
   return fp64_within(pos, xi, j, st, n, rc2);
 }
 
-// Warp per center.  fill = 0: count exact neighbors; fill = 1: write the
-// pair records in enumeration order (cells in a fixed order, atoms in index
-// order within a cell: deterministic); fill = 2: the same, sorted by
-// (neighbor atom, image) first.
-__global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
+// Per-warp shared memory of the fill passes: keys [max_keys] u64, species
+// of each key [max_keys] u16 (FILL 1), per-species counters [n_el] int.
+__host__ __device__ inline size_t fill_warp_bytes(int max_keys, int n_el) {
+  return ((size_t)max_keys * 10 + (size_t)n_el * 4 + 15) / 16 * 16;
+}
+
+// Warp per center.  FILL = 0: count exact neighbors; FILL = 1: write the
+// pair records grouped by neighbor species, in enumeration order within a
+// species (cells in a fixed order, atoms in index order within a cell:
+// deterministic); FILL = 2: sorted by (neighbor atom, image).
+template <int FILL>
+__global__ void k_neighbors(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
                             const GmpCenters C, int64_t N, float cutoff,
                             float rc2hi, float rc2lo, double rc2, const double* __restrict__ pos,
                             const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
                             const int32_t* __restrict__ bin_start, const float4* __restrict__ bin_y,
+                            const int2* __restrict__ bin_je, int n_el,
                             int64_t* __restrict__ counts, const int64_t* __restrict__ offsets,
                             GmpPair* __restrict__ pairs, int64_t pair_cap, int max_keys,
                             int32_t* __restrict__ maxm, uint32_t* __restrict__ err) {
-  extern __shared__ unsigned long long sh_keys[];
+  extern __shared__ __align__(16) unsigned char sh_fill[];
+  constexpr int fill = FILL;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= N) return;
-  unsigned long long* keys = sh_keys + (size_t)wib * max_keys;
+  unsigned char* wbase = sh_fill + (size_t)wib * fill_warp_bytes(max_keys, n_el);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(wbase);
+  uint16_t* kel = reinterpret_cast<uint16_t*>(wbase + (size_t)max_keys * 8);
+  int* ecnt = reinterpret_cast<int*>(wbase + (size_t)max_keys * 10);  // max_keys: a power of 2 >= 32
 
   const int s = C.sid[i];
   const GmpStruct& st = S[s];
@@ -515,6 +538,7 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
       const int slot = b0 + t;
       bool acc = false;
       unsigned long long key = 0;
+      int ej = 0;
       if (slot < b1) {
         const float4 yj = bin_y[slot];
         const float dx = (yj.x - yi[0]) + sh[0];
@@ -522,12 +546,15 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
         const float dz = (yj.z - yi[2]) + sh[2];
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 <= p2) {
-          const int64_t j = __float_as_int(yj.w);
           int wj[3];
-          gmp_unpack_shift(__float_as_int(__ldg(&atom_xl[j].w)), wj);
+          gmp_unpack_shift(__float_as_int(yj.w), wj);
           int n[3] = {m[0] + wi[0] - wj[0], m[1] + wi[1] - wj[1], m[2] + wi[2] - wj[2]};
           acc = true;
+          int64_t j = -1;
           if (r2 >= q2) {  // boundary shell: exact decision
+            const int2 je = bin_je[slot];
+            j = je.x;
+            ej = je.y;
             const float4 xhj = atom_xh[j], xlj = atom_xl[j];
             acc = exact_accept(pos, xi, j, xhi, xli, xhj, xlj, st, n, rc2hi, rc2lo, rc2, cutoff);
           }
@@ -535,7 +562,14 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
             atomicOr(err, GMP_DEV_SHIFT_RANGE);  // reported after the count pass
             acc = false;
           }
-          if (acc) key = sort_key(j, n);
+          if (fill && acc) {
+            if (j < 0) {
+              const int2 je = bin_je[slot];
+              j = je.x;
+              ej = je.y;
+            }
+            key = sort_key(j, n);
+          }
         }
       }
       if (!fill) {
@@ -543,7 +577,10 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
       } else {
         const unsigned mask = __ballot_sync(0xffffffffu, acc);
         const int slot_k = count + __popc(mask & ((1u << lane) - 1u));
-        if (acc && slot_k < max_keys) keys[slot_k] = key;
+        if (acc && slot_k < max_keys) {
+          keys[slot_k] = key;
+          if (fill == 1) kel[slot_k] = (uint16_t)ej;
+        }
         count += __popc(mask);
       }
     }
@@ -590,8 +627,41 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
       }
     }
   }
+  if (fill == 1) {
+    // destination of key t: species-major, enumeration order within a
+    // species (counting sort; lanes of one match group have one species)
+    for (int e = lane; e < n_el; e += 32) ecnt[e] = 0;
+    __syncwarp();
+    for (int t0 = 0; t0 < M; t0 += 32) {
+      const int t = t0 + lane;
+      const int e = t < M ? (int)kel[t] : -1;
+      const unsigned grp = __match_any_sync(0xffffffffu, e);
+      if (t < M && lane == __ffs(grp) - 1) ecnt[e] += __popc(grp);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      int run = 0;
+      for (int e = 0; e < n_el; ++e) {
+        const int c = ecnt[e];
+        ecnt[e] = run;
+        run += c;
+      }
+    }
+    __syncwarp();
+  }
   // records: the double-float displacement, rounded to FP32
-  for (int t = lane; t < M; t += 32) {
+  for (int t0 = 0; t0 < M; t0 += 32) {
+    const int t = t0 + lane;
+    int dst = t;
+    if (fill == 1) {
+      const int e = t < M ? (int)kel[t] : -1;
+      const unsigned grp = __match_any_sync(0xffffffffu, e);
+      if (t < M) dst = ecnt[e] + __popc(grp & ((1u << lane) - 1u));
+      __syncwarp();
+      if (t < M && lane == __ffs(grp) - 1) ecnt[e] += __popc(grp);
+      __syncwarp();
+    }
+    if (t >= M) continue;
     const unsigned long long key = keys[t];
     const int64_t j = (int64_t)(key >> 30);
     int n[3];
@@ -610,7 +680,7 @@ __global__ void k_neighbors(int fill, const GmpStruct* __restrict__ S, const Gmp
     p.e = __float_as_int(xhj.w);
     p.j = (int32_t)j;
     p.shift = packed;
-    pairs[base + t] = p;
+    pairs[base + dst] = p;
   }
 }
 
@@ -677,9 +747,9 @@ cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struc
 cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
                             const int32_t* d_struct_of, int64_t N, int64_t n_bins,
                             const int32_t* atom_bin, int32_t* bin_count, int32_t* bin_start,
-                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y,
-                            const GmpD4* atom_u, void* scan_tmp, size_t scan_tmp_bytes, cudaStream_t stream,
-                            int sm_count, int64_t* launches) {
+                            int32_t* bin_cursor, int4* atom_rng, float4* atom_y, float4* bin_y, int2* bin_je,
+                            const GmpD4* atom_u, const float4* atom_xh, const float4* atom_xl, void* scan_tmp,
+                            size_t scan_tmp_bytes, cudaStream_t stream, int sm_count, int64_t* launches) {
   (void)scan_tmp_bytes;
   cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * n_bins, stream);
   if (e != cudaSuccess) return e;
@@ -691,9 +761,10 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
   e = exclusive_scan<int32_t>(bin_count, bin_start, n_bins, scan_tmp, stream, launches);
   if (e != cudaSuccess) return e;
   k_bin_scatter<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, atom_bin,
-                                                                bin_start, bin_cursor, atom_u, bin_y);
+                                                                bin_start, bin_cursor, atom_u, atom_xh, atom_xl,
+                                                                bin_y, bin_je);
   ++*launches;
-  k_bin_sort<<<grid_for(n_bins, 256, sm_count), 256, 0, stream>>>(n_bins, bin_start, bin_y);
+  k_bin_sort<<<grid_for(n_bins, 256, sm_count), 256, 0, stream>>>(n_bins, bin_start, bin_y, bin_je);
   ++*launches;
   k_ranges<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, d_struct_of, N, atom_u, atom_rng,
                                                            atom_y);
@@ -715,30 +786,30 @@ cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* 
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const GmpCenters& C, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
-                                     const int32_t* bin_start,
-                                     const float4* bin_y, int64_t* counts, const int64_t* offsets,
+                                     const int32_t* bin_start, const float4* bin_y, const int2* bin_je, int n_el,
+                                     int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
   (void)sm_count;
+  if (fill < 0 || fill > 2) return cudaErrorInvalidValue;
   const double rc2 = cutoff * cutoff;
   const float rc2hi = (float)rc2;
   const float rc2lo = (float)(rc2 - (double)rc2hi);
+  auto fn = fill == 0 ? k_neighbors<0> : fill == 1 ? k_neighbors<1> : k_neighbors<2>;
   int warps = 4;
   size_t smem = 0;
   if (fill) {
-    while (warps > 1 && (size_t)warps * max_keys * 8 > 96 * 1024) warps >>= 1;
-    smem = (size_t)warps * max_keys * 8;
+    while (warps > 1 && (size_t)warps * fill_warp_bytes(max_keys, n_el) > 96 * 1024) warps >>= 1;
+    smem = (size_t)warps * fill_warp_bytes(max_keys, n_el);
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
   }
   const unsigned blocks = (unsigned)((N + warps - 1) / warps);
-  k_neighbors<<<blocks, warps * 32, smem, stream>>>(fill, d_structs, d_grid, C, N,
-                                                    (float)cutoff, rc2hi, rc2lo, rc2, pos, atom_xh,
-                                                    atom_xl, bin_start, bin_y, counts,
-                                                    offsets, pairs, pair_cap, max_keys, d_maxm, d_err);
+  fn<<<blocks, warps * 32, smem, stream>>>(d_structs, d_grid, C, N, (float)cutoff, rc2hi, rc2lo, rc2, pos,
+                                           atom_xh, atom_xl, bin_start, bin_y, bin_je, n_el, counts, offsets,
+                                           pairs, pair_cap, max_keys, d_maxm, d_err);
   ++*launches;
   return cudaGetLastError();
 }

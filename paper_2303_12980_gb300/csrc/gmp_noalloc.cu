@@ -41,7 +41,8 @@ struct Layout {
   static constexpr size_t bcursor = bcount + align256(4 * kMaxBins);
   static constexpr size_t bstart = bcursor + align256(4 * kMaxBins);
   static constexpr size_t by = bstart + align256(4 * (kMaxBins + 1));
-  static constexpr size_t rng = by + align256(16 * kNoAllocMaxAtoms);
+  static constexpr size_t bje = by + align256(16 * kNoAllocMaxAtoms);
+  static constexpr size_t rng = bje + align256(8 * kNoAllocMaxAtoms);
   static constexpr size_t ay = rng + align256(16 * kNoAllocMaxAtoms);
   static constexpr size_t scan = ay + align256(16 * kNoAllocMaxAtoms);
   static constexpr size_t scan_bytes = 16 * 1024;
@@ -164,6 +165,7 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
   int32_t* d_bcursor = reinterpret_cast<int32_t*>(base + Layout::bcursor);
   int32_t* d_bstart = reinterpret_cast<int32_t*>(base + Layout::bstart);
   float4* d_by = reinterpret_cast<float4*>(base + Layout::by);
+  int2* d_bje = reinterpret_cast<int2*>(base + Layout::bje);
   int4* d_rng = reinterpret_cast<int4*>(base + Layout::rng);
   float4* d_ay = reinterpret_cast<float4*>(base + Layout::ay);
   void* d_scan = base + Layout::scan;
@@ -180,11 +182,11 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
                                      d_u, d_bin, d_bbox, d_err, st, sm_count, &launches);
   if (e == cudaSuccess)
     e = gmp_launch_bins(d_st, d_grid, d_struct_of, n_atoms, n_bins, d_bin, d_bcount, d_bstart, d_bcursor, d_rng,
-                        d_ay, d_by, d_u, d_scan, Layout::scan_bytes, st, sm_count, &launches);
+                        d_ay, d_by, d_bje, d_u, d_xh, d_xl, d_scan, Layout::scan_bytes, st, sm_count, &launches);
   const GmpCenters centers{d_struct_of, pos, d_xh, d_xl, d_rng, d_ay};
   if (e == cudaSuccess)
     e = gmp_launch_neighbor_pass(0, d_st, d_grid, centers, n_atoms, cutoff, pos, d_xh, d_xl, d_bstart, d_by,
-                                 counts, nullptr, nullptr, 0, 0, d_maxm, d_err, st, sm_count, &launches);
+                                 d_bje, 1, counts, nullptr, nullptr, 0, 0, d_maxm, d_err, st, sm_count, &launches);
   uint32_t w = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d_err, sizeof(w), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
