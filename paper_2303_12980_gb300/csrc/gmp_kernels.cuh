@@ -158,17 +158,23 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
   j = __float_as_int(b.z);
 }
 
-// Radial factors of one pair for a group of 4 sigmas, orders 0..L+1 (the
-// extra order gives the derivative: dR_l/dr^2 = -beta R_{l+1}).  Each
-// 16-byte table load serves the four sigmas of the group.
-template <int L>
+// Pulls the cache line of a pair record into L1 ahead of its use (no registers held).
+__device__ __forceinline__ void prefetch_pair(const GmpPair* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Radial factors of one pair for a group of 4 sigmas, orders 0..NL-1 (the
+// forward needs L+1 orders; the backward one more, for the derivative
+// dR_l/dr^2 = -beta R_{l+1}).  Each 16-byte table load serves the four
+// sigmas of the group.
+template <int L, int NL = L + 2>
 __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
-                                         float r2l, float (&R)[4][L + 2]) {
+                                         float r2l, float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int l = 0; l <= L + 1; ++l) R[u][l] = 0.0f;
+    for (int l = 0; l < NL; ++l) R[u][l] = 0.0f;
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
     const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
@@ -176,37 +182,11 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
     const float E[4] = {gmp_exp_neg(bh.x, bl.x, r2h, r2l), gmp_exp_neg(bh.y, bl.y, r2h, r2l),
                         gmp_exp_neg(bh.z, bl.z, r2h, r2l), gmp_exp_neg(bh.w, bl.w, r2h, r2l)};
 #pragma unroll
-    for (int l = 0; l <= L + 1; ++l) {
+    for (int l = 0; l < NL; ++l) {
       const float4 a = blk[2 + l];
       const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
-    }
-  }
-}
-
-// Radial factors of one pair for half a sigma group (sigmas 4 sg + 2 hp and
-// 4 sg + 2 hp + 1): the same arithmetic as radial4 with half its registers;
-// each 8-byte table load serves two sigmas.
-template <int L>
-__device__ __forceinline__ void radial2(const float* __restrict__ tab_e, int kmax, int sg, int hp, float r2h,
-                                        float r2l, float (&R)[2][L + 1]) {
-  constexpr int RB = gmp_rad_block(L);
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int l = 0; l <= L; ++l) R[u][l] = 0.0f;
-#pragma unroll 1
-  for (int q = 0; q < kmax; ++q) {
-    const float2* blk = reinterpret_cast<const float2*>(tab_e) + ((sg * kmax + q) * RB) * 2 + hp;
-    const float2 bh = blk[0], bl = blk[2];
-    const float E0 = gmp_exp_neg(bh.x, bl.x, r2h, r2l);
-    const float E1 = gmp_exp_neg(bh.y, bl.y, r2h, r2l);
-#pragma unroll
-    for (int l = 0; l <= L; ++l) {
-      const float2 a = blk[2 * (2 + l)];
-      R[0][l] = __fmaf_rn(a.x, E0, R[0][l]);
-      R[1][l] = __fmaf_rn(a.y, E1, R[1][l]);
     }
   }
 }
@@ -294,6 +274,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       float dx, dy, dz, r2h, r2l;
       int e, j;
       load_pair(pairs, p0 + base + pl, dx, dy, dz, r2h, r2l, e, j);
+      if (half == 0 && base + SH::TILE + pl < M) prefetch_pair(pairs + p0 + base + SH::TILE + pl);
       float* srow = St + pl * SH::SSTR;
       if (half == 0) {  // MCSH components; r^l in the free slot of each order's last chunk
         float S[SH::NIND];
@@ -339,14 +320,11 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
       float* rrow = Rt + pl * SH::RSTR;
       for (int sg = sg0; sg < sg1; ++sg) {
-#pragma unroll 1
-        for (int hp = 0; hp < 2; ++hp) {
-          float R[2][L + 1];
-          radial2<L>(tab_e, P.kmax, sg, hp, r2h, r2l, R);
+        float R[4][L + 1];
+        radial4d<L, L + 1>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
-          for (int l = 0; l <= L; ++l)
-            *reinterpret_cast<float2*>(rrow + l * NS + 4 * sg + 2 * hp) = make_float2(R[0][l], R[1][l]);
-        }
+        for (int l = 0; l <= L; ++l)
+          *reinterpret_cast<float4*>(rrow + l * NS + 4 * sg) = make_float4(R[0][l], R[1][l], R[2][l], R[3][l]);
       }
       if (P.want_density && half == 0) {
         const float t = density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, nullptr);
@@ -575,6 +553,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     float dx, dy, dz, r2h, r2l;
     int e, j;
     load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
+    if (pp + 32 < M) prefetch_pair(K.pairs + p0 + pp + 32);
     float lam[SH::NIND], lamd[SH::NIND];
 #pragma unroll
     for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
