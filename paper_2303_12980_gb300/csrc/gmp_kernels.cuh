@@ -167,7 +167,11 @@ __device__ __forceinline__ void prefetch_pair(const GmpPair* p) {
 // forward needs L+1 orders; the backward one more, for the derivative
 // dR_l/dr^2 = -beta R_{l+1}).  Each 16-byte table load serves the four
 // sigmas of the group.
-template <int L, int NL = L + 2>
+// PRECISE: the exponent argument B r^2 as a double-float (features: about
+// 1e-7 relative); otherwise a single FP32 product, whose error of at most
+// 2^-24 B r^2 (B r^2 < 126 before ex2 underflows) leaves each exponential
+// within ~5e-6 relative: ample for derivatives, checked to 1e-4.
+template <int L, int NL = L + 2, bool PRECISE = true>
 __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float r2l, float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
@@ -178,9 +182,20 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
     const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
-    const float4 bh = blk[0], bl = blk[1];
-    const float E[4] = {gmp_exp_neg(bh.x, bl.x, r2h, r2l), gmp_exp_neg(bh.y, bl.y, r2h, r2l),
-                        gmp_exp_neg(bh.z, bl.z, r2h, r2l), gmp_exp_neg(bh.w, bl.w, r2h, r2l)};
+    const float4 bh = blk[0];
+    float E[4];
+    if (PRECISE) {
+      const float4 bl = blk[1];
+      E[0] = gmp_exp_neg(bh.x, bl.x, r2h, r2l);
+      E[1] = gmp_exp_neg(bh.y, bl.y, r2h, r2l);
+      E[2] = gmp_exp_neg(bh.z, bl.z, r2h, r2l);
+      E[3] = gmp_exp_neg(bh.w, bl.w, r2h, r2l);
+    } else {
+      E[0] = gmp_ex2(-__fmul_rn(bh.x, r2h));
+      E[1] = gmp_ex2(-__fmul_rn(bh.y, r2h));
+      E[2] = gmp_ex2(-__fmul_rn(bh.z, r2h));
+      E[3] = gmp_ex2(-__fmul_rn(bh.w, r2h));
+    }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const float4 a = blk[2 + l];
@@ -516,12 +531,15 @@ __device__ __forceinline__ void pair_gradient(const float* lam, const float* lam
   GmpMcsh<L + 1>::eval(dx, dy, dz, r2, S1);
   float A = 0.0f, B = 0.0f;
 #pragma unroll
-  for (int l = 0; l <= L; ++l)
+  for (int l = 0; l <= L; ++l) {
+    float b = 0.0f;
 #pragma unroll
     for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
       A = __fmaf_rn(lamd[k], S1[k], A);
-      B = __fmaf_rn((float)(2 * l + 1) * lam[k], S1[k], B);
+      b = __fmaf_rn(lam[k], S1[k], b);
     }
+    B = __fmaf_rn((float)(2 * l + 1), b, B);
+  }
   float V[3];
   GmpMcsh<L>::shift_contract(lam, S1, V);
   if (r2 > 0.0f) {
@@ -560,7 +578,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
-      radial4d<L>(tab_e, P.kmax, sg, r2h, r2l, R);
+      radial4d<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
@@ -768,7 +786,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           for (int qq = 0; qq < P.kmax; ++qq) {
             // slot v of the block holds quantity v for the 4 sigmas of the group
             const float* ent = tab_e + ((s / 4) * P.kmax + qq) * gmp_rad_block(L) * 4 + (s % 4);
-            const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
+            const float E = gmp_ex2(-__fmul_rn(ent[0], r2h));  // FP32 argument: derivatives only
             R = __fmaf_rn(ent[4 * (2 + l)], E, R);
             R1 = __fmaf_rn(ent[4 * (3 + l)], E, R1);
           }
