@@ -703,3 +703,88 @@ int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64
   }
   return bad ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Strain derivative (virial).                                          */
+/* ------------------------------------------------------------------ */
+
+/* L = sum_i sum_f g[i,f] f_i.  Under a homogeneous strain x -> (I + eps) x
+ * applied to positions and lattice vectors alike, every pair displacement
+ * becomes (I + eps) d, so per structure s
+ *   W[s][a][b] = dL/d eps_ab = sum over the pairs of s of (dL/dd)_a d_b,
+ *   dL/dd = sum_f g[i,f] d f_i / d d   (the per-pair chain rule of the
+ * Jacobian rows above).  W_abs (optional) [s][a][b]: the cancellation-free
+ * scale sum over pairs of |g| . |d f/d d| |d_b|. */
+int oracle_virial(const oracle_problem *P, const double *gcoef, double *W, double *W_abs) {
+  octx X;
+  if (ctx_init(&X, P)) return -1;
+  const int F = X.F;
+  const int64_t N = P->atom_off[P->n_struct];
+  memset(W, 0, sizeof(double) * 9 * P->n_struct);
+  if (W_abs) memset(W_abs, 0, sizeof(double) * 9 * P->n_struct);
+  int bad = 0;
+#pragma omp parallel
+  {
+    opair *buf = NULL;
+    int64_t cap = 0;
+    double *mu = (double *)calloc((size_t)X.ncol + 1, sizeof(double));
+    double *ab = (double *)calloc((size_t)X.ncol + 1, sizeof(double));
+    double *t = (double *)calloc((size_t)X.ncol + 1, sizeof(double));
+    double *dt = (double *)calloc(3 * (size_t)X.ncol + 1, sizeof(double));
+    double *Wt = (double *)calloc(9 * (size_t)P->n_struct, sizeof(double));
+    double *Wa = (double *)calloc(9 * (size_t)P->n_struct, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t m = list_neighbors(P, i, &buf, &cap);
+      if (m < 0) { bad = 1; continue; }
+      const int s = struct_of(P, i);
+      const double *gi = gcoef + i * F;
+      memset(mu, 0, sizeof(double) * X.ncol);
+      memset(ab, 0, sizeof(double) * X.ncol);
+      for (int64_t u = 0; u < m; ++u) {
+        double r;
+        pair_terms(&X, P->species[buf[u].j], buf[u].d, t, NULL, &r, NULL);
+        for (int cI = 0; cI < X.ncol; ++cI) { mu[cI] += t[cI]; ab[cI] += fabs(t[cI]); }
+      }
+      for (int64_t u = 0; u < m; ++u) {
+        double r, dr[3];
+        pair_terms(&X, P->species[buf[u].j], buf[u].d, t, dt, &r, dr);
+        double v[3] = {0.0, 0.0, 0.0}, vabs = 0.0;
+        int f = 0;
+        for (int o = 0; o < P->n_orders; ++o) {
+          int l = P->orders[o];
+          if (l < 0) {
+            for (int a = 0; a < 3; ++a) v[a] += gi[f] * dr[a];
+            vabs += fabs(gi[f]) * sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+            ++f;
+            continue;
+          }
+          for (int sg = 0; sg < X.n_sig; ++sg, ++f) {
+            for (int ci = 0; ci < X.T.ncomp[l]; ++ci) {
+              int col = col_of(&X, o, sg, ci);
+              double wmu2 = 2.0 * X.T.comp[l][ci].w * mu[col];
+              for (int a = 0; a < 3; ++a) v[a] += gi[f] * wmu2 * dt[3 * col + a];
+              vabs += fabs(gi[f]) * 2.0 * X.T.comp[l][ci].w * ab[col] *
+                      sqrt(dt[3 * col] * dt[3 * col] + dt[3 * col + 1] * dt[3 * col + 1] +
+                           dt[3 * col + 2] * dt[3 * col + 2]);
+            }
+          }
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            Wt[9 * s + 3 * a + b] += v[a] * buf[u].d[b];
+            Wa[9 * s + 3 * a + b] += vabs * fabs(buf[u].d[b]);
+          }
+      }
+    }
+#pragma omp critical
+    {
+      for (int64_t k = 0; k < 9 * (int64_t)P->n_struct; ++k) {
+        W[k] += Wt[k];
+        if (W_abs) W_abs[k] += Wa[k];
+      }
+    }
+    free(buf); free(mu); free(ab); free(t); free(dt); free(Wt); free(Wa);
+  }
+  return bad ? -1 : 0;
+}

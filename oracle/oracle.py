@@ -76,6 +76,7 @@ def lib():
             L.oracle_neighbor_lists.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             L.oracle_features.argtypes = [P, C.c_int64, vp, vp, vp, vp]
             L.oracle_point_features.argtypes = [P, C.c_int64, vp, vp, vp, vp]
+            L.oracle_virial.argtypes = [P, vp, vp, vp]
             L.oracle_jacobian_counts.argtypes = [P, C.c_int64, vp, vp]
             L.oracle_jacobian_rows.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
             _lib = L
@@ -195,6 +196,19 @@ def point_features(w, points, point_struct, want_abs=False):
                                    fa.ctypes.data if want_abs else None):
         raise ValueError("oracle_point_features failed")
     return (f, fa) if want_abs else f
+
+
+def virial(w, g, want_abs=False):
+    """Per-structure strain derivative W[s,a,b] = dL/d eps_ab of
+    L = sum_i sum_f g[i,f] f_i (positions and lattice vectors strained
+    alike), i.e. the sum over the structure's pairs of (dL/dd)_a d_b."""
+    P = Problem(w)
+    gg = np.ascontiguousarray(g, np.float64)
+    W = np.zeros((w.n_struct, 3, 3), np.float64)
+    Wa = np.zeros((w.n_struct, 3, 3), np.float64) if want_abs else None
+    if lib().oracle_virial(C.byref(P.s), gg.ctypes.data, W.ctypes.data, Wa.ctypes.data if want_abs else None):
+        raise ValueError("oracle_virial failed")
+    return (W, Wa) if want_abs else W
 
 
 def jacobian_rows(w, centers=None, want_abs=False):

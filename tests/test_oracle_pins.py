@@ -400,3 +400,56 @@ def test_point_features_special_points(oracle_mod):
     cl = next(s for s in range(w.n_struct) if not w.pbc[s].any())
     far = w.positions[w.atom_off[cl]:w.atom_off[cl + 1]].max(0) + w.cutoff + 0.01
     assert np.all(oracle_mod.point_features(w, far[None, :], [cl]) == 0.0)
+
+
+# ------------------------------------------------------------ strain derivative
+def _strained_loss(oracle_mod, w, g, eps):
+    M = np.eye(3) + eps
+    w2 = w.replace(positions=w.positions @ M.T, cells=w.cells @ M.T)
+    return float((oracle_mod.features(w2) * g).sum())
+
+
+@pytest.mark.parametrize("kind", ["periodic", "cluster", "triclinic"])
+def test_virial_matches_strained_central_differences(oracle_mod, kind):
+    # W_ab = dL/d eps_ab with positions and lattice vectors strained alike,
+    # against central differences of the oracle's own features (h = 1e-5;
+    # the neighbor lists at +-h are checked to be the same)
+    if kind == "periodic":
+        w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2])
+    elif kind == "cluster":
+        b = synth.batched10k(n_struct=2)
+        a0, a1 = int(b.atom_off[1]), int(b.atom_off[2])
+        w = b.replace(positions=b.positions[a0:a1], species=b.species[a0:a1],
+                      atom_off=np.array([0, a1 - a0], np.int64), cells=b.cells[1:2], pbc=b.pbc[1:2],
+                      orders=[-1, 0, 1, 3], sigmas=[0.3, 0.8])
+    else:
+        rng = np.random.default_rng(4)
+        tri = np.array([[7.0, 0.0, 0.0], [2.5, 6.5, 0.0], [1.0, 1.5, 8.0]])
+        pos = rng.uniform(0, 1, (24, 3)) @ tri
+        base = synth.workload("random64_box")
+        w = base.replace(positions=pos, species=rng.integers(0, 2, 24).astype(np.int32),
+                         atom_off=np.array([0, 24], np.int64), cells=tri[None], pbc=np.array([[1, 0, 1]], np.uint8),
+                         orders=[0, 1, 2])
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=12).astype(np.float64)
+    W, Wa = oracle_mod.virial(w, g, want_abs=True)
+    h = 1e-5
+    n0 = oracle_mod.neighbors(w)[0]
+    for a, b in [(0, 0), (1, 1), (2, 2), (0, 1), (2, 0), (1, 2)]:
+        E = np.zeros((3, 3))
+        E[a, b] = h
+        for sgn in (1, -1):
+            M = np.eye(3) + sgn * E
+            w2 = w.replace(positions=w.positions @ M.T, cells=w.cells @ M.T)
+            assert np.array_equal(oracle_mod.neighbors(w2)[0], n0)
+        fd = (_strained_loss(oracle_mod, w, g, E) - _strained_loss(oracle_mod, w, g, -E)) / (2 * h)
+        assert abs(fd - W[0, a, b]) <= 1e-8 * Wa[0].max(), (kind, a, b, fd, W[0, a, b])
+
+
+def test_virial_is_symmetric(oracle_mod):
+    # rotation invariance of the features: dL/d(theta) = 0 for every
+    # infinitesimal rotation, i.e. W - W^T = 0, structure by structure
+    w = synth.batched10k(n_struct=6)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=13).astype(np.float64)
+    W, Wa = oracle_mod.virial(w, g, want_abs=True)
+    for s in range(w.n_struct):
+        assert np.abs(W[s] - W[s].T).max() <= 1e-12 * max(Wa[s].max(), 1e-300)
