@@ -122,6 +122,22 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t *atom
                              const int32_t *species, const float *grad_feat,
                              float *features, float *grad_pos, void *stream);
 
+/* gmp_featurize_vjp plus the strain derivative of each structure (the
+ * virial, for stresses; an extension beyond the paper's outputs): with
+ * L = sum_i sum_f grad_feat[i, f] * features[i, f] and a homogeneous strain
+ * eps applied to positions and lattice vectors alike (x -> (I + eps) x, so
+ * every neighbor displacement d -> (I + eps) d),
+ *   virial[s, a, b] = dL / d eps_ab = sum over the neighbor images of the
+ *   centers of structure s of (dL/dd)_a * d_b.
+ * virial [S, 3, 3] float64 out, device or host like the other outputs.
+ * The stress of an energy E(features) is virial / cell volume with
+ * grad_feat = dE/dfeatures.  Symmetric up to rounding (rotation invariance). */
+gmp_status gmp_featurize_vjp_virial(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                                    const double *pos, const double *cell, const uint8_t *pbc,
+                                    const int32_t *species, const float *grad_feat,
+                                    float *features, float *grad_pos, double *virial,
+                                    void *stream);
+
 /* Features and the dense per-(center, neighbor atom) Jacobian
  * (Examples: entry["feature_primes"]).  Row i lists the distinct atoms j
  * whose position moves feature row i (the center itself included), images

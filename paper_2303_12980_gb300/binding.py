@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgmp.so")
 GMP_OK = 0
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
-EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp",
+EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_vjp_virial",
            "gmp_featurize_grad", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
            "gmp_sync", "gmp_profile", "gmp_profile_read",
            "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         common = [vp, i32, vp, vp, vp, vp, vp]
         L.gmp_featurize.argtypes = common + [vp, vp]
         L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
+        L.gmp_featurize_vjp_virial.argtypes = common + [vp, vp, vp, vp, vp]
         L.gmp_featurize_grad.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_featurize_points.argtypes = common + [vp, vp, vp, vp]
@@ -249,6 +250,27 @@ class GMPFeaturizer:
                                               pbc.ctypes.data, _ptr(species), _ptr(grad_feat), _ptr(feat),
                                               _ptr(gp), _stream_ptr(stream, on_dev)))
         return feat, gp
+
+    def featurize_vjp_virial(self, pos, species, atom_off, cell, pbc, grad_feat, stream=None):
+        """(features, grad_pos [N,3] float32, virial [S,3,3] float64): the
+        VJP plus, per structure, dL/d(strain) = sum over pairs of (dL/dd) d^T."""
+        torch = _torch()
+        off, cell, pbc = self._struct(atom_off, cell, pbc)
+        pos, species, on_dev = self._inputs(pos, species)
+        N = int(off[-1])
+        if isinstance(grad_feat, np.ndarray):
+            grad_feat = torch.from_numpy(np.ascontiguousarray(grad_feat, np.float32))
+        if grad_feat.dtype != torch.float32 or tuple(grad_feat.shape) != (N, self.num_features):
+            raise ValueError("grad_feat must be float32 [N, F]")
+        grad_feat = grad_feat.contiguous()
+        feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos)
+        gp = self._alloc((N, 3), torch.float32, on_dev, pos)
+        vir = self._alloc((off.size - 1, 3, 3), torch.float64, on_dev, pos)
+        self._check(self._L.gmp_featurize_vjp_virial(self._h, off.size - 1, off.ctypes.data, _ptr(pos),
+                                                     cell.ctypes.data, pbc.ctypes.data, _ptr(species),
+                                                     _ptr(grad_feat), _ptr(feat), _ptr(gp), _ptr(vir),
+                                                     _stream_ptr(stream, on_dev)))
+        return feat, gp, vir
 
     def featurize_grad(self, pos, species, atom_off, cell, pbc, stream=None):
         """(features [N,F], jac_off [N+1] int64, jac_j [nnz] int32, jac [nnz,F,3] float32):

@@ -18,9 +18,25 @@ cudaError_t gmp_launch_struct_of(const int64_t* d_atom_off, int n_struct, int32_
 
 namespace {
 
+// Device buffer that grows on demand and frees itself (move-only).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
   cudaError_t ensure(size_t need) {
     if (need <= bytes && p) return cudaSuccess;
     if (p) cudaFree(p);
@@ -83,7 +99,7 @@ struct gmp_ctx {
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // FP64 radial constants [n_el][n_sigmas][kmax][3] for the refinement kernel
   DevBuf flagq;  // queued ill-conditioned features
-  DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp;
+  DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp, stage_virial;
   DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
   int64_t P = 0;  // pairs of the last neighbor build
   int max_m = 0;
@@ -700,7 +716,7 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       return bad("device allocation for tables failed");
     }
     P.rad = pd.rad.as<float>();
-    h->passes.push_back(pd);
+    h->passes.push_back(std::move(pd));
   }
   {
     std::vector<float> dt((size_t)h->n_el * h->kmax * GMP_DENS_STRIDE, 0.0f);
@@ -820,20 +836,37 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
   return GMP_OK;
 }
 
-gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
-                             const double* cell, const uint8_t* pbc, const int32_t* species,
-                             const float* grad_feat, float* features, float* grad_pos, void* stream) {
+static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                           const double* cell, const uint8_t* pbc, const int32_t* species,
+                           const float* grad_feat, float* features, float* grad_pos, double* virial,
+                           void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int64_t N = 0;
   gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
   if (r != GMP_OK) return r;
-  if (N == 0) return GMP_OK;
+  if (N == 0) {
+    if (virial) {
+      if (is_device_ptr(virial)) {
+        GMP_CK(cudaMemsetAsync(virial, 0, sizeof(double) * 9 * n_struct, st), "zero virial");
+      } else {
+        std::memset(virial, 0, sizeof(double) * 9 * n_struct);
+      }
+    }
+    return GMP_OK;
+  }
   if (!grad_feat || !grad_pos) return fail(h, GMP_ERR_INVALID_ARG, "grad_feat and grad_pos are required");
   Io io;
   if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
   const float* gf = grad_feat;
   float* feat = features;
   float* gp = grad_pos;
+  double* vir = virial;
+  if (virial && io.host) {
+    GMP_CK(h->stage_virial.ensure(sizeof(double) * 9 * n_struct), "stage virial");
+    vir = h->stage_virial.as<double>();
+  } else if (virial && !is_device_ptr(virial)) {
+    return fail(h, GMP_ERR_INVALID_ARG, "virial must be a device pointer when inputs are");
+  }
   if (io.host) {
     GMP_CK(h->stage_gradf.ensure(sizeof(float) * N * h->F), "stage grad_feat");
     GMP_CK(cudaMemcpyAsync(h->stage_gradf.p, grad_feat, sizeof(float) * N * h->F, cudaMemcpyHostToDevice, st), "h2d grad_feat");
@@ -847,8 +880,8 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
   }
   const bool use_graph = h->graph_on && !io.host;
   const std::vector<uintptr_t> key = {1, (uintptr_t)io.pos, (uintptr_t)io.species, (uintptr_t)gf, (uintptr_t)feat,
-                                      (uintptr_t)gp, (uintptr_t)st, (uintptr_t)N, (uintptr_t)n_struct,
-                                      (uintptr_t)h->struct_gen};
+                                      (uintptr_t)gp, (uintptr_t)vir, (uintptr_t)st, (uintptr_t)N,
+                                      (uintptr_t)n_struct, (uintptr_t)h->struct_gen};
   if (use_graph && (r = replay_graph(h, key, st)) != GMP_ERR_CAPACITY) return r;
   // buffers first (no allocation may happen while a graph is captured)
   GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
@@ -859,6 +892,7 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
   gmp_status q = build_neighbors(h, n_struct, io.pos, io.species, N, st, false, capture);
   if (q != GMP_OK) return q;
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
+  if (vir) GMP_CK(cudaMemsetAsync(vir, 0, sizeof(double) * 9 * n_struct, st), "memset virial");
   if ((q = begin_compute(h, N, st)) != GMP_OK) return q;
   for (size_t g = 0; g < h->passes.size(); ++g) {
     const PassData& pd = h->passes[g];
@@ -867,7 +901,7 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     float* fout = feat ? feat : h->stage_feat.as<float>();
     gmpk::KParams K = base_params(h, pd, (int)g, N);
     K.features = fout;
-    if (pd.vjp_fused) {
+    if (pd.vjp_fused && !vir) {
       K.grad_feat = gf;
       K.grad_acc = h->grad_acc.as<double>();
       GMP_CK(prof_mark(h, 2, true, st), "profile");
@@ -883,8 +917,12 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     K.flags = nullptr;
     K.grad_feat = gf;
     K.grad_acc = h->grad_acc.as<double>();
+    K.virial = vir;
+    K.center_struct = h->struct_of.as<int32_t>();
     GMP_CK(prof_mark(h, 2, true, st), "profile");
-    GMP_CK(launch_compute(pd.L, GMP_KIND_BACKWARD, pd.NS, K, pd.bwd, st, h->sm_count, &h->launches), "backward");
+    GMP_CK(launch_compute(pd.L, vir ? GMP_KIND_BACKWARD_VIRIAL : GMP_KIND_BACKWARD, pd.NS, K, pd.bwd, st,
+                          h->sm_count, &h->launches),
+           "backward");
     GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
   GMP_CK(prof_mark(h, 3, true, st), "profile");
@@ -899,9 +937,25 @@ gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom
     if (features)
       GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
     GMP_CK(cudaMemcpyAsync(grad_pos, gp, sizeof(float) * N * 3, cudaMemcpyDeviceToHost, st), "d2h grad");
+    if (virial)
+      GMP_CK(cudaMemcpyAsync(virial, vir, sizeof(double) * 9 * n_struct, cudaMemcpyDeviceToHost, st), "d2h virial");
     GMP_CK(cudaStreamSynchronize(st), "sync");
   }
   return GMP_OK;
+}
+
+gmp_status gmp_featurize_vjp(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                             const double* cell, const uint8_t* pbc, const int32_t* species,
+                             const float* grad_feat, float* features, float* grad_pos, void* stream) {
+  return vjp_impl(h, n_struct, atom_off, pos, cell, pbc, species, grad_feat, features, grad_pos, nullptr, stream);
+}
+
+gmp_status gmp_featurize_vjp_virial(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                                    const double* cell, const uint8_t* pbc, const int32_t* species,
+                                    const float* grad_feat, float* features, float* grad_pos, double* virial,
+                                    void* stream) {
+  if (!virial) return fail(h, GMP_ERR_INVALID_ARG, "virial is required");
+  return vjp_impl(h, n_struct, atom_off, pos, cell, pbc, species, grad_feat, features, grad_pos, virial, stream);
 }
 
 gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
@@ -1280,18 +1334,12 @@ void gmp_destroy(gmp_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   for (auto& pd : h->passes) pd.rad.release();
-  DevBuf* bufs[] = {&h->mu, &h->ktab, &h->flagq, &h->dens, &h->structs, &h->grid, &h->atom_off, &h->struct_of, &h->bbox, &h->atom_xh,
-                    &h->atom_xl, &h->atom_u, &h->atom_bin, &h->atom_rng, &h->atom_y, &h->bin_count, &h->bin_cursor, &h->bin_start,
-                    &h->bin_y, &h->counts, &h->nbr_off, &h->scan_tmp, &h->pairs, &h->scalars, &h->grad_acc,
-                    &h->jac_counts, &h->stage_pos, &h->stage_species, &h->stage_feat, &h->stage_gradf,
-                    &h->stage_gradp};
-  for (DevBuf* b : bufs) b->release();
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->h_small) cudaFreeHost(h->h_small);
   for (auto& v : h->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (h->ev) cudaEventDestroy(h->ev);
-  delete h;
+  delete h;  // the device buffers free themselves, with this device current
 }
 
 }  // extern "C"

@@ -20,7 +20,8 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
   const int tile = (kind == GMP_KIND_FORWARD && shape.tile == 32) ? 32 : 16;
   void (*fn)(KParams) = kind == GMP_KIND_FORWARD    ? (tile == 32 ? k_forward<L, NS, 32> : k_forward<L, NS, 16>)
                         : kind == GMP_KIND_VJP      ? k_vjp<L, NS>
-                        : kind == GMP_KIND_BACKWARD ? k_backward<L, NS>
+                        : kind == GMP_KIND_BACKWARD ? k_backward<L, NS, false>
+                        : kind == GMP_KIND_BACKWARD_VIRIAL ? k_backward<L, NS, true>
                                                     : k_jacobian<L, NS>;
   auto smem_of = [&](int w) {
     return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w) : smem_bytes<L, NS, 16>(K.pass, w);

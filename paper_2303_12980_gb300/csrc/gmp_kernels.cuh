@@ -124,6 +124,8 @@ struct KParams {
   int32_t* jac_j;
   float* jac;             // [nnz, F, 3]
   int32_t* counter;
+  const int32_t* center_struct;  // [N] structure of each center (virial)
+  double* virial;                // [S, 3, 3] strain derivative accumulators (virial)
   // features too ill-conditioned for FP32 (recomputed in FP64 afterwards)
   unsigned long long* flags;  // packed (center, order, sigma, column)
   int32_t* flag_count;
@@ -558,8 +560,10 @@ __device__ __forceinline__ void pair_gradient(const float* lam, const float* lam
 
 // ------------------------------------------------------------------------
 // Backward only: moments come from the forward kernel (K.mu_out, read), the
-// per-pair terms are recomputed.  Lane = pair.
-template <int L, int NS>
+// per-pair terms are recomputed.  Lane = pair.  With VIRIAL, also the
+// strain derivative of the structure: sum over pairs of (dL/dd)_a d_b
+// (positions and lattice vectors strained alike move every d to (I+eps) d).
+template <int L, int NS, bool VIRIAL = false>
 __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
                                                const float* __restrict__ Lam, float gd) {
@@ -567,6 +571,9 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
   const GmpPass& P = K.pass;
   const int lane = threadIdx.x & 31;
   float own[3] = {0.0f, 0.0f, 0.0f};
+  float wv[VIRIAL ? 9 : 1];
+#pragma unroll
+  for (int v = 0; v < (VIRIAL ? 9 : 1); ++v) wv[v] = 0.0f;
   for (int pp = lane; pp < M; pp += 32) {
     float dx, dy, dz, r2h, r2l;
     int e, j;
@@ -617,6 +624,23 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     own[0] -= g[0];
     own[1] -= g[1];
     own[2] -= g[2];
+    if constexpr (VIRIAL) {
+      const float d[3] = {dx, dy, dz};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) wv[3 * a + b] = __fmaf_rn(g[a], d[b], wv[3 * a + b]);
+    }
+  }
+  if constexpr (VIRIAL) {
+    double* wrow = K.virial + 9 * (int64_t)K.center_struct[i];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) {
+      double o = (double)wv[v];
+#pragma unroll
+      for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
+      if (lane == 0) atomicAdd(wrow + v, o);
+    }
   }
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
@@ -660,8 +684,8 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   }
 }
 
-template <int L, int NS>
-__global__ void __launch_bounds__(384) k_backward(KParams K) {
+template <int L, int NS, bool VIRIAL = false>
+__global__ void __launch_bounds__(VIRIAL ? 256 : 384) k_backward(KParams K) {
   using SH = Shape<L, NS>;
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
@@ -683,7 +707,7 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
     const float* grow = K.grad_feat + i * P.F;
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS>(K, s_rad, s_dens, i, p0, M, Lam, gd);
+    backward_sweep<L, NS, VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd);
     __syncwarp();
   }
 }

@@ -8,6 +8,7 @@
 #define GMP_KIND_VJP 1
 #define GMP_KIND_JACOBIAN 2
 #define GMP_KIND_BACKWARD 3
+#define GMP_KIND_BACKWARD_VIRIAL 4  // backward + per-structure strain derivative
 
 namespace gmpk {
 struct KParams;

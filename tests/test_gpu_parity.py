@@ -319,3 +319,27 @@ def test_mixed_sign_density_tables(torch, oracle_mod):
     record("mixed_sign/random64_box", features_max_rel_err=ferr.max(), vjp_max_rel_err=gerr.max())
     assert ferr.max() <= FEAT_TOL, ferr.max()
     assert gerr.max() <= GRAD_TOL, gerr.max()
+
+
+@pytest.mark.parametrize("name", ["random64_box", "batched300", "fcc4096"])
+def test_virial_parity(torch, oracle_mod, name):
+    """Per-structure strain derivative against the oracle; the gradient and
+    features of the same call equal gmp_featurize_vjp's."""
+    w = wl(name)
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=21)
+    gd = torch.from_numpy(g).cuda()
+    feat, gp, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, gd)
+    f2, gp2 = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, gd)
+    torch.cuda.synchronize()
+    assert torch.equal(feat, f2)
+    assert torch.allclose(gp, gp2, rtol=0, atol=1e-6 * float(gp2.abs().max()))
+    W, Wa = oracle_mod.virial(w, g.astype(np.float64), want_abs=True)
+    V = vir.cpu().numpy()
+    err = np.abs(V - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    record(f"virial/{name}", max_rel_err=err.max(), structures=w.n_struct)
+    assert err.max() <= GRAD_TOL, err.max()
+    # host buffers give the same result
+    _, _, vh = F.featurize_vjp_virial(w.positions, w.species, w.atom_off, w.cells, w.pbc, g)
+    assert np.allclose(np.asarray(vh), V, rtol=1e-6, atol=0)
