@@ -103,6 +103,12 @@ struct gmp_ctx {
   DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
   int64_t P = 0;  // pairs of the last neighbor build
   int max_m = 0;
+  // Pair layout of the last build: CSR by center (nbr_off) or, after a
+  // single-pass build, one block per center with ranges in nbr_rng [2N].
+  DevBuf nbr_rng;
+  bool rng_mode = false;
+  int64_t last_nc = -1;    // batch (centers, description) the P / max_m above belong to
+  int64_t last_gen = -1;
   // pinned host scratch for small readbacks
   int64_t* h_small = nullptr;
   std::string err;
@@ -374,13 +380,46 @@ gmp_status bin_atoms(gmp_ctx* h, int32_t S, const double* pos, const int32_t* sp
 // h->pairs / h->nbr_off.  Synchronises `st` once (to size the pair buffer)
 // unless capturing.
 gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const double* pos, cudaStream_t st,
-                          bool sorted, bool capture) {
+                          bool sorted, bool capture, bool single_ok = false) {
   int64_t* L = &h->launches;
   uint32_t* d_err = h->scalars.as<uint32_t>();
   int32_t* d_maxm = reinterpret_cast<int32_t*>(d_err + 1);
+  unsigned long long* d_cursor = reinterpret_cast<unsigned long long*>(h->scalars.as<char>() + 16);
+  h->rng_mode = false;
   // the error word is cleared after it is read (below), so a condition
   // raised after the read of the previous call is reported here
   GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
+  if (single_ok && !sorted && !capture && h->last_nc == NC && h->last_gen == h->struct_gen && h->P > 0) {
+    // Repeated batch: one enumeration pass, each center allocating its
+    // block of records, with capacities from the last build + 12.5%.
+    const int64_t cap = h->P + h->P / 8 + 4096;
+    int keys = 32;
+    while (keys < h->max_m + h->max_m / 8 + 8) keys <<= 1;
+    if ((size_t)keys * 8 <= 200 * 1024) {
+      GMP_CK(h->pairs.ensure(sizeof(GmpPair) * cap), "pairs");
+      GMP_CK(h->nbr_rng.ensure(sizeof(int64_t) * 2 * NC), "nbr_rng");
+      GMP_CK(cudaMemsetAsync(d_cursor, 0, 8, st), "memset cursor");
+      GMP_CK(gmp_launch_neighbor_pass(1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
+                                      h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
+                                      h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, nullptr, nullptr,
+                                      h->pairs.as<GmpPair>(), cap, keys, d_maxm, d_err, st, h->sm_count, L, d_cursor,
+                                      h->nbr_rng.as<int64_t>()),
+             "neighbor single pass");
+      GMP_CK(cudaMemcpyAsync(h->h_small, d_cursor, 8, cudaMemcpyDeviceToHost, st), "read P");
+      GMP_CK(cudaMemcpyAsync(h->h_small + 1, d_err, 8, cudaMemcpyDeviceToHost, st), "read err");
+      GMP_CK(cudaStreamSynchronize(st), "neighbor sync");
+      const uint32_t w = (uint32_t)(h->h_small[1] & 0xffffffffu);
+      if (!w) {
+        h->P = h->h_small[0];
+        h->max_m = (int)(h->h_small[1] >> 32);
+        h->rng_mode = true;
+        return GMP_OK;
+      }
+      GMP_CK(cudaMemsetAsync(d_err, 0, 8, st), "clear err");  // error word and maxm
+      if (w != GMP_DEV_CAPACITY) return decode_device_error(h, w);
+      // outgrew the guessed capacity: count exactly below
+    }
+  }
   GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
                                   h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
                                   h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, h->counts.as<int64_t>(),
@@ -410,6 +449,8 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
   }
   h->P = h->h_small[0];
   h->max_m = maxm;
+  h->last_nc = NC;
+  h->last_gen = h->struct_gen;
   int keys = 32;
   while (keys < maxm) keys <<= 1;
   if ((size_t)keys * 8 > 200 * 1024)
@@ -434,7 +475,7 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
   if (r != GMP_OK) return r;
   const GmpCenters C{h->struct_of.as<int32_t>(), pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                      h->atom_rng.as<int4>(), h->atom_y.as<float4>()};
-  if ((r = neighbor_lists(h, C, N, pos, st, sorted, capture)) != GMP_OK) return r;
+  if ((r = neighbor_lists(h, C, N, pos, st, sorted, capture, true)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 0, false, st), "profile");
   return GMP_OK;
 }
@@ -450,7 +491,8 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   std::memset(&K, 0, sizeof(K));
   K.pass = pd.pass;
   K.N = N;
-  K.nbr_off = h->nbr_off.as<int64_t>();
+  K.nbr_beg = h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>();
+  K.nbr_end = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
   K.pairs = h->pairs.as<GmpPair>();
   K.counter = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 2);
   K.flags = h->flagq.as<unsigned long long>();
@@ -477,7 +519,9 @@ gmp_status refine(gmp_ctx* h, int64_t N, const double* pos, float* features, cud
                            reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3), flag_capacity(N),
                            features, h->F, pos, center_pos ? center_pos : pos,
                            center_struct ? center_struct : h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
-                           h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->ktab.as<double>(),
+                           h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>(),
+                           h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1,
+                           h->pairs.as<GmpPair>(), h->ktab.as<double>(),
                            (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->scalars.as<uint32_t>(),
                            h->sm_count, st, &h->launches),
          "refine");
@@ -1078,7 +1122,9 @@ gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t* a
            "point prepare");
     const GmpCenters C{h->pt_struct.as<int32_t>(), pts, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(),
                        h->pt_rng.as<int4>(), h->pt_y.as<float4>()};
+    h->last_nc = -1;  // the capacities below describe the points, not the atoms
     if ((r = neighbor_lists(h, C, NP, io.pos, st, false, false)) != GMP_OK) return r;
+    h->last_nc = -1;
     GMP_CK(prof_mark(h, 0, false, st), "profile");
     if ((r = begin_compute(h, NP, st)) != GMP_OK) return r;
     GMP_CK(prof_mark(h, 1, true, st), "profile");

@@ -196,16 +196,20 @@ cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* 
                                      const int32_t* point_struct, int64_t n_points, const double* points,
                                      float4* pt_xh, float4* pt_xl, int4* pt_rng, float4* pt_y,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
-// fill: 0 = count only, 1 = records in enumeration order (deterministic),
+// fill: 0 = count only, 1 = records grouped by species (deterministic),
 // 2 = records sorted by (neighbor atom, image).  Centers C [N]; neighbors
-// are the binned atoms (pos, atom_xh, atom_xl).
+// are the binned atoms (pos, atom_xh, atom_xl).  Records go to the CSR
+// offsets (from a count pass), or, with cursor (fill 1 only), to blocks
+// allocated from *cursor whose ranges are written to rng[i], rng[N + i].
+// Over-capacity blocks set GMP_DEV_CAPACITY.
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const GmpCenters& C, int64_t N, double cutoff,
                                      const double* pos, const float4* atom_xh, const float4* atom_xl,
                                      const int32_t* bin_start, const float4* bin_y, const int2* bin_je, int n_el,
                                      int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
-                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches,
+                                     unsigned long long* cursor = nullptr, int64_t* rng = nullptr);
 cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
                                       int64_t* counts, cudaStream_t stream, int sm_count,
                                       int64_t* launches);
@@ -213,8 +217,8 @@ cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* gra
                                    cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
                               float* features, int F, const double* pos, const double* center_pos,
-                              const int32_t* center_struct,
-                              const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
+                              const int32_t* center_struct, const GmpStruct* structs, const int64_t* nbr_beg,
+                              const int64_t* nbr_end, const GmpPair* pairs,
                               const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
                               cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,

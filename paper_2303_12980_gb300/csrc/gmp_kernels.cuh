@@ -114,7 +114,8 @@ __host__ __device__ inline int dens_elem_stride(int kmax) {
 struct KParams {
   GmpPass pass;
   int64_t N;
-  const int64_t* nbr_off;
+  const int64_t* nbr_beg;  // pairs of center i: nbr_beg[i] .. nbr_end[i]-1 (CSR: end = beg + 1)
+  const int64_t* nbr_end;
   const GmpPair* pairs;
   float* features;        // [N, F] or null
   float* mu_out;          // [N, nsig, NIND] or null
@@ -487,9 +488,9 @@ __global__ void __launch_bounds__(512) k_forward(KParams K) {
   bool it_ok[SH::Q];
   setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
-    const int64_t p0 = K.nbr_off[i];
-    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
-    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
+    if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
+    const int M = (int)(p1 - p0);
     const float rho = forward_sweep<L, NS, TILE>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch,
                                                  it_ok);
     write_features<L, NS>(K, i, Mu, rho);
@@ -671,9 +672,9 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   bool it_ok[SH::Q];
   setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
-    const int64_t p0 = K.nbr_off[i];
-    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
-    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
+    if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
+    const int M = (int)(p1 - p0);
     const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
     const float* grow = K.grad_feat + i * P.F;
     if (K.features) write_features<L, NS>(K, i, Mu, rho);
@@ -698,9 +699,9 @@ __global__ void __launch_bounds__(VIRIAL ? 256 : 384) k_backward(KParams K) {
   float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
   float* Lam = Mu + SH::TILE * SH::RSTR;
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
-    const int64_t p0 = K.nbr_off[i];
-    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
-    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
+    if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
+    const int M = (int)(p1 - p0);
     const float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
     for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
     __syncwarp();
@@ -738,9 +739,9 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
   constexpr int QF = (8 * 16 + 1 + 31) / 32;  // features per lane (<= 8 orders x 16 sigmas + density)
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
-    const int64_t p0 = K.nbr_off[i];
-    if (K.nbr_off[i + 1] > K.pair_cap) continue;  // over capacity: flagged by the fill pass
-    const int M = (int)(K.nbr_off[i + 1] - p0);
+    const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
+    if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
+    const int M = (int)(p1 - p0);
     const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
     const int nf = P.n_ord * P.nsig;
     if (K.features) write_features<L, NS>(K, i, Mu, rho);

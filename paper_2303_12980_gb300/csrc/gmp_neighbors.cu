@@ -470,6 +470,7 @@ __global__ void k_neighbors(const GmpStruct* __restrict__ S, const GmpGrid* __re
                             const int32_t* __restrict__ bin_start, const float4* __restrict__ bin_y,
                             const int2* __restrict__ bin_je, int n_el,
                             int64_t* __restrict__ counts, const int64_t* __restrict__ offsets,
+                            unsigned long long* __restrict__ cursor, int64_t* __restrict__ rng,
                             GmpPair* __restrict__ pairs, int64_t pair_cap, int max_keys,
                             int32_t* __restrict__ maxm, uint32_t* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char sh_fill[];
@@ -595,14 +596,35 @@ __global__ void k_neighbors(const GmpStruct* __restrict__ S, const GmpGrid* __re
   }
   __syncwarp();
   const int M = count;
-  const int64_t base = offsets[i];
-  if (offsets[i + 1] > pair_cap || M > max_keys) {  // capacities fixed in advance (graph replay)
-    if (lane == 0) atomicOr(err, GMP_DEV_CAPACITY);
-    return;
-  }
-  if (M != (int)(offsets[i + 1] - base)) {
-    if (lane == 0) atomicOr(err, GMP_DEV_TOO_MANY_NEIGHBORS);
-    return;
+  int64_t base;
+  if (cursor) {
+    // single pass (no count pass before): this center's block is allocated
+    // here; its range goes to rng[i], rng[N + i]; a block beyond the
+    // capacity guessed from an earlier call is flagged and the caller
+    // repeats the build with the two-pass scheme
+    unsigned long long b = 0;
+    if (lane == 0) {
+      b = atomicAdd(cursor, (unsigned long long)M);
+      atomicMax(maxm, M);
+    }
+    base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+    const bool over = base + M > pair_cap || M > max_keys;
+    if (lane == 0) {
+      rng[i] = over ? 0 : base;
+      rng[N + i] = over ? 0 : base + M;
+      if (over) atomicOr(err, GMP_DEV_CAPACITY);
+    }
+    if (over) return;
+  } else {
+    base = offsets[i];
+    if (offsets[i + 1] > pair_cap || M > max_keys) {  // capacities fixed in advance (graph replay)
+      if (lane == 0) atomicOr(err, GMP_DEV_CAPACITY);
+      return;
+    }
+    if (M != (int)(offsets[i + 1] - base)) {
+      if (lane == 0) atomicOr(err, GMP_DEV_TOO_MANY_NEIGHBORS);
+      return;
+    }
   }
   if (fill == 2) {
     // bitonic sort of the M keys (padded to a power of two with ~0)
@@ -789,9 +811,10 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      const int32_t* bin_start, const float4* bin_y, const int2* bin_je, int n_el,
                                      int64_t* counts, const int64_t* offsets,
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
-                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
+                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches,
+                                     unsigned long long* cursor, int64_t* rng) {
   (void)sm_count;
-  if (fill < 0 || fill > 2) return cudaErrorInvalidValue;
+  if (fill < 0 || fill > 2 || (cursor && fill != 1)) return cudaErrorInvalidValue;
   const double rc2 = cutoff * cutoff;
   const float rc2hi = (float)rc2;
   const float rc2lo = (float)(rc2 - (double)rc2hi);
@@ -809,7 +832,7 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
   const unsigned blocks = (unsigned)((N + warps - 1) / warps);
   fn<<<blocks, warps * 32, smem, stream>>>(d_structs, d_grid, C, N, (float)cutoff, rc2hi, rc2lo, rc2, pos,
                                            atom_xh, atom_xl, bin_start, bin_y, bin_je, n_el, counts, offsets,
-                                           pairs, pair_cap, max_keys, d_maxm, d_err);
+                                           cursor, rng, pairs, pair_cap, max_keys, d_maxm, d_err);
   ++*launches;
   return cudaGetLastError();
 }

@@ -18,7 +18,8 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
                          int64_t cap, float* __restrict__ features, int F, const double* __restrict__ pos,
                          const double* __restrict__ cpos, const int32_t* __restrict__ cstruct,
                          const GmpStruct* __restrict__ S,
-                         const int64_t* __restrict__ nbr_off, const GmpPair* __restrict__ pairs,
+                         const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
+                         const GmpPair* __restrict__ pairs,
                          const double* __restrict__ ktab, int nsig_total, int kmax, uint32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -37,7 +38,7 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
     const GmpStruct& st = S[cstruct[i]];
     double mu[13];
     for (int k = 0; k < 13; ++k) mu[k] = 0.0;
-    const int64_t p0 = nbr_off[i], p1 = nbr_off[i + 1];
+    const int64_t p0 = nbr_beg[i], p1 = nbr_end[i];
     for (int64_t p = p0 + lane; p < p1; p += 32) {
       const GmpPair pr = pairs[p];
       int nn[3];
@@ -71,10 +72,11 @@ __global__ void k_refine(const unsigned long long* __restrict__ flags, const int
 
 cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
                               float* features, int F, const double* pos, const double* center_pos,
-                              const int32_t* center_struct, const GmpStruct* structs, const int64_t* nbr_off, const GmpPair* pairs,
+                              const int32_t* center_struct, const GmpStruct* structs, const int64_t* nbr_beg,
+                              const int64_t* nbr_end, const GmpPair* pairs,
                               const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
                               cudaStream_t stream, int64_t* launches) {
-  k_refine<<<sm_count * 4, 256, 0, stream>>>(flags, count, cap, features, F, pos, center_pos, center_struct, structs, nbr_off,
+  k_refine<<<sm_count * 4, 256, 0, stream>>>(flags, count, cap, features, F, pos, center_pos, center_struct, structs, nbr_beg, nbr_end,
                                              pairs, ktab, nsig_total, kmax, err);
   ++*launches;
   return cudaGetLastError();

@@ -343,3 +343,24 @@ def test_virial_parity(torch, oracle_mod, name):
     # host buffers give the same result
     _, _, vh = F.featurize_vjp_virial(w.positions, w.species, w.atom_off, w.cells, w.pbc, g)
     assert np.allclose(np.asarray(vh), V, rtol=1e-6, atol=0)
+
+
+def test_repeated_calls_single_pass_neighbors(torch):
+    """A repeated batch builds its neighbor records in one pass with the last
+    call's capacities; a batch that outgrows them falls back to counting.
+    Every call equals a fresh handle's first (two-pass) call bit for bit."""
+    w = wl("fcc4096")
+    F = _featurizer(w)
+    pos, sp = _dev(torch, w)
+    g = torch.from_numpy(synth.upstream_gradient(w.n_atoms, w.n_features, seed=6)).cuda()
+    # the cell stays fixed (same batch description); positions: same, same,
+    # slightly compressed, much compressed (more pairs than the last call's
+    # capacity), back to the start
+    moves = [1.0, 1.0, 0.98, 0.8, 1.0]
+    for k, scale in enumerate(moves):
+        p = (pos * scale).contiguous()
+        f1, g1 = F.featurize_vjp(p, sp, w.atom_off, w.cells, w.pbc, g)
+        f0, g0 = _featurizer(w).featurize_vjp(p, sp, w.atom_off, w.cells, w.pbc, g)
+        torch.cuda.synchronize()
+        assert torch.equal(f1, f0), k
+        assert torch.allclose(g1, g0, rtol=1e-6, atol=1e-6 * float(g0.abs().max())), k
