@@ -112,9 +112,9 @@ def work_model(w, pairs: int):
 
 # DRAM bytes per neighbor pair of the forward and backward kernels, from one
 # ncu capture of fcc_slab32k (same instantiation as the default workload;
-# dram__bytes_read.sum + dram__bytes_write.sum over 4.64 M pairs), scaled by
-# the pairs of the run.  Update together with profiles/ when the kernels change.
-# (profiles/k_forward_k_backward_fcc_slab32k.md: 4,585,082 pairs.)
+# dram__bytes_read.sum + dram__bytes_write.sum over its 4,585,082 pairs),
+# scaled by the pairs of the run.  Update with the ncu summaries whenever
+# the kernels change.
 TRAFFIC_PER_PAIR = {"forward": (147.628288e6 + 79.097856e6) / 4585082,
                     "backward": (265.742336e6 + 3.993344e6) / 4585082}
 

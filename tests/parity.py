@@ -5,8 +5,10 @@ Tolerances (floating point; neighbor sets are compared bit for bit):
   features   : |f_gpu - f_ref| <= FEAT_TOL * max(|f_ref|, FEAT_TAU * F_abs)
   derivatives: |g_gpu - g_ref| <= GRAD_TOL * max(|g_ref|, GRAD_TAU * G_abs)
 F_abs / G_abs are the oracle's cancellation-free scales (the same reduction
-applied to sums of |per-pair contribution|).  See the design doc for how the
-floors follow from FP32 arithmetic.
+applied to sums of |per-pair contribution|).  The floors follow from FP32
+arithmetic: a per-pair contribution carries rounding of ~1e-7 of its own
+magnitude, so a result that cancels below FEAT_TAU (GRAD_TAU) of its
+absolute scale cannot keep the relative bound in FP32.
 
 Both denominators are also floored at FP32_MIN_NORMAL = 2^-126: the outputs
 are FP32, and below the smallest normal FP32 number the format itself has
