@@ -114,6 +114,9 @@ struct gmp_ctx {
   std::string err;
   int64_t launches = 0;
   cudaEvent_t ev = nullptr;
+  // host-buffer calls: copies on a side stream overlap the kernels
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_feat = nullptr, ev_out = nullptr;
   // CUDA-graph replay of whole calls (gmp_set_graph)
   bool graph_on = false;
   bool graph_valid = false;
@@ -815,6 +818,13 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
   }
   if (cudaMallocHost((void**)&h->h_small, 64) != cudaSuccess) { cudaGetLastError(); return bad("pinned alloc failed"); }
   if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return bad("event"); }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_feat, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bad("stream/event creation failed");
+  }
   *out = h;
   return GMP_OK;
 }
@@ -912,8 +922,14 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     return fail(h, GMP_ERR_INVALID_ARG, "virial must be a device pointer when inputs are");
   }
   if (io.host) {
+    // the upstream gradient goes up on the side stream while the neighbor
+    // lists and the forward kernel run; the backward kernel waits for it
     GMP_CK(h->stage_gradf.ensure(sizeof(float) * N * h->F), "stage grad_feat");
-    GMP_CK(cudaMemcpyAsync(h->stage_gradf.p, grad_feat, sizeof(float) * N * h->F, cudaMemcpyHostToDevice, st), "h2d grad_feat");
+    GMP_CK(cudaEventRecord(h->ev_in, st), "event");
+    GMP_CK(cudaStreamWaitEvent(h->side, h->ev_in, 0), "side wait");
+    GMP_CK(cudaMemcpyAsync(h->stage_gradf.p, grad_feat, sizeof(float) * N * h->F, cudaMemcpyHostToDevice, h->side),
+           "h2d grad_feat");
+    GMP_CK(cudaEventRecord(h->ev_in, h->side), "event");
     gf = h->stage_gradf.as<float>();
     if (features) {
       GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "stage features");
@@ -938,6 +954,8 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
   if (vir) GMP_CK(cudaMemsetAsync(vir, 0, sizeof(double) * 9 * n_struct, st), "memset virial");
   if ((q = begin_compute(h, N, st)) != GMP_OK) return q;
+  bool refined = false, waited = false;
+  const bool overlap = io.host && !capture;
   for (size_t g = 0; g < h->passes.size(); ++g) {
     const PassData& pd = h->passes[g];
     // forward kernel (features + moments), then the backward kernel reading
@@ -945,6 +963,10 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     float* fout = feat ? feat : h->stage_feat.as<float>();
     gmpk::KParams K = base_params(h, pd, (int)g, N);
     K.features = fout;
+    if (overlap && !waited && (pd.vjp_fused && !vir)) {
+      GMP_CK(cudaStreamWaitEvent(st, h->ev_in, 0), "wait grad_feat");
+      waited = true;
+    }
     if (pd.vjp_fused && !vir) {
       K.grad_feat = gf;
       K.grad_acc = h->grad_acc.as<double>();
@@ -957,6 +979,24 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     GMP_CK(prof_mark(h, 1, true, st), "profile");
     GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
     GMP_CK(prof_mark(h, 1, false, st), "profile");
+    if (g + 1 == h->passes.size() && feat) {
+      // every feature is final once the last forward kernel and the FP64
+      // refinement ran: its download overlaps the backward kernel
+      GMP_CK(prof_mark(h, 3, true, st), "profile");
+      if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+      GMP_CK(prof_mark(h, 3, false, st), "profile");
+      refined = true;
+      if (overlap && features) {
+        GMP_CK(cudaEventRecord(h->ev_feat, st), "event");
+        GMP_CK(cudaStreamWaitEvent(h->side, h->ev_feat, 0), "side wait");
+        GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, h->side),
+               "d2h features");
+      }
+    }
+    if (overlap && !waited) {
+      GMP_CK(cudaStreamWaitEvent(st, h->ev_in, 0), "wait grad_feat");
+      waited = true;
+    }
     K.features = nullptr;
     K.flags = nullptr;
     K.grad_feat = gf;
@@ -969,20 +1009,31 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
            "backward");
     GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
-  GMP_CK(prof_mark(h, 3, true, st), "profile");
-  if (feat && (q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+  if (feat && !refined) {
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+  }
   GMP_CK(gmp_launch_grad_finish(N, h->grad_acc.as<double>(), gp, st, &h->launches), "grad finish");
-  GMP_CK(prof_mark(h, 3, false, st), "profile");
+  if (overlap && features && !refined) {  // fused path: features final only now
+    GMP_CK(cudaEventRecord(h->ev_feat, st), "event");
+    GMP_CK(cudaStreamWaitEvent(h->side, h->ev_feat, 0), "side wait");
+    GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, h->side),
+           "d2h features");
+  }
   return GMP_OK;
   };
-  if ((r = seq(false)) != GMP_OK) return r;
+  if ((r = seq(false)) != GMP_OK) {
+    if (io.host) cudaStreamSynchronize(h->side);  // no copy may outlive the call
+    return r;
+  }
   if (use_graph && (r = capture_graph(h, key, st, seq)) != GMP_OK) return r;
   if (io.host) {
-    if (features)
-      GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
     GMP_CK(cudaMemcpyAsync(grad_pos, gp, sizeof(float) * N * 3, cudaMemcpyDeviceToHost, st), "d2h grad");
     if (virial)
       GMP_CK(cudaMemcpyAsync(virial, vir, sizeof(double) * 9 * n_struct, cudaMemcpyDeviceToHost, st), "d2h virial");
+    GMP_CK(cudaEventRecord(h->ev_out, h->side), "event");
+    GMP_CK(cudaStreamWaitEvent(st, h->ev_out, 0), "wait d2h features");
     GMP_CK(cudaStreamSynchronize(st), "sync");
   }
   return GMP_OK;
@@ -1385,6 +1436,9 @@ void gmp_destroy(gmp_handle h) {
   for (auto& v : h->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (h->ev) cudaEventDestroy(h->ev);
+  for (cudaEvent_t e : {h->ev_in, h->ev_feat, h->ev_out})
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;  // the device buffers free themselves, with this device current
 }
 

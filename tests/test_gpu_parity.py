@@ -167,6 +167,19 @@ def test_host_buffers_match_device(torch):
     torch.cuda.synchronize()
     fh = F.featurize(w.positions, w.species, w.atom_off, w.cells, w.pbc)
     assert np.array_equal(fd.cpu().numpy(), np.asarray(fh))
+    # the VJP from host buffers (copies overlapped with the kernels on a
+    # side stream) equals the device-buffer call
+    for name in ("random64_box", "batched300"):
+        w = wl(name)
+        pos, sp = _dev(torch, w)
+        F = _featurizer(w)
+        g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=33)
+        fdv, gdv = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+        torch.cuda.synchronize()
+        for _ in range(2):
+            fhv, ghv = F.featurize_vjp(w.positions, w.species, w.atom_off, w.cells, w.pbc, g)
+            assert np.array_equal(fdv.cpu().numpy(), np.asarray(fhv)), name
+            assert np.allclose(gdv.cpu().numpy(), np.asarray(ghv), rtol=1e-6, atol=1e-6 * float(gdv.abs().max()))
 
 
 def test_deterministic(torch):
