@@ -146,6 +146,25 @@ __device__ __forceinline__ float gmp_ex2(float x) {
   return y;
 }
 
+// Packed FP32 pairs: on the sm_100 family one instruction performs the
+// operation for both lanes of a float2, rounded to nearest exactly like
+// the scalar __fmaf_rn / __fadd_rn / __fmul_rn, while taking one issue slot.
+__device__ __forceinline__ float2 gmp_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 gmp_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 gmp_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Two exponentials exp(-B r^2) (B of two sigmas, one pair's r^2), with the
+// operations of gmp_exp_neg below in packed form: bit-identical results.
+// nr2h = -r2hi in both lanes, r2h = r2hi, r2l = r2lo in both lanes.
+__device__ __forceinline__ float2 gmp_exp_neg2(float2 Bhi, float2 Blo, float2 nr2h, float2 r2h, float2 r2l) {
+  const float2 nxh = gmp_mul2(Bhi, nr2h);        // -(Bhi r2hi), rounded as the scalar product
+  float2 xl = gmp_fma2(Bhi, r2h, nxh);
+  xl = gmp_fma2(Bhi, r2l, xl);
+  xl = gmp_fma2(Blo, r2h, xl);
+  const float2 E = make_float2(gmp_ex2(nxh.x), gmp_ex2(nxh.y));
+  return gmp_fma2(E, gmp_mul2(make_float2(-0.69314718055994531f, -0.69314718055994531f), xl), E);
+}
+
 // exp(-B r^2) with B and r^2 given as double-floats: the product is formed
 // to about 2^-44 relative, the SFU takes its high part and the low part is
 // applied to first order, exp2(-(h+l)) = exp2(-h) (1 - ln2 l).

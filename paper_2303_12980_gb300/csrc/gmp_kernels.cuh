@@ -170,12 +170,52 @@ __device__ __forceinline__ void prefetch_pair(const GmpPair* p) {
 // forward needs L+1 orders; the backward one more, for the derivative
 // dR_l/dr^2 = -beta R_{l+1}).  Each 16-byte table load serves the four
 // sigmas of the group.
-// PRECISE: the exponent argument B r^2 as a double-float (features: about
-// 1e-7 relative); otherwise a single FP32 product, whose error of at most
+// Radial factors with the exponent argument B r^2 as a double-float (about
+// 1e-7 relative: the features), computed on packed FP32 pairs (sigmas
+// (0,1) and (2,3) of the group) with the rounding of the scalar form.
+template <int L, int NL = L + 2>
+__device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+                                         float r2l, float (&R)[4][NL]) {
+  constexpr int RB = gmp_rad_block(L);
+  // sigma pairs (0,1) and (2,3) of the group as packed FP32 pairs
+  float2 Rp[2][NL];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int l = 0; l < NL; ++l) Rp[h][l] = make_float2(0.0f, 0.0f);
+  const float2 nr2h = make_float2(-r2h, -r2h), r2h2 = make_float2(r2h, r2h), r2l2 = make_float2(r2l, r2l);
+#pragma unroll 1
+  for (int q = 0; q < kmax; ++q) {
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4 bh = blk[0];
+    const float4 bl = blk[1];
+    float2 E[2];
+    E[0] = gmp_exp_neg2(make_float2(bh.x, bh.y), make_float2(bl.x, bl.y), nr2h, r2h2, r2l2);
+    E[1] = gmp_exp_neg2(make_float2(bh.z, bh.w), make_float2(bl.z, bl.w), nr2h, r2h2, r2l2);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const float4 a = blk[2 + l];
+      Rp[0][l] = gmp_fma2(make_float2(a.x, a.y), E[0], Rp[0][l]);
+      Rp[1][l] = gmp_fma2(make_float2(a.z, a.w), E[1], Rp[1][l]);
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    R[0][l] = Rp[0][l].x;
+    R[1][l] = Rp[0][l].y;
+    R[2][l] = Rp[1][l].x;
+    R[3][l] = Rp[1][l].y;
+  }
+}
+
+// The same radial factors with scalar FP32 operations (the backward kernel
+// keeps its 168-register budget with these; packed pairs need aligned
+// register pairs and spill there).  PRECISE: the double-float exponent
+// argument; otherwise a single FP32 product, whose error of at most
 // 2^-24 B r^2 (B r^2 < 126 before ex2 underflows) leaves each exponential
 // within ~5e-6 relative: ample for derivatives, checked to 1e-4.
 template <int L, int NL = L + 2, bool PRECISE = true>
-__device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+__device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float r2l, float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
 #pragma unroll
@@ -586,7 +626,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
-      radial4d<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
+      radial4s<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
