@@ -153,6 +153,18 @@ __device__ __forceinline__ float2 gmp_fma2(float2 a, float2 b, float2 c) { retur
 __device__ __forceinline__ float2 gmp_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 gmp_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// TwoSum on packed pairs: returns a + b rounded and adds its exact rounding
+// error to lo (the operations of gmp_two_sum per lane; x - y as x + (-1) y,
+// which rounds once like the subtraction).
+__device__ __forceinline__ float2 gmp_two_sum2(float2 a, float2 b, float2& lo) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 s = gmp_add2(a, b);
+  const float2 bb = gmp_fma2(a, m1, s);
+  const float2 e = gmp_add2(gmp_fma2(gmp_fma2(bb, m1, s), m1, a), gmp_fma2(bb, m1, b));
+  lo = gmp_add2(lo, e);
+  return s;
+}
+
 // Two exponentials exp(-B r^2) (B of two sigmas, one pair's r^2), with the
 // operations of gmp_exp_neg below in packed form: bit-identical results.
 // nr2h = -r2hi in both lanes, r2h = r2hi, r2l = r2lo in both lanes.

@@ -413,25 +413,31 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       }
       for (int b0 = 0; b0 < np; b0 += SH::FOLD) {
         const int b1 = min(np, b0 + SH::FOLD);
-        float acc[16];
+        // acc2[2u + h] = components (2h, 2h+1) of sigma u, as packed pairs
+        float2 acc2[8];
 #pragma unroll
-        for (int v = 0; v < 16; ++v) acc[v] = 0.0f;
+        for (int v = 0; v < 8; ++v) acc2[v] = make_float2(0.0f, 0.0f);
 #pragma unroll 4
         for (int pp = b0; pp < b1; ++pp) {
           const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
           const float4 s = *reinterpret_cast<const float4*>(sp + pp * SH::SSTR);
           const float rv[4] = {r.x, r.y, r.z, r.w};
-          const float sv[4] = {s.x, s.y, s.z, s.w};
+          const float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[4 * u + c] = __fmaf_rn(rv[u], sv[c], acc[4 * u + c]);
+          for (int u = 0; u < 4; ++u) {
+            const float2 ru = make_float2(rv[u], rv[u]);
+            acc2[2 * u] = gmp_fma2(ru, s01, acc2[2 * u]);
+            acc2[2 * u + 1] = gmp_fma2(ru, s23, acc2[2 * u + 1]);
+          }
         }
 #pragma unroll
-        for (int v = 0; v < 16; ++v) {
-          const gmp_f2 s2 = gmp_two_sum(hi[q][v], acc[v]);
-          hi[q][v] = s2.hi;
-          lo[q][v] += s2.lo;
+        for (int v = 0; v < 8; ++v) {
+          float2 l2 = make_float2(lo[q][2 * v], lo[q][2 * v + 1]);
+          const float2 sm = gmp_two_sum2(make_float2(hi[q][2 * v], hi[q][2 * v + 1]), acc2[v], l2);
+          hi[q][2 * v] = sm.x;
+          hi[q][2 * v + 1] = sm.y;
+          lo[q][2 * v] = l2.x;
+          lo[q][2 * v + 1] = l2.y;
         }
       }
     }
