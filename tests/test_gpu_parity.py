@@ -377,3 +377,40 @@ def test_repeated_calls_single_pass_neighbors(torch):
         torch.cuda.synchronize()
         assert torch.equal(f1, f0), k
         assert torch.allclose(g1, g0, rtol=1e-6, atol=1e-6 * float(g0.abs().max())), k
+
+
+@pytest.mark.parametrize("orders,n_sig", [([0, 1, 2, 3], 21), ([-1], 1), ([0], 3), ([-1, 5], 2), ([6, 1, -1], 17)])
+def test_vjp_probe_sets(torch, oracle_mod, orders, n_sig):
+    """Probe sets beyond the workloads': more than 16 sigmas (several kernel
+    passes sharing the moment buffer), density only, one order, unordered
+    orders with the density in the middle of the column list."""
+    w = wl("random64_box").replace(orders=orders, sigmas=list(np.geomspace(0.1, 1.4, n_sig)))
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=41)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    assert feature_errors(feat.cpu().numpy(), ref, fabs).max() <= FEAT_TOL
+    atoms = synth.subset_centers(w.n_atoms, 16, seed=2)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    assert grad_errors(gp.cpu().numpy()[atoms], gref, gscale).max() <= GRAD_TOL
+
+
+def test_jacobian_batched_clusters_and_cells(torch, oracle_mod):
+    """Jacobian rows of a batch mixing clusters and periodic cells."""
+    w = wl("batched300")
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    joff, jj, jac = joff.cpu().numpy(), jj.cpu().numpy(), jac.cpu().numpy()
+    centers = synth.subset_centers(w.n_atoms, 64, seed=19)
+    ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+    worst = 0.0
+    for t, i in enumerate(centers):
+        a, b = joff[i], joff[i + 1]
+        assert np.array_equal(jj[a:b], oj[ooff[t]:ooff[t + 1]])
+        worst = max(worst, float(grad_errors(jac[a:b], ojac[ooff[t]:ooff[t + 1]], oabs[ooff[t]:ooff[t + 1]]).max()))
+    record("jacobian/batched300", max_rel_err=worst)
+    assert worst <= GRAD_TOL, worst
