@@ -423,6 +423,21 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
       // outgrew the guessed capacity: count exactly below
     }
   }
+  if (capture && !sorted) {
+    // graph replay: the single pass with the capacities fixed at capture
+    // time; a block beyond them is flagged on the device and the call then
+    // runs eagerly (and recaptures)
+    GMP_CK(h->nbr_rng.ensure(sizeof(int64_t) * 2 * NC), "nbr_rng");
+    GMP_CK(cudaMemsetAsync(d_cursor, 0, 8, st), "memset cursor");
+    GMP_CK(gmp_launch_neighbor_pass(1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
+                                    h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
+                                    h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, nullptr, nullptr,
+                                    h->pairs.as<GmpPair>(), h->cap_pairs, h->cap_keys, d_maxm, d_err, st, h->sm_count,
+                                    L, d_cursor, h->nbr_rng.as<int64_t>()),
+           "neighbor single pass");
+    h->rng_mode = true;
+    return GMP_OK;
+  }
   GMP_CK(gmp_launch_neighbor_pass(0, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
                                   h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
                                   h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, h->counts.as<int64_t>(),
@@ -433,7 +448,7 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
   if (capture) {
     // capacities fixed at capture time; the fill and compute kernels skip
     // (and flag) centers beyond them
-    GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
+    GMP_CK(gmp_launch_neighbor_pass(2, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC,
                                     h->cutoff, pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                                     h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, nullptr,
                                     h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), h->cap_pairs, h->cap_keys,
@@ -593,14 +608,16 @@ gmp_status replay_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStrea
 // into a CUDA graph for later replays; capacities get 12.5% headroom over
 // the eager run that just finished.
 template <typename Seq>
-gmp_status capture_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStream_t st, Seq& seq) {
+gmp_status capture_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStream_t st, Seq& seq, int64_t N) {
   if (!st) return GMP_OK;  // the legacy default stream cannot be captured
   h->cap_pairs = h->P + h->P / 8 + 4096;
   int keys = 32;
   while (keys < h->max_m + h->max_m / 8 + 8) keys <<= 1;
   if ((size_t)keys * 8 > 200 * 1024) return GMP_OK;  // too large for a fixed capacity: stay eager
   h->cap_keys = keys;
+  // every buffer the captured sequence uses exists before the capture
   GMP_CK(h->pairs.ensure(sizeof(GmpPair) * h->cap_pairs), "pairs");
+  GMP_CK(h->nbr_rng.ensure(sizeof(int64_t) * 2 * N), "nbr_rng");
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
@@ -882,7 +899,7 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
     return GMP_OK;
   };
   if ((r = seq(false)) != GMP_OK) return r;
-  if (use_graph && (r = capture_graph(h, key, st, seq)) != GMP_OK) return r;
+  if (use_graph && (r = capture_graph(h, key, st, seq, N)) != GMP_OK) return r;
   if (io.host) {
     GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
     GMP_CK(cudaStreamSynchronize(st), "sync");
@@ -1027,7 +1044,7 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     if (io.host) cudaStreamSynchronize(h->side);  // no copy may outlive the call
     return r;
   }
-  if (use_graph && (r = capture_graph(h, key, st, seq)) != GMP_OK) return r;
+  if (use_graph && (r = capture_graph(h, key, st, seq, N)) != GMP_OK) return r;
   if (io.host) {
     GMP_CK(cudaMemcpyAsync(grad_pos, gp, sizeof(float) * N * 3, cudaMemcpyDeviceToHost, st), "d2h grad");
     if (virial)
