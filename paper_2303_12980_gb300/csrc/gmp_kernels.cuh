@@ -133,7 +133,7 @@ struct KParams {
   int64_t flag_cap;
   int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
-  float flag_tau;             // flag when f < flag_tau * C_l l! (2l-1)!! B^2
+  float flag_tau;             // flag when f < flag_tau * l! (2l-1)!! B^2
 };
 
 // Packed flag entry: center (31 bits) | order (4) | global sigma (12) | column (12)
@@ -142,11 +142,14 @@ __host__ __device__ inline unsigned long long pack_flag(int64_t i, int l, int si
          (unsigned long long)col;
 }
 
-// C_l l! (2l-1)!!: with B = sum_pairs |R_{l,s}| r^l, sum_c w_c (sum_pairs |R S_c|)^2
-// <= C_l l! (2l-1)!! B^2 since sum_c w_c S_c^2 = l! (2l-1)!! r^(2l).
+// l! (2l-1)!!: with B = sum_pairs |R_{l,s}| r^l, the cancellation-free scale
+// F_abs = sum_c w_c (sum_pairs |R S_c|)^2 is the squared weighted norm of a
+// sum over pairs of non-negative vectors, so by the triangle inequality
+// F_abs <= (sum_pairs |R| sqrt(sum_c w_c S_c^2))^2 = l! (2l-1)!! B^2, using
+// sum_c w_c S_c^2 = l! (2l-1)!! r^(2l).
 __host__ __device__ constexpr float flag_scale(int l) {
-  return l == 0 ? 1.0f : l == 1 ? 3.0f : l == 2 ? 36.0f : l == 3 ? 900.0f : l == 4 ? 37800.0f
-       : l == 5 ? 2381400.0f : 209563200.0f;
+  return l == 0 ? 1.0f : l == 1 ? 1.0f : l == 2 ? 6.0f : l == 3 ? 90.0f : l == 4 ? 2520.0f
+       : l == 5 ? 113400.0f : 7484400.0f;
 }
 
 __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int64_t idx, float& dx,
