@@ -232,6 +232,50 @@ def emit_eval(L, dtype="float"):
     return "\n".join(lines)
 
 
+def emit_eval_df(L):
+    """The same recurrences in double-float arithmetic (gmp_f2, FP32 pairs):
+    products of a coordinate and a lower component, integer coefficients
+    applied exactly enough by gmp_df_mul_f, sums by gmp_df_add."""
+    name = f"gmp_mcsh_indep_df_{L}"
+    lines = [f"__device__ __forceinline__ void {name}(gmp_f2 x, gmp_f2 y, gmp_f2 z, gmp_f2 r2, gmp_f2* __restrict__ S) {{"]
+    for l in range(L + 1):
+        for t in indep_components(l):
+            k = flat(t)
+            rec = recurrence_terms(t)
+            if rec[0][1] == "1":
+                lines.append(f"  S[{k}] = gmp_f2{{1.0f, 0.0f}};")
+                continue
+            expr = None
+            for coef, kind, src in rec:
+                v = "r2" if kind == "r2" else kind
+                prod = f"gmp_df_mul({v}, S[{flat(src)}])"
+                term = prod if coef == 1 else f"gmp_df_mul_f({prod}, {fnum(coef)})"
+                expr = term if expr is None else f"gmp_df_add({term}, {expr})"
+            lines.append(f"  S[{k}] = {expr};")
+    lines.append("}")
+    return "\n".join(lines)
+
+
+def emit_feature_df(l):
+    """f = sum_all w mu_all^2 from the 2l+1 independent moments, double-float."""
+    T_ = reconstruction(l)
+
+    def combo_expr(combo):
+        e = None
+        for k, v in sorted(combo.items()):
+            term = f"mu[{k}]" if v == 1 else f"gmp_df_mul_f(mu[{k}], {fnum(v)})"
+            e = term if e is None else f"gmp_df_add({term}, {e})"
+        return e
+
+    lines = [f"__device__ __forceinline__ gmp_f2 gmp_mcsh_invariant_df_{l}(const gmp_f2* __restrict__ mu) {{",
+             "  gmp_f2 f{0.0f, 0.0f};"]
+    for t in all_components(l):
+        lines.append(f"  {{ const gmp_f2 m = {combo_expr(T_[t])}; "
+                     f"f = gmp_df_add(gmp_df_mul_f(gmp_df_mul(m, m), {fnum(weight(*t))}), f); }}")
+    lines += ["  return f;", "}"]
+    return "\n".join(lines)
+
+
 def emit_feature(l, dtype="float"):
     """f = sum_all w mu_all^2 from the 2l+1 independent moments, and the
     adjoint lam_k = g * df/dmu_k (float only)."""
@@ -354,10 +398,10 @@ def generate() -> str:
     for L in range(LMAX + 2):
         out.append(emit_eval(L))
     for L in range(LMAX + 1):
-        out.append(emit_eval(L, "double"))
+        out.append(emit_eval_df(L))
     for l in range(LMAX + 1):
         out.append(emit_feature(l))
-        out.append(emit_feature(l, "double"))
+        out.append(emit_feature_df(l))
     for L in range(LMAX + 1):
         out.append(emit_shift_contract(L))
     for l in range(LMAX + 1):
@@ -382,16 +426,16 @@ def generate() -> str:
     for l in range(LMAX + 1):
         out.append(f"    case {l}: return gmp_mcsh_invariant_{l}(mu);")
     out.append("    default: return 0.0f;\n  }\n}")
-    out.append("__device__ __forceinline__ double gmp_mcsh_invariant_d(int l, const double* mu) {")
+    out.append("__device__ __forceinline__ gmp_f2 gmp_mcsh_invariant_df(int l, const gmp_f2* mu) {")
     out.append("  switch (l) {")
     for l in range(LMAX + 1):
-        out.append(f"    case {l}: return gmp_mcsh_invariant_d_{l}(mu);")
-    out.append("    default: return 0.0;\n  }\n}")
-    out.append("// independent components of orders 0..l in double precision (l <= L of the caller)")
-    out.append("__device__ __forceinline__ void gmp_mcsh_indep_d(int l, double x, double y, double z, double r2, double* S) {")
+        out.append(f"    case {l}: return gmp_mcsh_invariant_df_{l}(mu);")
+    out.append("    default: return gmp_f2{0.0f, 0.0f};\n  }\n}")
+    out.append("// independent components of orders 0..l in double-float arithmetic (l <= L of the caller)")
+    out.append("__device__ __forceinline__ void gmp_mcsh_indep_df(int l, gmp_f2 x, gmp_f2 y, gmp_f2 z, gmp_f2 r2, gmp_f2* S) {")
     out.append("  switch (l) {")
     for l in range(LMAX + 1):
-        out.append(f"    case {l}: gmp_mcsh_indep_d_{l}(x, y, z, r2, S); break;")
+        out.append(f"    case {l}: gmp_mcsh_indep_df_{l}(x, y, z, r2, S); break;")
     out.append("    default: break;\n  }\n}")
     out.append("__device__ __forceinline__ void gmp_mcsh_shift_contract_order(int l, const float* lam, const float* S1, float* V) {")
     out.append("  switch (l) {")

@@ -97,7 +97,7 @@ struct gmp_ctx {
   DevBuf scalars;  // err word, maxm, counter
   DevBuf grad_acc, jac_counts;
   DevBuf mu;     // per-center moments between the forward and backward kernels
-  DevBuf ktab;   // FP64 radial constants [n_el][n_sigmas][kmax][3] for the refinement kernel
+  DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
   DevBuf flagq;  // queued ill-conditioned features
   DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp, stage_virial;
   DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
@@ -530,16 +530,19 @@ gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
 }
 
 // FP64 recomputation of the queued features.
-// Centers are the atoms unless center_pos / center_struct give reference points.
-gmp_status refine(gmp_ctx* h, int64_t N, const double* pos, float* features, cudaStream_t st,
-                  const double* center_pos = nullptr, const int32_t* center_struct = nullptr) {
+// Centers are the atoms unless center_xh / center_xl / center_struct give
+// reference points.
+gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const float4* center_xh = nullptr,
+                  const float4* center_xl = nullptr, const int32_t* center_struct = nullptr) {
   GMP_CK(gmp_launch_refine(h->flagq.as<unsigned long long>(),
                            reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3), flag_capacity(N),
-                           features, h->F, pos, center_pos ? center_pos : pos,
+                           features, h->F, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
+                           center_xh ? center_xh : h->atom_xh.as<float4>(),
+                           center_xl ? center_xl : h->atom_xl.as<float4>(),
                            center_struct ? center_struct : h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
                            h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>(),
                            h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1,
-                           h->pairs.as<GmpPair>(), h->ktab.as<double>(),
+                           h->pairs.as<GmpPair>(), h->ktab.as<float>(),
                            (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->scalars.as<uint32_t>(),
                            h->sm_count, st, &h->launches),
          "refine");
@@ -805,10 +808,15 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     for (auto& pd : h->passes) pd.pass.dens = h->dens.as<float>();
   }
   {
-    // FP64 constants for the refinement kernel: per (element, sigma, primitive)
-    // c N_s (pi/g)^(3/2), alpha/g, alpha beta/g
+    // Double-float constants for the refinement kernel: per (element, sigma,
+    // primitive) the exponent rate b = alpha beta/g and A_l = c N_s (pi/g)^(3/2)
+    // (alpha/g)^l, l = 0..6, each computed in FP64 and split into (hi, lo)
     const int ns = std::max<int>((int)h->sigmas.size(), 1);
-    std::vector<double> kt((size_t)h->n_el * ns * h->kmax * 3, 0.0);
+    std::vector<float> kt((size_t)h->n_el * ns * h->kmax * 16, 0.0f);
+    auto split = [](double v, float* out) {
+      out[0] = (float)v;
+      out[1] = (float)(v - (double)out[0]);
+    };
     int64_t off = 0;
     for (int e = 0; e < h->n_el; ++e) {
       for (int s = 0; s < (int)h->sigmas.size(); ++s) {
@@ -818,16 +826,16 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
         for (int q = 0; q < h->n_gauss[e]; ++q) {
           const double a = h->alpha[off + q], c = h->coef[off + q];
           const double gam = a + beta;
-          double* ent = &kt[(((size_t)e * ns + s) * h->kmax + q) * 3];
-          ent[0] = c * Ns * std::pow(M_PI / gam, 1.5);
-          ent[1] = a / gam;
-          ent[2] = a * beta / gam;
+          float* ent = &kt[(((size_t)e * ns + s) * h->kmax + q) * 16];
+          split(a * beta / gam, ent);
+          const double K0 = c * Ns * std::pow(M_PI / gam, 1.5);
+          for (int l = 0; l <= 6; ++l) split(K0 * std::pow(a / gam, l), ent + 2 + 2 * l);
         }
       }
       off += h->n_gauss[e];
     }
-    if (h->ktab.ensure(kt.size() * sizeof(double)) != cudaSuccess ||
-        cudaMemcpy(h->ktab.p, kt.data(), kt.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (h->ktab.ensure(kt.size() * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(h->ktab.p, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         h->scalars.ensure(64) != cudaSuccess || cudaMemset(h->scalars.p, 0, 64) != cudaSuccess) {
       cudaGetLastError();
       return bad("device allocation for tables failed");
@@ -894,7 +902,7 @@ gmp_status gmp_featurize(gmp_handle h, int32_t n_struct, const int64_t* atom_off
     }
     GMP_CK(prof_mark(h, 1, false, st), "profile");
     GMP_CK(prof_mark(h, 3, true, st), "profile");
-    if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+    if ((q = refine(h, N, feat, st)) != GMP_OK) return q;
     GMP_CK(prof_mark(h, 3, false, st), "profile");
     return GMP_OK;
   };
@@ -1000,7 +1008,7 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
       // every feature is final once the last forward kernel and the FP64
       // refinement ran: its download overlaps the backward kernel
       GMP_CK(prof_mark(h, 3, true, st), "profile");
-      if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+      if ((q = refine(h, N, feat, st)) != GMP_OK) return q;
       GMP_CK(prof_mark(h, 3, false, st), "profile");
       refined = true;
       if (overlap && features) {
@@ -1028,7 +1036,7 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
   }
   if (feat && !refined) {
     GMP_CK(prof_mark(h, 3, true, st), "profile");
-    if ((q = refine(h, N, io.pos, feat, st)) != GMP_OK) return q;
+    if ((q = refine(h, N, feat, st)) != GMP_OK) return q;
     GMP_CK(prof_mark(h, 3, false, st), "profile");
   }
   GMP_CK(gmp_launch_grad_finish(N, h->grad_acc.as<double>(), gp, st, &h->launches), "grad finish");
@@ -1125,7 +1133,7 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
   }
   GMP_CK(prof_mark(h, 1, false, st), "profile");
   GMP_CK(prof_mark(h, 3, true, st), "profile");
-  if (feat && (r = refine(h, N, io.pos, feat, st)) != GMP_OK) return r;
+  if (feat && (r = refine(h, N, feat, st)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 3, false, st), "profile");
   const cudaMemcpyKind k_off = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (N + 1), k_off, st), "copy jac_off");
@@ -1205,7 +1213,7 @@ gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t* a
     }
     GMP_CK(prof_mark(h, 1, false, st), "profile");
     GMP_CK(prof_mark(h, 3, true, st), "profile");
-    if ((r = refine(h, NP, io.pos, feat, st, pts, h->pt_struct.as<int32_t>())) != GMP_OK) return r;
+    if ((r = refine(h, NP, feat, st, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(), h->pt_struct.as<int32_t>())) != GMP_OK) return r;
     GMP_CK(prof_mark(h, 3, false, st), "profile");
   }
   if (host) {

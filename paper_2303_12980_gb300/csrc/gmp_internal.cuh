@@ -131,6 +131,54 @@ __device__ __forceinline__ gmp_f2 gmp_df_mul(gmp_f2 a, gmp_f2 b) {
   float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
   return gmp_fast_two_sum(p.hi, e);
 }
+// Double-float times a float.
+__device__ __forceinline__ gmp_f2 gmp_df_mul_f(gmp_f2 a, float b) {
+  gmp_f2 p = gmp_two_prod(a.hi, b);
+  float e = __fmaf_rn(a.lo, b, p.lo);
+  return gmp_fast_two_sum(p.hi, e);
+}
+// Addition where |a| >= |b| is not required but the result's low word is
+// the plain sum of the rounding errors (one renormalisation): enough for a
+// Horner step whose terms decrease.
+__device__ __forceinline__ gmp_f2 gmp_df_add_sloppy(gmp_f2 a, gmp_f2 b) {
+  gmp_f2 s = gmp_two_sum(a.hi, b.hi);
+  return gmp_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// exp(-x) for a double-float x >= 0 to about 1e-14 relative, in FP32
+// arithmetic only: x = k ln2 + r with |r| <= ln2/2 (ln2 as a double-float,
+// k ln2 formed exactly enough by two products), exp(-r) by Horner's rule on
+// its Taylor series through degree 13 (the first omitted term is below
+// 4e-18), then the exact scaling by 2^-k.  Results below the FP32 normal
+// range (x > 87) are returned as 0.
+__device__ __forceinline__ gmp_f2 gmp_df_exp_neg(gmp_f2 x) {
+  if (!(x.hi <= 87.0f)) return gmp_f2{0.0f, 0.0f};
+  // (-1)^n / n!, n = 0..13, as double-floats (hi, lo)
+  constexpr float C[14][2] = {{1.0f, 0.0f},
+                              {-1.0f, 0.0f},
+                              {0.5f, 0.0f},
+                              {-0.1666666716337204f, 4.967053879312289e-09f},
+                              {0.0416666679084301f, -1.2417634698280722e-09f},
+                              {-0.008333333767950535f, 4.34617203337595e-10f},
+                              {0.0013888889225199819f, -3.3631094437103215e-11f},
+                              {-0.00019841270113829523f, 2.725596874933456e-12f},
+                              {2.4801587642286904e-05f, -3.40699609366682e-13f},
+                              {-2.7557318844628753e-06f, -3.793571224297229e-14f},
+                              {2.755731998149713e-07f, -7.575112209051195e-15f},
+                              {-2.5052107943679403e-08f, -4.4176230446483665e-16f},
+                              {2.0876755879584152e-09f, 1.1082839147459852e-16f},
+                              {-1.6059044372074283e-10f, 5.352526511562726e-18f}};
+  const float LN2_HI = 0.6931471824645996f, LN2_LO = -1.9046542121259336e-09f;
+  const float k = rintf(__fmul_rn(x.hi, 1.4426950408889634f));
+  const gmp_f2 kl = gmp_df_add(gmp_two_prod(k, LN2_HI), gmp_two_prod(k, LN2_LO));
+  const gmp_f2 r = gmp_df_add(x, gmp_df_neg(kl));
+  gmp_f2 p{C[13][0], C[13][1]};
+#pragma unroll
+  for (int n = 12; n >= 0; --n) p = gmp_df_add_sloppy(gmp_df_mul(p, r), gmp_f2{C[n][0], C[n][1]});
+  const int ki = (int)k;
+  return gmp_f2{ldexpf(p.hi, -ki), ldexpf(p.lo, -ki)};
+}
+
 // Integer (|n| < 2^24) times double-float, exact product of the high part.
 __device__ __forceinline__ gmp_f2 gmp_df_mul_int(int n, gmp_f2 a) {
   float fn = (float)n;
@@ -187,6 +235,31 @@ __device__ __forceinline__ float gmp_exp_neg(float Bhi, float Blo, float r2hi, f
   xl = __fmaf_rn(Blo, r2hi, xl);
   float E = gmp_ex2(-xh);
   return __fmaf_rn(E, -0.69314718055994531f * xl, E);
+}
+
+// Double-float displacement of j's image n from i, and its r^2.
+__device__ __forceinline__ void gmp_df_disp(const float4& xhi, const float4& xli, const float4& xhj,
+                                        const float4& xlj, const GmpStruct& st, const int* n,
+                                        gmp_f2* d, gmp_f2& r2, float& mag) {
+  const float xi_h[3] = {xhi.x, xhi.y, xhi.z}, xi_l[3] = {xli.x, xli.y, xli.z};
+  const float xj_h[3] = {xhj.x, xhj.y, xhj.z}, xj_l[3] = {xlj.x, xlj.y, xlj.z};
+  const bool shifted = (n[0] | n[1] | n[2]) != 0;
+  mag = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    gmp_f2 dd = gmp_df_add(gmp_f2{xj_h[c], xj_l[c]}, gmp_f2{-xi_h[c], -xi_l[c]});
+    float m = fabsf(xj_h[c]) + fabsf(xi_h[c]);
+    if (shifted) {
+      gmp_f2 s0 = gmp_df_mul_int(n[0], gmp_f2{st.Ahi[c], st.Alo[c]});
+      gmp_f2 s1 = gmp_df_mul_int(n[1], gmp_f2{st.Ahi[3 + c], st.Alo[3 + c]});
+      gmp_f2 s2 = gmp_df_mul_int(n[2], gmp_f2{st.Ahi[6 + c], st.Alo[6 + c]});
+      gmp_f2 sh = gmp_df_add(gmp_df_add(s0, s1), s2);
+      dd = gmp_df_add(dd, sh);
+      m += fabsf(s0.hi) + fabsf(s1.hi) + fabsf(s2.hi);
+    }
+    d[c] = dd;
+    mag = fmaxf(mag, m);
+  }
+  r2 = gmp_df_add(gmp_df_add(gmp_df_mul(d[0], d[0]), gmp_df_mul(d[1], d[1])), gmp_df_mul(d[2], d[2]));
 }
 
 // ---------------------------------------------------------------- host side
@@ -247,11 +320,11 @@ cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const G
 cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,
                                    cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
-                              float* features, int F, const double* pos, const double* center_pos,
-                              const int32_t* center_struct, const GmpStruct* structs, const int64_t* nbr_beg,
-                              const int64_t* nbr_end, const GmpPair* pairs,
-                              const double* ktab, int nsig_total, int kmax, uint32_t* err, int sm_count,
-                              cudaStream_t stream, int64_t* launches);
+                              float* features, int F, const float4* atom_xh, const float4* atom_xl,
+                              const float4* center_xh, const float4* center_xl, const int32_t* center_struct,
+                              const GmpStruct* structs, const int64_t* nbr_beg, const int64_t* nbr_end,
+                              const GmpPair* pairs, const float* ktab, int nsig_total, int kmax, uint32_t* err,
+                              int sm_count, cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,
                                         int32_t* nbr_shift, cudaStream_t stream,
                                         int64_t* launches);

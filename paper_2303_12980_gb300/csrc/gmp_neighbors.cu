@@ -399,31 +399,6 @@ struct Cand {
   int n[3];
 };
 
-// Double-float displacement of j's image n from i, and its r^2.
-__device__ __forceinline__ void df_disp(const float4& xhi, const float4& xli, const float4& xhj,
-                                        const float4& xlj, const GmpStruct& st, const int* n,
-                                        gmp_f2* d, gmp_f2& r2, float& mag) {
-  const float xi_h[3] = {xhi.x, xhi.y, xhi.z}, xi_l[3] = {xli.x, xli.y, xli.z};
-  const float xj_h[3] = {xhj.x, xhj.y, xhj.z}, xj_l[3] = {xlj.x, xlj.y, xlj.z};
-  const bool shifted = (n[0] | n[1] | n[2]) != 0;
-  mag = 0.0f;
-  for (int c = 0; c < 3; ++c) {
-    gmp_f2 dd = gmp_df_add(gmp_f2{xj_h[c], xj_l[c]}, gmp_f2{-xi_h[c], -xi_l[c]});
-    float m = fabsf(xj_h[c]) + fabsf(xi_h[c]);
-    if (shifted) {
-      gmp_f2 s0 = gmp_df_mul_int(n[0], gmp_f2{st.Ahi[c], st.Alo[c]});
-      gmp_f2 s1 = gmp_df_mul_int(n[1], gmp_f2{st.Ahi[3 + c], st.Alo[3 + c]});
-      gmp_f2 s2 = gmp_df_mul_int(n[2], gmp_f2{st.Ahi[6 + c], st.Alo[6 + c]});
-      gmp_f2 sh = gmp_df_add(gmp_df_add(s0, s1), s2);
-      dd = gmp_df_add(dd, sh);
-      m += fabsf(s0.hi) + fabsf(s1.hi) + fabsf(s2.hi);
-    }
-    d[c] = dd;
-    mag = fmaxf(mag, m);
-  }
-  r2 = gmp_df_add(gmp_df_add(gmp_df_mul(d[0], d[0]), gmp_df_mul(d[1], d[1])), gmp_df_mul(d[2], d[2]));
-}
-
 // The FP64 expression of the neighbor definition, evaluated exactly as written.
 __device__ __noinline__ bool fp64_within(const double* __restrict__ pos, const double* __restrict__ xi,
                                          int64_t j, const GmpStruct& st, const int* n, double rc2) {
@@ -443,7 +418,7 @@ __device__ __forceinline__ bool exact_accept(const double* __restrict__ pos, con
                                              float rc2hi, float rc2lo, double rc2, float cutoff) {
   gmp_f2 d[3], r2;
   float mag;
-  df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
+  gmp_df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
   gmp_f2 diff = gmp_df_add(r2, gmp_f2{-rc2hi, -rc2lo});
   // double-float error bound (generous): 2^-36 (mag + rc + 1) (rc + 1) * 16
   const float tol = ldexpf((mag + cutoff + 1.0f) * (cutoff + 1.0f) * 16.0f, -36);
@@ -692,7 +667,7 @@ __global__ void k_neighbors(const GmpStruct* __restrict__ S, const GmpGrid* __re
     const float4 xhj = atom_xh[j], xlj = atom_xl[j];
     gmp_f2 d[3], r2;
     float mag;
-    df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
+    gmp_df_disp(xhi, xli, xhj, xlj, st, n, d, r2, mag);
     GmpPair p;
     p.dx = d[0].hi + d[0].lo;
     p.dy = d[1].hi + d[1].lo;
