@@ -255,7 +255,7 @@ int64_t gmp_kernel_launches(gmp_handle h);
  *   stage 0: neighbor search (binning, count, fill),
  *   stage 1: the feature kernel (forward, or Jacobian),
  *   stage 2: the backward kernel of gmp_featurize_vjp,
- *   stage 3: FP64 refinement of ill-conditioned features;
+ *   stage 3: double-float refinement of ill-conditioned features;
  * gmp_profile_read synchronises those events and writes, per stage, the
  * summed milliseconds and the number of stage executions since the last
  * read (arrays of length n_stages <= 4), then clears the counters. */

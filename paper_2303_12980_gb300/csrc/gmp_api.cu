@@ -529,7 +529,7 @@ gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
   return GMP_OK;
 }
 
-// FP64 recomputation of the queued features.
+// Double-float recomputation of the queued features.
 // Centers are the atoms unless center_xh / center_xl / center_struct give
 // reference points.
 gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const float4* center_xh = nullptr,

@@ -496,7 +496,7 @@ __device__ __forceinline__ int64_t next_center(int32_t* counter) {
 }
 
 // Features of center i from Mu; features whose value is below the FP32
-// resolution bound are queued for the FP64 refinement kernel.
+// resolution bound are queued for the double-float refinement kernel.
 template <int L, int NS>
 __device__ __forceinline__ void write_features(const KParams& K, int64_t i, const float* Mu, float rho) {
   using SH = Shape<L, NS>;
