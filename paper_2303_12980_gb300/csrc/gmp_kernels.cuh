@@ -17,12 +17,18 @@
 // (a <= 1) are accumulated; the rest follow from tracelessness.
 //
 // Layout: one warp per center (persistent warps take centers from an atomic
-// counter).  A warp walks its center's neighbor list in tiles of 32 pairs:
-//   phase 1, lane = pair: exps and radial factors R[l][s] (double-float
-//            exponent argument), MCSH values S[k] -> shared-memory tile;
-//   phase 2, lane = block of 4 sigmas x 4 components: FP32 FMAs over the
-//            tile, then the tile partial is folded into a (hi, lo) pair by
-//            TwoSum (blocked compensated summation over neighbors).
+// counter).  The forward kernel walks its center's neighbor list in tiles of
+// 16 pairs (two lanes per pair) or 32 (one lane per pair):
+//   phase 1, lane = pair (and half of its sigma groups): exps and radial
+//            factors R[l][s] (double-float exponent argument, four sigmas per
+//            16-byte table load, packed FP32 pairs), MCSH values S[k] ->
+//            shared-memory tiles;
+//   phase 2, lane = block of 4 sigmas x 4 components: packed FP32 FMAs over
+//            the tile, the partial of every 16 pairs folded into a (hi, lo)
+//            pair by TwoSum (blocked compensated summation over neighbors).
+// The backward kernel takes one pair per lane and recomputes its radial
+// factors (one order more: dR_l/dr^2 = -beta R_{l+1}) and MCSH values to
+// apply the adjoints of the center's features.
 #pragma once
 
 #include "gmp_internal.cuh"
