@@ -95,9 +95,9 @@ gmp_status gmp_create(const gmp_params *params, int device, gmp_handle *out);
 gmp_status gmp_num_features(gmp_handle h, int32_t *F);
 
 /* The cutoff in use (Angstrom).  When it was derived from overlap_threshold
- * t (PAPER Examples: the cutoff "will be inferred by the overlap_threshold
- * setting"), it is the largest r at which some single-primitive bound still
- * exceeds t:
+ * t (the paper's Examples section: with no cutoff given, the threshold on
+ * overlaps decides it), it is the largest r at which some single-primitive
+ * bound still exceeds t:
  *   order l >= 0, sigma s, primitive (c, alpha), g = alpha + 1/(2 s^2):
  *     |c| N_s (pi/g)^(3/2) (alpha/g)^l sqrt(l! (2l-1)!!) r^l exp(-(alpha/(2 s^2 g)) r^2)
  *     (the largest overlap of that primitive with any MCSH component of the
@@ -153,8 +153,8 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t *ato
                                   int32_t *jac_j, float *jac, int64_t cap, int64_t *nnz_out,
                                   void *stream);
 
-/* Features at reference points (PAPER Overview: the features can be
- * computed at arbitrary reference points of a structure, not only at its
+/* Features at reference points (the paper's Overview section: features are
+ * defined around arbitrary points of a structure, not only around its
  * atoms).  The probes are centred on each point; the neighbor set is every
  * atom image of the point's structure with |(x_j - p) + n1 a1 + n2 a2 + n3 a3|
  * < cutoff, decided in FP64 exactly as gmp_neighbors does for atoms (a point

@@ -500,8 +500,8 @@ int oracle_features(const oracle_problem *P, int64_t n_centers, const int64_t *c
   return features_impl(P, n_centers, centers, NULL, NULL, feat, fabs_out, mu_out);
 }
 
-/* Features at reference points (PAPER Overview: features "at any set of
- * reference points" of a structure): points [n,3], point_struct [n]. */
+/* Features at reference points (the paper's Overview section: the probes may
+ * be centred on arbitrary points of a structure): points [n,3], point_struct [n]. */
 int oracle_point_features(const oracle_problem *P, int64_t n_points, const double *points,
                           const int32_t *point_struct, double *feat, double *fabs_out) {
   return features_impl(P, n_points, NULL, points, point_struct, feat, fabs_out, NULL);

@@ -35,6 +35,7 @@ def test_full_size_sampled(torch, oracle_mod, name, n_centers, n_atoms):
     F = GMPFeaturizer.from_workload(w)
     pos = torch.from_numpy(w.positions).cuda()
     sp = torch.from_numpy(w.species).cuda()
+    F.tune(pos, sp, w.atom_off, w.cells, w.pbc, reps=1)   # the launch shapes bench.py times
     g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=2024)
     feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
@@ -104,3 +105,43 @@ def test_invalid_inputs_are_reported(torch):
     f = F.featurize(pos, torch.from_numpy(w.species).cuda(), w.atom_off, w.cells, w.pbc)
     torch.cuda.synchronize()
     assert torch.isfinite(f).all()
+
+
+def test_coincident_atoms(torch, oracle_mod):
+    """Distinct atoms at the same position (r = 0 pairs other than the self
+    term, where only order 1 has a gradient) in a cluster and in a cell."""
+    base = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2, 3])
+    p = base.positions[:12].copy()
+    p[5] = p[2]
+    p[9] = p[2]
+    p[11] = p[7]
+    w = base.replace(positions=np.concatenate([p, p + 0.0]), species=np.concatenate([base.species[:12]] * 2),
+                     atom_off=np.array([0, 12, 24], np.int64), cells=np.stack([base.cells[0], np.zeros((3, 3))]),
+                     pbc=np.array([[1, 1, 1], [0, 0, 0]], np.uint8))
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=17)
+    feat, gp = F.featurize_vjp(torch.from_numpy(w.positions).cuda(), torch.from_numpy(w.species).cuda(),
+                               w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    assert feature_errors(feat.cpu().numpy(), ref, fabs).max() <= FEAT_TOL
+    atoms = np.arange(w.n_atoms)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    assert grad_errors(gp.cpu().numpy(), gref, gscale).max() <= GRAD_TOL
+
+
+def test_neighbor_image_limit(torch):
+    """More neighbor images per center than the fill kernels hold (25,600):
+    a capacity error with the count, and the handle stays usable."""
+    from paper_2303_12980_gb300.binding import GMPError, GMPFeaturizer
+    w = synth.workload("random64_box")
+    big = w.replace(cutoff=52.0, orders=[0], sigmas=[0.5])   # ~64 x 590 cells of 10 A: ~37,000 images
+    F = GMPFeaturizer.from_workload(big)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    with pytest.raises(GMPError, match="neighbor images"):
+        F.featurize(pos, sp, w.atom_off, w.cells, w.pbc)
+    ok = GMPFeaturizer.from_workload(w).featurize(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ok).all()
