@@ -8,8 +8,9 @@
 namespace gmpk {
 
 template <int L, int NS, int TILE>
-size_t smem_bytes(const GmpPass& P, int warps) {
-  return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax) + (size_t)warps * Shape<L, NS, TILE>::WARP_FLOATS);
+size_t smem_bytes(const GmpPass& P, int warps, int extra_per_warp) {
+  return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax) +
+                          (size_t)warps * (Shape<L, NS, TILE>::WARP_FLOATS + extra_per_warp));
 }
 
 // shape.tile: 16 or 32 pairs per forward tile; shape.warps: warps per CTA
@@ -23,8 +24,9 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
                         : kind == GMP_KIND_BACKWARD ? k_backward<L, NS, false>
                         : kind == GMP_KIND_BACKWARD_VIRIAL ? k_backward<L, NS, true>
                                                     : k_jacobian<L, NS>;
+  const int extra = kind == GMP_KIND_BACKWARD_VIRIAL ? kVirialFloats : 0;
   auto smem_of = [&](int w) {
-    return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w) : smem_bytes<L, NS, 16>(K.pass, w);
+    return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w, 0) : smem_bytes<L, NS, 16>(K.pass, w, extra);
   };
   cudaFuncAttributes fa;
   cudaError_t ea = cudaFuncGetAttributes(&fa, fn);

@@ -104,6 +104,10 @@ struct Shape {
   static_assert(NS * NINDP <= TILE * SSTR, "adjoints must fit the S tile");
 };
 
+// Per-warp shared floats of the backward kernel's strain-derivative sums
+// ([9][32]: one column per lane).
+constexpr int kVirialFloats = 9 * 32;
+
 // Per-element strides of the shared-memory tables: an odd number of float4s,
 // so lanes reading different elements hit different banks.
 __host__ __device__ inline int rad_elem_stride(int L, int NS, int kmax) {
@@ -255,6 +259,41 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
 #pragma unroll
       for (int u = 0; u < 4; ++u) R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
     }
+  }
+}
+
+// The radial factors of radial4s<..., PRECISE = false> (FP32 exponent
+// argument) on packed FP32 pairs, sigmas (0,1) and (2,3) of the group:
+// bit-identical to the scalar form, half the issue slots.
+template <int L, int NL = L + 2>
+__device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+                                         float (&R)[4][NL]) {
+  constexpr int RB = gmp_rad_block(L);
+  float2 Rp[2][NL];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int l = 0; l < NL; ++l) Rp[h][l] = make_float2(0.0f, 0.0f);
+  const float2 nr2 = make_float2(-r2h, -r2h);
+#pragma unroll 1
+  for (int q = 0; q < kmax; ++q) {
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4 bh = blk[0];
+    const float2 x0 = gmp_mul2(make_float2(bh.x, bh.y), nr2), x1 = gmp_mul2(make_float2(bh.z, bh.w), nr2);
+    const float2 E0 = make_float2(gmp_ex2(x0.x), gmp_ex2(x0.y)), E1 = make_float2(gmp_ex2(x1.x), gmp_ex2(x1.y));
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const float4 a = blk[2 + l];
+      Rp[0][l] = gmp_fma2(make_float2(a.x, a.y), E0, Rp[0][l]);
+      Rp[1][l] = gmp_fma2(make_float2(a.z, a.w), E1, Rp[1][l]);
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    R[0][l] = Rp[0][l].x;
+    R[1][l] = Rp[0][l].y;
+    R[2][l] = Rp[1][l].x;
+    R[3][l] = Rp[1][l].y;
   }
 }
 
@@ -618,18 +657,23 @@ __device__ __forceinline__ void pair_gradient(const float* lam, const float* lam
 // Backward only: moments come from the forward kernel (K.mu_out, read), the
 // per-pair terms are recomputed.  Lane = pair.  With VIRIAL, also the
 // strain derivative of the structure: sum over pairs of (dL/dd)_a d_b
-// (positions and lattice vectors strained alike move every d to (I+eps) d).
-template <int L, int NS, bool VIRIAL = false>
+// (positions and lattice vectors strained alike move every d to (I+eps) d),
+// each lane's partial sums kept in its column of Wv ([9][32] floats of
+// warp-private shared memory) rather than in registers.
+// PACKED: radial factors on packed FP32 pairs (same results; needs more
+// than the 168 registers of the 12-warp backward launch).
+template <int L, int NS, bool VIRIAL = false, bool PACKED = false>
 __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
-                                               const float* __restrict__ Lam, float gd) {
+                                               const float* __restrict__ Lam, float gd, float* Wv = nullptr) {
   using SH = Shape<L, NS>;
   const GmpPass& P = K.pass;
   const int lane = threadIdx.x & 31;
   float own[3] = {0.0f, 0.0f, 0.0f};
-  float wv[VIRIAL ? 9 : 1];
+  if constexpr (VIRIAL) {
 #pragma unroll
-  for (int v = 0; v < (VIRIAL ? 9 : 1); ++v) wv[v] = 0.0f;
+    for (int v = 0; v < 9; ++v) Wv[32 * v + lane] = 0.0f;
+  }
   for (int pp = lane; pp < M; pp += 32) {
     float dx, dy, dz, r2h, r2l;
     int e, j;
@@ -641,7 +685,10 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
-      radial4s<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
+      if constexpr (PACKED)
+        radial4p<L, L + 2>(tab_e, P.kmax, sg, r2h, R);
+      else
+        radial4s<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
@@ -685,14 +732,14 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) wv[3 * a + b] = __fmaf_rn(g[a], d[b], wv[3 * a + b]);
+        for (int b = 0; b < 3; ++b) Wv[32 * (3 * a + b) + lane] = __fmaf_rn(g[a], d[b], Wv[32 * (3 * a + b) + lane]);
     }
   }
   if constexpr (VIRIAL) {
     double* wrow = K.virial + 9 * (int64_t)K.center_struct[i];
 #pragma unroll
     for (int v = 0; v < 9; ++v) {
-      double o = (double)wv[v];
+      double o = (double)Wv[32 * v + lane];
 #pragma unroll
       for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
       if (lane == 0) atomicAdd(wrow + v, o);
@@ -735,13 +782,13 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
     if (K.features) write_features<L, NS>(K, i, Mu, rho);
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS>(K, s_rad, s_dens, i, p0, M, Lam, gd);
+    backward_sweep<L, NS, false, true>(K, s_rad, s_dens, i, p0, M, Lam, gd);
     __syncwarp();
   }
 }
 
 template <int L, int NS, bool VIRIAL = false>
-__global__ void __launch_bounds__(VIRIAL ? 256 : 384) k_backward(KParams K) {
+__global__ void __launch_bounds__(384) k_backward(KParams K) {
   using SH = Shape<L, NS>;
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
@@ -751,8 +798,9 @@ __global__ void __launch_bounds__(VIRIAL ? 256 : 384) k_backward(KParams K) {
   load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* Mu = s_warp + (size_t)wib * (SH::WARP_FLOATS + (VIRIAL ? kVirialFloats : 0));
   float* Lam = Mu + SH::TILE * SH::RSTR;
+  float* Wv = Mu + SH::WARP_FLOATS;
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
     if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
@@ -763,7 +811,7 @@ __global__ void __launch_bounds__(VIRIAL ? 256 : 384) k_backward(KParams K) {
     const float* grow = K.grad_feat + i * P.F;
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS, VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd);
+    backward_sweep<L, NS, VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
     __syncwarp();
   }
 }
