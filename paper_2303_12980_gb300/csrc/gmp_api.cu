@@ -1193,7 +1193,7 @@ gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t* a
     GMP_CK(prof_mark(h, 0, true, st), "profile");
     if ((r = bin_atoms(h, n_struct, io.pos, io.species, N, NP, st)) != GMP_OK) return r;
     GMP_CK(gmp_launch_point_prepare(h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), h->pt_struct.as<int32_t>(), NP,
-                                    pts, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(), h->pt_rng.as<int4>(),
+                                    pts, io.pos, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(), h->pt_rng.as<int4>(),
                                     h->pt_y.as<float4>(), h->scalars.as<uint32_t>(), st, h->sm_count, &h->launches),
            "point prepare");
     const GmpCenters C{h->pt_struct.as<int32_t>(), pts, h->pt_xh.as<float4>(), h->pt_xl.as<float4>(),

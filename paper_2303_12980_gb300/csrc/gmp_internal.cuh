@@ -295,11 +295,13 @@ struct GmpCenters {
   const float4* y;
 };
 // Per reference point: the GmpCenters fields above from its FP64 position
-// and structure (after the atom grid of each structure is built).
+// and structure (after the atom grid of each structure is built); atom_pos
+// gives each structure's reference cell (that of its first atom).
 cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const int32_t* point_struct, int64_t n_points, const double* points,
-                                     float4* pt_xh, float4* pt_xl, int4* pt_rng, float4* pt_y,
-                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches);
+                                     const double* atom_pos, float4* pt_xh, float4* pt_xl, int4* pt_rng,
+                                     float4* pt_y, uint32_t* d_err, cudaStream_t stream, int sm_count,
+                                     int64_t* launches);
 // fill: 0 = count only, 1 = records grouped by species (deterministic),
 // 2 = records sorted by (neighbor atom, image).  Centers C [N]; neighbors
 // are the binned atoms (pos, atom_xh, atom_xl).  Records go to the CSR

@@ -55,6 +55,43 @@ __device__ __forceinline__ void sort_key_image(unsigned long long key, int* n) {
 }
 
 // Per atom: checks, fractional coordinates, wrap, double-float split, bbox.
+// Reference cell of a structure: the cell index of its first atom along
+// each periodic axis (0 when it has no atoms or that position is not
+// finite).  Atoms and reference points store their cell index relative to
+// it, so a structure placed any number of cells away from its cell keeps
+// small stored indices; pair image indices, which are differences of the
+// stored indices, do not change.
+__device__ inline void struct_ref_cell(const GmpStruct& st, const double* __restrict__ atom_pos, double (&f0)[3]) {
+  f0[0] = f0[1] = f0[2] = 0.0;
+  if (st.n_atoms <= 0) return;
+  const double* x = atom_pos + 3 * st.atom_base;
+  const double x0 = x[0], x1 = x[1], x2 = x[2];
+  if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) return;
+  for (int k = 0; k < 3; ++k) {
+    if (!st.periodic[k]) continue;
+    const double f = floor(x0 * st.Ainv[k] + x1 * st.Ainv[3 + k] + x2 * st.Ainv[6 + k]);
+    if (fabs(f) < 1e9) f0[k] = f;
+  }
+}
+
+// Wraps the fractional coordinate u of a periodic axis into [0, 1) and
+// returns the cell index relative to the reference cell f0 (error flag and
+// 0 when it does not fit the packed image index).
+__device__ inline int wrap_axis(double& u, double f0, uint32_t* err) {
+  const double fl = floor(u);
+  const double f = fl - f0;
+  int w = 0;
+  if (fabs(f) > 500.0) {  // image index would not fit the packed shift
+    atomicOr(err, GMP_DEV_SHIFT_RANGE);
+  } else {
+    w = (int)f;
+  }
+  u -= fl;
+  if (u >= 1.0) { u -= 1.0; w += 1; }
+  if (u < 0.0) u = 0.0;
+  return w;
+}
+
 __global__ void k_prepare(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
                           int64_t N, const double* __restrict__ pos,
                           const int32_t* __restrict__ species, int n_el,
@@ -75,20 +112,13 @@ __global__ void k_prepare(const GmpStruct* __restrict__ S, const int32_t* __rest
       atomicOr(err, GMP_DEV_NONFINITE);
       x[0] = x[1] = x[2] = 0.0;
     }
-    double u[3];
+    double u[3], f0[3];
     int w[3] = {0, 0, 0};
+    struct_ref_cell(st, pos, f0);
     for (int k = 0; k < 3; ++k) {
       u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
       if (st.periodic[k]) {
-        double f = floor(u[k]);
-        if (fabs(f) > 500.0) {  // image index would not fit the packed shift
-          atomicOr(err, GMP_DEV_SHIFT_RANGE);
-          f = 0.0;
-        }
-        w[k] = (int)f;
-        u[k] -= f;
-        if (u[k] >= 1.0) { u[k] -= 1.0; w[k] += 1; }
-        if (u[k] < 0.0) u[k] = 0.0;
+        w[k] = wrap_axis(u[k], f0[k], err);
       } else {
         // both slots start at all-ones; the max slot stores the complemented key
         atomicMin(&bbox[6 * s + 2 * k], order_key(u[k]));
@@ -281,8 +311,9 @@ __global__ void k_ranges(const GmpStruct* __restrict__ S, const GmpGrid* __restr
 // k_prepare and the bin range of k_ranges, in the structure's atom grid.
 __global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
                                 const int32_t* __restrict__ point_struct, int64_t n, const double* __restrict__ pts,
-                                float4* __restrict__ pt_xh, float4* __restrict__ pt_xl, int4* __restrict__ pt_rng,
-                                float4* __restrict__ pt_y, uint32_t* __restrict__ err) {
+                                const double* __restrict__ atom_pos, float4* __restrict__ pt_xh,
+                                float4* __restrict__ pt_xl, int4* __restrict__ pt_rng, float4* __restrict__ pt_y,
+                                uint32_t* __restrict__ err) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
     const int s = point_struct[a];
@@ -292,21 +323,12 @@ __global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* 
       atomicOr(err, GMP_DEV_NONFINITE);
       x[0] = x[1] = x[2] = 0.0;
     }
-    double u[3];
+    double u[3], f0[3];
     int w[3] = {0, 0, 0};
+    struct_ref_cell(st, atom_pos, f0);  // the reference cell of the structure's atoms
     for (int k = 0; k < 3; ++k) {
       u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
-      if (st.periodic[k]) {
-        double f = floor(u[k]);
-        if (fabs(f) > 500.0) {
-          atomicOr(err, GMP_DEV_SHIFT_RANGE);
-          f = 0.0;
-        }
-        w[k] = (int)f;
-        u[k] -= f;
-        if (u[k] >= 1.0) { u[k] -= 1.0; w[k] += 1; }
-        if (u[k] < 0.0) u[k] = 0.0;
-      }
+      if (st.periodic[k]) w[k] = wrap_axis(u[k], f0[k], err);
     }
     float h[3], l[3];
     for (int k = 0; k < 3; ++k) {
@@ -771,11 +793,12 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
 
 cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* d_grid,
                                      const int32_t* point_struct, int64_t n_points, const double* points,
-                                     float4* pt_xh, float4* pt_xl, int4* pt_rng, float4* pt_y,
-                                     uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches) {
+                                     const double* atom_pos, float4* pt_xh, float4* pt_xl, int4* pt_rng,
+                                     float4* pt_y, uint32_t* d_err, cudaStream_t stream, int sm_count,
+                                     int64_t* launches) {
   if (n_points <= 0) return cudaSuccess;
-  k_point_prepare<<<grid_for(n_points, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, point_struct, n_points,
-                                                                         points, pt_xh, pt_xl, pt_rng, pt_y, d_err);
+  k_point_prepare<<<grid_for(n_points, 256, sm_count), 256, 0, stream>>>(
+      d_structs, d_grid, point_struct, n_points, points, atom_pos, pt_xh, pt_xl, pt_rng, pt_y, d_err);
   ++*launches;
   return cudaGetLastError();
 }

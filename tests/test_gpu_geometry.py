@@ -1,0 +1,137 @@
+"""Geometry stress cases on the GPU against the FP64 oracle: images lying on
+the cutoff sphere to the last bit (and within 1e-11 A of it), coordinates
+far from the origin, and small or strongly skewed cells whose cutoff spans
+several cell widths.  Neighbor sets bit-exact, features and position
+gradients within the parity tolerances."""
+import numpy as np
+import pytest
+
+from paper_2303_12980_gb300 import synth
+
+from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2303_12980_gb300 import build
+    build.build()
+    return t
+
+
+def _batch(base, parts, **kw):
+    """One workload from (positions, species, cell, pbc) structures."""
+    pos = np.concatenate([p for p, _, _, _ in parts])
+    sp = np.concatenate([s for _, s, _, _ in parts]).astype(np.int32)
+    off = np.cumsum([0] + [len(p) for p, _, _, _ in parts]).astype(np.int64)
+    cells = np.stack([c for _, _, c, _ in parts]).astype(np.float64)
+    pbc = np.array([b for _, _, _, b in parts], np.uint8)
+    return base.replace(positions=pos, species=sp, atom_off=off, cells=cells, pbc=pbc, **kw)
+
+
+def _check(torch, oracle_mod, w, grad_atoms=None):
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    noff, nj, nsh = F.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+    ooff, oj, osh, _ = oracle_mod.neighbors(w)
+    assert np.array_equal(noff.cpu().numpy(), ooff)
+    assert np.array_equal(nj.cpu().numpy(), oj)
+    assert np.array_equal(nsh.cpu().numpy(), osh)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=77)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    ferr = feature_errors(feat.cpu().numpy(), ref, fabs)
+    assert ferr.max() <= FEAT_TOL, ferr.max()
+    atoms = np.arange(w.n_atoms) if grad_atoms is None else np.asarray(grad_atoms)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    assert gerr.max() <= GRAD_TOL, gerr.max()
+    return ooff
+
+
+def _cubic_lattice(a, n):
+    g = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    return a * g.astype(np.float64)
+
+
+@pytest.mark.parametrize("rc", [4.0, 32.0 ** 0.5, 6.0])
+def test_cutoff_on_lattice_distances(torch, oracle_mod, rc):
+    """Simple cubic lattice, a = 2 A: with rc = 4, sqrt(32) or 6 A whole
+    shells of images sit on the cutoff sphere (|d| = rc in exact
+    arithmetic); the FP64 expression decides each one, periodic and cluster."""
+    base = synth.workload("random64_box")
+    x = _cubic_lattice(2.0, 4)
+    sp = np.arange(len(x)) % 2
+    cell = np.eye(3) * 8.0
+    w = _batch(base, [(x, sp, cell, (1, 1, 1)), (x + 0.5, sp, np.zeros((3, 3)), (0, 0, 0))],
+               cutoff=rc, orders=[0, 1, 2], sigmas=[0.2, 0.5])
+    ooff = _check(torch, oracle_mod, w, grad_atoms=[0, 5, 21, 64, 100])
+    assert np.diff(ooff).min() > 0
+
+
+def test_cutoff_within_1e11_of_lattice_distances(torch, oracle_mod):
+    """The same lattice with every coordinate moved by up to 1e-11 A, so
+    that the images of the 4 A shell straddle rc = 4 on both sides."""
+    base = synth.workload("random64_box")
+    rng = np.random.default_rng(11)
+    x = _cubic_lattice(2.0, 4)
+    x = x + rng.uniform(-1e-11, 1e-11, x.shape)
+    sp = np.arange(len(x)) % 2
+    w = _batch(base, [(x, sp, np.eye(3) * 8.0, (1, 1, 1)), (x, sp, np.zeros((3, 3)), (0, 0, 0))],
+               cutoff=4.0, orders=[0, 1, 2], sigmas=[0.2, 0.5])
+    _check(torch, oracle_mod, w, grad_atoms=[0, 9, 64, 99])
+
+
+def test_far_from_origin(torch, oracle_mod):
+    """A cluster translated by ~3e4 A and a periodic box whose atoms sit
+    700 lattice vectors away from the cell: the double-float positions keep
+    the displacements, the FP64 expression keeps the neighbor sets."""
+    base = synth.workload("random64_box")
+    x = base.positions[:40]
+    sp = base.species[:40]
+    cell = base.cells[0]
+    shift = np.array([12345.678, -23456.789, 34567.891])
+    far = x + 700.0 * (cell[0] + cell[1] - cell[2]) + 0.25
+    w = _batch(base, [(x + shift, sp, np.zeros((3, 3)), (0, 0, 0)), (far, sp, cell, (1, 1, 1))],
+               orders=[-1, 0, 1, 2, 3])
+    _check(torch, oracle_mod, w, grad_atoms=[0, 7, 40, 63])
+
+
+def test_small_and_skewed_cells(torch, oracle_mod):
+    """Two atoms in a 2.5 A cube (cutoff 6: 2.4 cell widths), and a strongly
+    skewed triclinic cell with mixed periodicity (reach ~10 cell widths
+    along the short reciprocal direction)."""
+    base = synth.workload("random64_box")
+    cube = np.eye(3) * 2.5
+    skew = np.array([[3.0, 0.0, 0.0], [2.95, 0.6, 0.0], [0.3, 0.2, 2.8]])
+    p_cube = np.array([[0.1, 0.2, 0.3], [1.4, 1.1, 1.6]])
+    p_skew = np.array([[0.0, 0.0, 0.0], [1.7, 0.35, 1.2], [3.9, 0.4, 0.7]])
+    w = _batch(base, [(p_cube, np.array([0, 1]), cube, (1, 1, 1)),
+                      (p_skew, np.array([1, 0, 1]), skew, (1, 1, 0))],
+               orders=[-1, 0, 1, 2], sigmas=[0.1, 0.6])
+    ooff = _check(torch, oracle_mod, w)
+    assert np.diff(ooff).max() > 150   # many images of few atoms
+
+
+def test_image_index_limit_reported(torch):
+    """Atoms of one periodic structure more than 500 cells apart (an
+    unwrapped trajectory that drifted): the packed image index cannot hold
+    their pair shifts, so the call fails with a device error naming it, and
+    the handle stays usable."""
+    from paper_2303_12980_gb300.binding import GMPError, GMPFeaturizer
+    w = synth.workload("random64_box")
+    pos = w.positions.copy()
+    pos[1] += 600.0 * w.cells[0][0]
+    F = GMPFeaturizer.from_workload(w)
+    sp = torch.from_numpy(w.species).cuda()
+    with pytest.raises(GMPError, match="image index"):
+        F.featurize(torch.from_numpy(pos).cuda(), sp, w.atom_off, w.cells, w.pbc)
+    f = F.featurize(torch.from_numpy(w.positions).cuda(), sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(f).all()
