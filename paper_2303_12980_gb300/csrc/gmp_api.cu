@@ -98,7 +98,10 @@ struct gmp_ctx {
   DevBuf grad_acc, jac_counts;
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
-  DevBuf flagq;  // queued ill-conditioned features
+  DevBuf flagq;     // queued ill-conditioned features (center << 16 | column)
+  DevBuf flagbits;  // the rest when the queue is full: [N][flag_words] bitmask
+  DevBuf colinfo;   // per feature column: (order << 16) | sigma, -1 for the density
+  int flag_words = 1;
   DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp, stage_virial;
   DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
   int64_t P = 0;  // pairs of the last neighbor build
@@ -499,10 +502,15 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
 }
 
 // Features below this fraction of their FP32 resolution bound are recomputed
-// in FP64 (see gmp_refine.cu and the flag test in write_features).
+// in double-float arithmetic (see gmp_refine.cu and the flag test in
+// write_features).
 constexpr float kFlagTau = 1e-4f;
 
 int64_t flag_capacity(int64_t N) { return 4 * N + 1024; }
+// 64-bit count of flagged features (bytes 24..31 of the scalar block)
+unsigned long long* flag_counter(gmp_ctx* h) {
+  return reinterpret_cast<unsigned long long*>(h->scalars.as<char>() + 24);
+}
 
 gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_t N) {
   gmpk::KParams K;
@@ -514,18 +522,23 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   K.pairs = h->pairs.as<GmpPair>();
   K.counter = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 2);
   K.flags = h->flagq.as<unsigned long long>();
-  K.flag_count = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3);
+  K.flag_count = flag_counter(h);
   K.flag_cap = flag_capacity(N);
+  K.flag_bits = h->flagbits.as<uint32_t>();
+  K.flag_words = h->flag_words;
   K.pair_cap = h->capturing ? h->cap_pairs : h->P;
   K.sig0 = 16 * pass_index;
   K.flag_tau = kFlagTau;
   return K;
 }
 
-// Prepares the flag queue before the compute kernels of one call.
+// Resets the flag queue and bitmask before the compute kernels of one call.
 gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
+  const size_t bytes = sizeof(uint32_t) * (size_t)h->flag_words * (size_t)std::max<int64_t>(N, 1);
   GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * flag_capacity(N)), "flags");
-  GMP_CK(cudaMemsetAsync(h->scalars.as<uint32_t>() + 3, 0, sizeof(int32_t), st), "flag reset");
+  GMP_CK(h->flagbits.ensure(bytes), "flag bits");
+  GMP_CK(cudaMemsetAsync(flag_counter(h), 0, sizeof(unsigned long long), st), "flag reset");
+  GMP_CK(cudaMemsetAsync(h->flagbits.p, 0, bytes, st), "flag bits reset");
   return GMP_OK;
 }
 
@@ -535,7 +548,8 @@ gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
 gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const float4* center_xh = nullptr,
                   const float4* center_xl = nullptr, const int32_t* center_struct = nullptr) {
   GMP_CK(gmp_launch_refine(h->flagq.as<unsigned long long>(),
-                           reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 3), flag_capacity(N),
+                           flag_counter(h), flag_capacity(N),
+                           h->flagbits.as<uint32_t>(), N, h->flag_words, h->colinfo.as<int32_t>(),
                            features, h->F, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                            center_xh ? center_xh : h->atom_xh.as<float4>(),
                            center_xl ? center_xl : h->atom_xl.as<float4>(),
@@ -543,8 +557,8 @@ gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const
                            h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>(),
                            h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1,
                            h->pairs.as<GmpPair>(), h->ktab.as<float>(),
-                           (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->scalars.as<uint32_t>(),
-                           h->sm_count, st, &h->launches),
+                           (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->sm_count, st,
+                           &h->launches),
          "refine");
   return GMP_OK;
 }
@@ -834,8 +848,16 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       }
       off += h->n_gauss[e];
     }
+    // feature column -> (order << 16) | sigma for the refinement kernel
+    std::vector<int32_t> ci((size_t)std::max(h->F, 1), -1);
+    for (size_t o = 0; o < h->orders.size(); ++o)
+      if (h->orders[o] >= 0)
+        for (int s = 0; s < (int)h->sigmas.size(); ++s) ci[col[o] + s] = (h->orders[o] << 16) | s;
+    h->flag_words = (std::max(h->F, 1) + 31) / 32;
     if (h->ktab.ensure(kt.size() * sizeof(float)) != cudaSuccess ||
         cudaMemcpy(h->ktab.p, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        h->colinfo.ensure(ci.size() * sizeof(int32_t)) != cudaSuccess ||
+        cudaMemcpy(h->colinfo.p, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         h->scalars.ensure(64) != cudaSuccess || cudaMemset(h->scalars.p, 0, 64) != cudaSuccess) {
       cudaGetLastError();
       return bad("device allocation for tables failed");

@@ -24,7 +24,7 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
                         : kind == GMP_KIND_BACKWARD ? k_backward<L, NS, false>
                         : kind == GMP_KIND_BACKWARD_VIRIAL ? k_backward<L, NS, true>
                                                     : k_jacobian<L, NS>;
-  const int extra = kind == GMP_KIND_BACKWARD_VIRIAL ? kVirialFloats : 0;
+  const int extra = kind == GMP_KIND_BACKWARD_VIRIAL ? virial_extra_floats<L, NS>() : 0;
   auto smem_of = [&](int w) {
     return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w, 0) : smem_bytes<L, NS, 16>(K.pass, w, extra);
   };

@@ -105,8 +105,14 @@ struct Shape {
 };
 
 // Per-warp shared floats of the backward kernel's strain-derivative sums
-// ([9][32]: one column per lane).
+// ([9][32]: one column per lane).  They reuse the moment block of the
+// warp's region (dead once the adjoints are formed) when it is large
+// enough, else they take extra space after the region.
 constexpr int kVirialFloats = 9 * 32;
+template <int L, int NS>
+constexpr int virial_extra_floats() {
+  return Shape<L, NS>::TILE * Shape<L, NS>::RSTR >= kVirialFloats ? 0 : kVirialFloats;
+}
 
 // Per-element strides of the shared-memory tables: an odd number of float4s,
 // so lanes reading different elements hit different banks.
@@ -137,20 +143,18 @@ struct KParams {
   int32_t* counter;
   const int32_t* center_struct;  // [N] structure of each center (virial)
   double* virial;                // [S, 3, 3] strain derivative accumulators (virial)
-  // features too ill-conditioned for FP32 (recomputed in FP64 afterwards)
-  unsigned long long* flags;  // packed (center, order, sigma, column)
-  int32_t* flag_count;
+  // features too ill-conditioned for FP32 (recomputed in double-float
+  // afterwards): queued as (center << 16 | column) while the queue has room,
+  // then as bit (col % 32) of word flag_bits[i * flag_words + col / 32]
+  unsigned long long* flags;
+  unsigned long long* flag_count;
   int64_t flag_cap;
+  uint32_t* flag_bits;
+  int flag_words;
   int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
   float flag_tau;             // flag when f < flag_tau * l! (2l-1)!! B^2
 };
-
-// Packed flag entry: center (31 bits) | order (4) | global sigma (12) | column (12)
-__host__ __device__ inline unsigned long long pack_flag(int64_t i, int l, int sig, int col) {
-  return ((unsigned long long)i << 28) | ((unsigned long long)l << 24) | ((unsigned long long)sig << 12) |
-         (unsigned long long)col;
-}
 
 // l! (2l-1)!!: with B = sum_pairs |R_{l,s}| r^l, the cancellation-free scale
 // F_abs = sum_c w_c (sum_pairs |R S_c|)^2 is the squared weighted norm of a
@@ -556,8 +560,12 @@ __device__ __forceinline__ void write_features(const KParams& K, int64_t i, cons
     frow[P.ord_col[o] + s] = f;
     const float B = Mu[NS * SH::NIND + s * (L + 1) + l];
     if (K.flags && f < __fmul_rn(__fmul_rn(K.flag_tau, flag_scale(l)), __fmul_rn(B, B))) {
-      const int slot = atomicAdd(K.flag_count, 1);
-      if (slot < K.flag_cap) K.flags[slot] = pack_flag(i, l, K.sig0 + s, P.ord_col[o] + s);
+      const int col = P.ord_col[o] + s;
+      const unsigned long long slot = atomicAdd(K.flag_count, 1ull);
+      if (slot < (unsigned long long)K.flag_cap)
+        K.flags[slot] = ((unsigned long long)i << 16) | (unsigned long long)col;
+      else
+        atomicOr(K.flag_bits + i * K.flag_words + (col >> 5), 1u << (col & 31));
     }
   }
   if (P.want_density && lane == 0) frow[P.dens_col] = rho;
@@ -798,9 +806,10 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
   load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* Mu = s_warp + (size_t)wib * (SH::WARP_FLOATS + (VIRIAL ? kVirialFloats : 0));
+  constexpr int EXTRA = VIRIAL ? virial_extra_floats<L, NS>() : 0;
+  float* Mu = s_warp + (size_t)wib * (SH::WARP_FLOATS + EXTRA);
   float* Lam = Mu + SH::TILE * SH::RSTR;
-  float* Wv = Mu + SH::WARP_FLOATS;
+  float* Wv = EXTRA ? Mu + SH::WARP_FLOATS : Mu;  // Mu is dead once Lam is formed
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
     if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass

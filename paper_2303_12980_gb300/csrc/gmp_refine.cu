@@ -13,6 +13,7 @@
 #include "gmp_internal.cuh"
 #include "mcsh_gen.cuh"
 
+
 namespace {
 
 // Moments of order L (2L+1 independent components) of one center and one
@@ -23,7 +24,7 @@ __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, cons
                                                const GmpPair* __restrict__ pairs,
                                                const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
                                                const float* __restrict__ ktab, int nsig_total, int sig, int kmax,
-                                               gmp_f2 (&mu)[13]) {
+                                               gmp_f2 (&mu)[2 * L + 1]) {
   for (int64_t p = p0 + lane; p < p1; p += 32) {
     const GmpPair pr = pairs[p];
     int nn[3];
@@ -46,65 +47,117 @@ __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, cons
   }
 }
 
-__global__ void k_refine(const unsigned long long* __restrict__ flags, const int32_t* __restrict__ count,
-                         int64_t cap, float* __restrict__ features, int F, const float4* __restrict__ atom_xh,
-                         const float4* __restrict__ atom_xl, const float4* __restrict__ cxh,
-                         const float4* __restrict__ cxl, const int32_t* __restrict__ cstruct,
-                         const GmpStruct* __restrict__ S, const int64_t* __restrict__ nbr_beg,
-                         const int64_t* __restrict__ nbr_end, const GmpPair* __restrict__ pairs,
-                         const float* __restrict__ ktab, int nsig_total, int kmax, uint32_t* __restrict__ err) {
+// One flagged feature f_{L,sigma} of one center: moments over the center's
+// pairs (lane-strided), warp-reduced, and the invariant, all double-float;
+// the result (rounded to FP32) is valid in every lane.
+template <int L>
+__device__ __forceinline__ float refine_feature(int lane, const float4& xhi, const float4& xli, const GmpStruct& st,
+                                                int64_t p0, int64_t p1, const GmpPair* __restrict__ pairs,
+                                                const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
+                                                const float* __restrict__ ktab, int nsig_total, int sig, int kmax) {
+  gmp_f2 mu[2 * L + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * L; ++k) mu[k] = gmp_f2{0.0f, 0.0f};
+  refine_moments<L>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu);
+#pragma unroll
+  for (int k = 0; k <= 2 * L; ++k)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const gmp_f2 other{__shfl_xor_sync(0xffffffffu, mu[k].hi, o), __shfl_xor_sync(0xffffffffu, mu[k].lo, o)};
+      mu[k] = gmp_df_add(mu[k], other);
+    }
+  const gmp_f2 f = gmp_mcsh_invariant_df(L, mu);
+  return f.hi + f.lo;
+}
+
+// One flagged feature (center i, column col) recomputed by the whole warp;
+// col_info[col] = (order << 16) | global sigma.
+__device__ __forceinline__ void refine_entry(int lane, int64_t i, int col, const int32_t* __restrict__ col_info,
+                                             float* __restrict__ features, int F,
+                                             const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
+                                             const float4* __restrict__ cxh, const float4* __restrict__ cxl,
+                                             const int32_t* __restrict__ cstruct, const GmpStruct* __restrict__ S,
+                                             const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
+                                             const GmpPair* __restrict__ pairs, const float* __restrict__ ktab,
+                                             int nsig_total, int kmax) {
+  const int info = col < F ? col_info[col] : -1;
+  if (info < 0) return;
+  const int l = info >> 16, sig = info & 0xffff;
+  const GmpStruct& st = S[cstruct[i]];
+  const float4 xhi = cxh[i], xli = cxl[i];
+  const int64_t p0 = nbr_beg[i], p1 = nbr_end[i];
+  float f = 0.0f;
+  switch (l) {
+    case 0: f = refine_feature<0>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 1: f = refine_feature<1>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 2: f = refine_feature<2>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 3: f = refine_feature<3>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 4: f = refine_feature<4>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 5: f = refine_feature<5>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 6: f = refine_feature<6>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    default: return;
+  }
+  if (lane == 0) features[i * F + col] = f;
+}
+
+// Flagged features: first the queue (entries center << 16 | column, spread
+// over the warps one entry each); when it overflowed, the rest are the set
+// bits of the bitmask (bit col % 32 of word i * FW + col / 32), which each
+// warp reads 32 words at a time (lane = word).
+__global__ void k_refine(const unsigned long long* __restrict__ queue, const unsigned long long* __restrict__ count,
+                         int64_t cap, const uint32_t* __restrict__ bits, int64_t n_words, int FW,
+                         const int32_t* __restrict__ col_info, float* __restrict__ features, int F,
+                         const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
+                         const float4* __restrict__ cxh, const float4* __restrict__ cxl,
+                         const int32_t* __restrict__ cstruct, const GmpStruct* __restrict__ S,
+                         const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
+                         const GmpPair* __restrict__ pairs, const float* __restrict__ ktab, int nsig_total,
+                         int kmax) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t n = *count;
-  if (n > cap) {
-    if (warp == 0 && lane == 0) atomicOr(err, GMP_DEV_CAPACITY);
-    n = cap;
+  const unsigned long long n = *count;
+  const int64_t nq = n < (unsigned long long)cap ? (int64_t)n : cap;
+  for (int64_t t = warp; t < nq; t += nw) {
+    const unsigned long long e = queue[t];
+    refine_entry(lane, (int64_t)(e >> 16), (int)(e & 0xffffu), col_info, features, F, atom_xh, atom_xl, cxh, cxl,
+                 cstruct, S, nbr_beg, nbr_end, pairs, ktab, nsig_total, kmax);
   }
-  for (int64_t t = warp; t < n; t += nw) {
-    const unsigned long long e = flags[t];
-    const int64_t i = (int64_t)(e >> 28);
-    const int l = (int)((e >> 24) & 15);
-    const int sig = (int)((e >> 12) & 4095);
-    const int col = (int)(e & 4095);
-    const GmpStruct& st = S[cstruct[i]];
-    const float4 xhi = cxh[i], xli = cxl[i];
-    gmp_f2 mu[13];
-    for (int k = 0; k < 13; ++k) mu[k] = gmp_f2{0.0f, 0.0f};
-    const int64_t p0 = nbr_beg[i], p1 = nbr_end[i];
-    switch (l) {  // warp-uniform: every lane works on the same entry
-      case 0: refine_moments<0>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 1: refine_moments<1>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 2: refine_moments<2>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 3: refine_moments<3>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 4: refine_moments<4>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 5: refine_moments<5>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      case 6: refine_moments<6>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu); break;
-      default: break;
-    }
-    for (int k = 0; k <= 2 * l; ++k)
-      for (int o = 16; o; o >>= 1) {
-        const gmp_f2 other{__shfl_xor_sync(0xffffffffu, mu[k].hi, o), __shfl_xor_sync(0xffffffffu, mu[k].lo, o)};
-        mu[k] = gmp_df_add(mu[k], other);
+  if (n <= (unsigned long long)cap) return;
+  for (int64_t base = warp * 32; base < n_words; base += nw * 32) {
+    const uint32_t word = base + lane < n_words ? bits[base + lane] : 0u;
+    unsigned live = __ballot_sync(0xffffffffu, word != 0u);
+    while (live) {  // warp-uniform from here on
+      const int src = __ffs(live) - 1;
+      live &= live - 1;
+      uint32_t wv = __shfl_sync(0xffffffffu, word, src);
+      const int64_t tw = base + src;
+      const int64_t i = tw / FW;
+      const int cbase = (int)(tw - i * FW) * 32;
+      while (wv) {
+        const int col = cbase + __ffs(wv) - 1;
+        wv &= wv - 1;
+        refine_entry(lane, i, col, col_info, features, F, atom_xh, atom_xl, cxh, cxl, cstruct, S, nbr_beg, nbr_end,
+                     pairs, ktab, nsig_total, kmax);
       }
-    if (lane == 0) {
-      const gmp_f2 f = gmp_mcsh_invariant_df(l, mu);
-      features[i * F + col] = f.hi + f.lo;
     }
   }
 }
 
 }  // namespace
 
-cudaError_t gmp_launch_refine(const unsigned long long* flags, const int32_t* count, int64_t cap,
+cudaError_t gmp_launch_refine(const unsigned long long* queue, const unsigned long long* count, int64_t cap,
+                              const uint32_t* bits, int64_t n_centers, int FW, const int32_t* col_info,
                               float* features, int F, const float4* atom_xh, const float4* atom_xl,
                               const float4* center_xh, const float4* center_xl, const int32_t* center_struct,
                               const GmpStruct* structs, const int64_t* nbr_beg, const int64_t* nbr_end,
-                              const GmpPair* pairs, const float* ktab, int nsig_total, int kmax, uint32_t* err,
-                              int sm_count, cudaStream_t stream, int64_t* launches) {
-  k_refine<<<sm_count * 4, 256, 0, stream>>>(flags, count, cap, features, F, atom_xh, atom_xl, center_xh, center_xl,
-                                             center_struct, structs, nbr_beg, nbr_end, pairs, ktab, nsig_total, kmax,
-                                             err);
+                              const GmpPair* pairs, const float* ktab, int nsig_total, int kmax, int sm_count,
+                              cudaStream_t stream, int64_t* launches) {
+  if (n_centers <= 0) return cudaSuccess;
+  k_refine<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(queue, count, cap, bits, n_centers * FW, FW, col_info,
+                                                         features, F, atom_xh, atom_xl, center_xh, center_xl,
+                                                         center_struct, structs, nbr_beg, nbr_end, pairs, ktab,
+                                                         nsig_total, kmax);
   ++*launches;
   return cudaGetLastError();
 }

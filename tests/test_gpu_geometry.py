@@ -135,3 +135,26 @@ def test_image_index_limit_reported(torch):
     f = F.featurize(torch.from_numpy(w.positions).cuda(), sp, w.atom_off, w.cells, w.pbc)
     torch.cuda.synchronize()
     assert torch.isfinite(f).all()
+
+
+def test_near_symmetric_crystals(torch, oracle_mod):
+    """One-element FCC crystals, perfect and with 1e-4 / 1e-3 A jitter:
+    by symmetry the orders 1, 2, 3 and 5 vanish or nearly vanish at every
+    center, so most of each center's 112 features are ill-conditioned in
+    FP32 and take the double-float recomputation (64 per center)."""
+    base = synth.fcc_slab262k(reps=(3, 3, 3))
+    rng = np.random.default_rng(3)
+    parts = []
+    for jitter in (0.0, 1e-4, 1e-3):
+        pos, cell = synth.fcc_supercell(rng, 3.9, (4, 4, 4), jitter)
+        parts.append((pos, np.zeros(len(pos), np.int32), cell, (1, 1, 1)))
+    w = _batch(base, parts)
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    f = F.featurize(torch.from_numpy(w.positions).cuda(), torch.from_numpy(w.species).cuda(),
+                    w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    centers = np.concatenate([np.arange(0, 256, 5), np.arange(256, 768, 3)])
+    ref, fabs = oracle_mod.features(w, centers, want_abs=True)
+    err = feature_errors(f.cpu().numpy()[centers], ref, fabs)
+    assert err.max() <= FEAT_TOL, err.max()
