@@ -313,12 +313,26 @@ def cpu_baseline(w, feat_dev, gp_dev, g_np, budget_s=15.0):
     base = {"value": n * w.n_features / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": f"{n} random centers of {w.name}: FP64 features + d(features)/d(positions) rows"}
     f = feat_dev.cpu().numpy()[c]
-    ferr = float(np.max(np.abs(f - f_ref) / np.maximum(np.abs(f_ref), 1e-6 * f_abs)))
+    err = np.abs(f - f_ref) / np.maximum(np.abs(f_ref), 1e-6 * f_abs)
+    ferr = float(np.max(err))
+    # per feature group: the (order, sigma) columns, order-major; order -1 has one column
+    col_err = err.max(axis=0)
+    by_order, worst, c0 = {}, (None, None, -1.0), 0
+    for l in w.orders:
+        nc = 1 if l < 0 else len(w.sigmas)
+        e = col_err[c0:c0 + nc]
+        by_order[str(l)] = float(e.max())
+        k = int(np.argmax(e))
+        if e[k] > worst[2]:
+            worst = (int(l), None if l < 0 else float(w.sigmas[k]), float(e[k]))
+        c0 += nc
     atoms = synth.subset_centers(w.n_atoms, 4, seed=12)
     gref, gscale = O.vjp_atoms(w, g_np, atoms, want_abs=True)
     gerr = float(np.max(np.linalg.norm(gp_dev.cpu().numpy()[atoms] - gref, axis=1)
                         / np.maximum(np.linalg.norm(gref, axis=1), 1e-3 * gscale)))
     acc = {"features_max_rel_err": ferr, "grad_max_rel_err": gerr,
+           "features_max_rel_err_by_order": by_order,
+           "worst_group": {"order": worst[0], "sigma": worst[1], "rel_err": worst[2]},
            "sample": f"{n} centers (features), 4 atoms (VJP)",
            "floors": "features: max(|f|, 1e-6 F_abs); grads: max(|g|, 1e-3 G_abs)"}
     return base, acc

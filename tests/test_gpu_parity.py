@@ -7,7 +7,8 @@ import pytest
 
 from paper_2303_12980_gb300 import synth
 
-from parity import (FEAT_TAU, FEAT_TOL, GRAD_TAU, GRAD_TOL, feature_errors, grad_errors, record)
+from parity import (FEAT_TAU, FEAT_TOL, FP32_MIN_NORMAL, GRAD_TAU, GRAD_TOL, feature_errors, grad_errors,
+                    record)
 
 pytestmark = pytest.mark.gpu
 
@@ -143,6 +144,79 @@ def test_jacobian_parity(torch, oracle_mod, name, n_centers):
         worst = max(worst, float(err.max()))
     record(f"jacobian/{name}", max_rel_err=worst, nnz=int(joff[-1]))
     assert worst <= GRAD_TOL, worst
+
+
+def test_jacobian_central_differences(torch, oracle_mod):
+    """The GPU Jacobian (featurize_grad) and VJP against central differences
+    of the FP64 oracle features, h = 1e-4 A, on fcc4096: (a) 32 atoms one at
+    a time, each moved along its own random direction, every feature of
+    every center that sees it; (b) the whole structure along one random
+    displacement field, contracted with random feature weights.  Atoms
+    with an image pair near the cutoff stay fixed (the features are
+    discontinuous there)."""
+    w = wl("fcc4096")
+    h = 1e-4
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    joff, jj, jac = joff.cpu().numpy(), jj.cpu().numpy(), jac.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(123)
+    # The features jump where a pair crosses the hard cutoff, so only atoms
+    # with no image pair within 2e-3 A of rc (on either side) are moved; the
+    # steps below move any pair distance by less than 1e-3 A.
+    noff_all, nj_all, _, nd_all = oracle_mod.neighbors(w.replace(cutoff=w.cutoff + 2e-3))
+    near = np.abs(np.linalg.norm(nd_all, axis=1) - w.cutoff) < 2e-3
+    center_of = np.repeat(np.arange(w.n_atoms), np.diff(noff_all))
+    movable = np.ones(w.n_atoms, bool)
+    movable[center_of[near]] = False
+    movable[nj_all[near]] = False
+    free = np.flatnonzero(movable)
+    assert free.size > w.n_atoms // 2
+    worst = 0.0
+    for a in free[synth.subset_centers(free.size, 32, seed=41)]:
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        noff, nj, _, _ = oracle_mod.neighbors(w, np.array([a]))
+        centers = np.unique(np.concatenate([nj[noff[0]:noff[1]], [a]])).astype(np.int64)
+        fd = []
+        for sgn in (1.0, -1.0):
+            x = w.positions.copy()
+            x[a] += sgn * h * u
+            fd.append(oracle_mod.features(w.replace(positions=x), centers))
+        fd = (fd[0] - fd[1]) / (2.0 * h)                       # [nc, F]
+        # denominators as in grad_errors: the derivative vector's length
+        # (from the oracle's analytic row), floored at GRAD_TAU x its
+        # cancellation-free scale and at the smallest normal FP32 number
+        ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+        gpu = np.zeros_like(fd)
+        den = np.zeros_like(fd)
+        for t, i in enumerate(centers):
+            k = joff[i] + np.searchsorted(jj[joff[i]:joff[i + 1]], a)
+            assert jj[k] == a
+            gpu[t] = jac[k] @ u
+            ko = ooff[t] + np.searchsorted(oj[ooff[t]:ooff[t + 1]], a)
+            den[t] = np.maximum(np.maximum(np.linalg.norm(ojac[ko], axis=-1), GRAD_TAU * oabs[ko]), FP32_MIN_NORMAL)
+        err = np.abs(gpu - fd) / den
+        worst = max(worst, float(err.max()))
+    # (b) one displacement field over all atoms, weights g: d/de sum g . f(x + e delta)
+    delta = np.clip(rng.normal(size=w.positions.shape), -2.5, 2.5) * movable[:, None]
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=5)
+    sums = []
+    for sgn in (1.0, -1.0):
+        sums.append(float(np.sum(g * oracle_mod.features(w.replace(positions=w.positions + sgn * h * delta)))))
+    fd_all = (sums[0] - sums[1]) / (2.0 * h)
+    _, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    vjp_dir = float(np.sum(gp.cpu().numpy().astype(np.float64) * delta))
+    rows_i = np.repeat(np.arange(w.n_atoms), np.diff(joff))
+    jd = np.einsum("rfc,rc->rf", jac, delta[jj])                 # per row: J delta_j
+    jac_dir = float(np.sum(g[rows_i] * jd))
+    scale_all = float(np.sum(np.abs(g[rows_i] * jd)))
+    err_all = max(abs(vjp_dir - fd_all), abs(jac_dir - fd_all)) / max(abs(fd_all), 1e-3 * scale_all)
+    record("jacobian/central_differences", per_atom_max_rel_err=worst, field_rel_err=err_all)
+    assert worst <= GRAD_TOL, worst
+    assert err_all <= GRAD_TOL, err_all
 
 
 def test_autograd_function_matches_vjp(torch):
