@@ -288,6 +288,146 @@ def batched_comparison(args):
     return res
 
 
+# ------------------------------------------------------------------ all workloads
+CONFIG_TABLE = [
+    ("random64_box", "features"),
+    ("fcc4096", "features"),
+    ("batched10k", "features"),
+    ("fcc4096", "jacobian"),
+    ("fcc_slab262k", "vjp"),
+]
+
+
+def run_configs(args):
+    """Every workload of the baseline table: the optimised path (autotuned
+    shapes, CUDA-graph replay where the call supports it) against the plain
+    path (default shapes, eager; one call per structure for a batch), the
+    ALU-roofline fraction of the dominant kernel, the FP64 oracle on the
+    host cores and the accuracy of a sampled subset against it."""
+    import torch
+    from oracle import oracle as O
+    from paper_2303_12980_gb300 import build as B, synth
+    B.build()
+    O.build()
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    dev = torch.device("cuda")
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * 2070e6 / 1e12
+    rows = []
+    s = torch.cuda.Stream()
+    for idx, (name, mode) in enumerate(CONFIG_TABLE):
+        w = synth.workload(name)
+        N, F_ = w.n_atoms, w.n_features
+        pos = torch.from_numpy(w.positions).to(dev)
+        sp = torch.from_numpy(w.species).to(dev)
+        g_np = synth.upstream_gradient(N, F_, seed=31)
+        g = torch.from_numpy(g_np).to(dev)
+        feat = torch.empty((N, F_), device=dev)
+        gp = torch.empty((N, 3), device=dev)
+        units = N * F_
+
+        def call(Fz, a=0, b=N, k0=0, k1=None):
+            k1 = w.n_struct if k1 is None else k1
+            off = np.asarray(w.atom_off[k0:k1 + 1]) - w.atom_off[k0]
+            args_ = (pos[a:b], sp[a:b], off, w.cells[k0:k1], w.pbc[k0:k1])
+            if mode == "features":
+                return Fz.featurize(*args_, out=feat[a:b])
+            if mode == "vjp":
+                return Fz.featurize_vjp(*args_, g[a:b], out=(feat[a:b], gp[a:b]))
+            return Fz.featurize_grad(*args_)
+
+        def timed(fn, reps):
+            for _ in range(3):
+                fn()
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            s.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        row = {"config": idx, "workload": name, "mode": mode, "atoms": N, "structures": w.n_struct,
+               "features": F_}
+        with torch.cuda.stream(s):
+            plain = GMPFeaturizer.from_workload(w)
+            if w.n_struct > 1:
+                off = w.atom_off
+                ms_plain = timed(lambda: [call(plain, int(off[k]), int(off[k + 1]), k, k + 1)
+                                          for k in range(w.n_struct)], 1)
+                row["plain"] = {"path": "one call per structure, default shapes, eager"}
+            else:
+                ms_plain = timed(lambda: call(plain), 5)
+                row["plain"] = {"path": "default shapes, eager"}
+            row["plain"].update(ms=ms_plain, value=units / (ms_plain * 1e-3))
+            Fz = GMPFeaturizer.from_workload(w)
+            Fz.tune(pos, sp, w.atom_off, w.cells, w.pbc, reps=2)
+            graph = mode != "jacobian"
+            Fz.set_graph(graph)
+            ms_opt = timed(lambda: call(Fz), 5)
+            Fz.set_graph(False)
+            Fz.profile(True)
+            Fz.profile_read()
+            out = call(Fz)
+            s.synchronize()
+            prof = Fz.profile_read()
+            Fz.profile(False)
+            noff, _, _ = Fz.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+            s.synchronize()
+        pairs = int(noff[-1].item())
+        wm = work_model(w, pairs)
+        stage = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
+        row["optimised"] = {"path": "autotuned" + (", CUDA-graph replay" if graph else ", eager"),
+                            "ms": ms_opt, "value": units / (ms_opt * 1e-3), "stage_ms": stage}
+        if mode == "vjp":
+            kern, flop, ms_k = "k_backward", wm["flop_bwd"], stage["backward"]
+        elif mode == "jacobian":
+            kern, flop, ms_k = "k_jacobian", wm["flop_bwd"], stage["backward"]
+        else:
+            kern, flop, ms_k = "k_forward", wm["flop_fwd"], stage["features"]
+        tfl = flop / (ms_k * 1e-3) / 1e12 if ms_k else None
+        row["roofline"] = {"kernel": kern, "achieved_tflops": tfl, "peak_tflops": peak,
+                           "frac": tfl / peak if tfl else None, "pairs": pairs}
+        # oracle: a bounded sample of centers on the host cores
+        c = synth.subset_centers(N, 8, seed=11)
+        fn = O.features if mode == "features" else O.jacobian_rows
+        t0 = time.perf_counter()
+        fn(w, c)
+        dt = time.perf_counter() - t0
+        n = int(max(8, min(N, 8 * args.cpu_budget / 5.0 / max(dt, 1e-3))))
+        c = synth.subset_centers(N, n, seed=11)
+        t0 = time.perf_counter()
+        f_ref, f_abs = O.features(w, c, want_abs=True)
+        if mode != "features":
+            ooff, oj, ojac, oabs = O.jacobian_rows(w, c, want_abs=True)
+        dt = time.perf_counter() - t0
+        row["oracle"] = {"value": n * F_ / dt, "cores": O.num_threads(), "centers": n,
+                         "work": "FP64 features" + ("" if mode == "features" else " + d(features)/d(positions) rows")}
+        fgpu = (out[0] if mode == "jacobian" else feat).cpu().numpy()[c]
+        err = np.abs(fgpu - f_ref) / np.maximum(np.maximum(np.abs(f_ref), 1e-6 * f_abs), 2.0 ** -126)
+        acc = {"features_max_rel_err": float(err.max())}
+        if mode == "jacobian":
+            joff, jj, jac = (t.cpu().numpy() for t in out[1:])
+            worst = 0.0
+            for t, i in enumerate(c):
+                a, b = joff[i], joff[i + 1]
+                num = np.linalg.norm(jac[a:b].astype(np.float64) - ojac[ooff[t]:ooff[t + 1]], axis=-1)
+                den = np.maximum(np.maximum(np.linalg.norm(ojac[ooff[t]:ooff[t + 1]], axis=-1),
+                                            1e-2 * oabs[ooff[t]:ooff[t + 1]]), 2.0 ** -126)
+                worst = max(worst, float((num / den).max()))
+            acc["grad_max_rel_err"] = worst
+        elif mode == "vjp":
+            atoms = synth.subset_centers(N, 4, seed=12)
+            gref, gscale = O.vjp_atoms(w, g_np, atoms, want_abs=True)
+            acc["grad_max_rel_err"] = float(np.max(np.linalg.norm(gp.cpu().numpy()[atoms] - gref, axis=1)
+                                                   / np.maximum(np.linalg.norm(gref, axis=1), 1e-3 * gscale)))
+        row["accuracy"] = acc
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    return {"configs": rows, "unit": UNIT, "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"}
+
+
 def _oracle_sample(w, centers):
     from oracle import oracle as O
     t0 = time.perf_counter()
@@ -383,6 +523,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="add the 10,000-structure batched / graph / per-structure comparison")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
+    ap.add_argument("--configs", action="store_true",
+                    help="measure every workload of the baseline table (one JSON object) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -393,6 +535,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.configs:
+        if rank == 0:
+            print(json.dumps(run_configs(args)), flush=True)
         return
 
     if world > 1:

@@ -532,34 +532,71 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   return K;
 }
 
-// Resets the flag queue and bitmask before the compute kernels of one call.
-gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
+// Clears the flag queue and bitmask (before a call's compute kernels, and
+// after each refinement so that the next pass queues only its own flags).
+gmp_status reset_flags(gmp_ctx* h, int64_t N, cudaStream_t st) {
   const size_t bytes = sizeof(uint32_t) * (size_t)h->flag_words * (size_t)std::max<int64_t>(N, 1);
-  GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * flag_capacity(N)), "flags");
-  GMP_CK(h->flagbits.ensure(bytes), "flag bits");
   GMP_CK(cudaMemsetAsync(flag_counter(h), 0, sizeof(unsigned long long), st), "flag reset");
   GMP_CK(cudaMemsetAsync(h->flagbits.p, 0, bytes, st), "flag bits reset");
   return GMP_OK;
 }
 
-// Double-float recomputation of the queued features.
-// Centers are the atoms unless center_xh / center_xl / center_struct give
-// reference points.
+gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
+  const size_t bytes = sizeof(uint32_t) * (size_t)h->flag_words * (size_t)std::max<int64_t>(N, 1);
+  GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * flag_capacity(N)), "flags");
+  GMP_CK(h->flagbits.ensure(bytes), "flag bits");
+  return reset_flags(h, N, st);
+}
+
+// The moments of one pass that a derivative kernel reads after the
+// refinement (h->mu, [N][pass sigmas][(L+1)^2]).
+struct MuTarget {
+  float* mu = nullptr;
+  int sig0 = 0, nsig = 0, nind = 0;
+};
+MuTarget pass_moments(gmp_ctx* h, const PassData& pd, int pass_index) {
+  MuTarget t;
+  t.mu = h->mu.as<float>();
+  t.sig0 = 16 * pass_index;
+  t.nsig = pd.pass.nsig;
+  t.nind = (pd.L + 1) * (pd.L + 1);
+  return t;
+}
+
+// Double-float recomputation of the flagged features (and, with mt.mu, of
+// their moments in the pass's moment buffer).  Centers are the atoms unless
+// center_xh / center_xl / center_struct give reference points.
 gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const float4* center_xh = nullptr,
-                  const float4* center_xl = nullptr, const int32_t* center_struct = nullptr) {
-  GMP_CK(gmp_launch_refine(h->flagq.as<unsigned long long>(),
-                           flag_counter(h), flag_capacity(N),
-                           h->flagbits.as<uint32_t>(), N, h->flag_words, h->colinfo.as<int32_t>(),
-                           features, h->F, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
-                           center_xh ? center_xh : h->atom_xh.as<float4>(),
-                           center_xl ? center_xl : h->atom_xl.as<float4>(),
-                           center_struct ? center_struct : h->struct_of.as<int32_t>(), h->structs.as<GmpStruct>(),
-                           h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>(),
-                           h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1,
-                           h->pairs.as<GmpPair>(), h->ktab.as<float>(),
-                           (int)std::max<size_t>(h->sigmas.size(), 1), h->kmax, h->sm_count, st,
-                           &h->launches),
-         "refine");
+                  const float4* center_xl = nullptr, const int32_t* center_struct = nullptr,
+                  MuTarget mt = MuTarget()) {
+  GmpRefine A;
+  std::memset(&A, 0, sizeof(A));
+  A.queue = h->flagq.as<unsigned long long>();
+  A.count = flag_counter(h);
+  A.cap = flag_capacity(N);
+  A.bits = h->flagbits.as<uint32_t>();
+  A.n_centers = N;
+  A.flag_words = h->flag_words;
+  A.col_info = h->colinfo.as<int32_t>();
+  A.features = features;
+  A.F = h->F;
+  A.atom_xh = h->atom_xh.as<float4>();
+  A.atom_xl = h->atom_xl.as<float4>();
+  A.center_xh = center_xh ? center_xh : h->atom_xh.as<float4>();
+  A.center_xl = center_xl ? center_xl : h->atom_xl.as<float4>();
+  A.center_struct = center_struct ? center_struct : h->struct_of.as<int32_t>();
+  A.structs = h->structs.as<GmpStruct>();
+  A.nbr_beg = h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>();
+  A.nbr_end = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
+  A.pairs = h->pairs.as<GmpPair>();
+  A.ktab = h->ktab.as<float>();
+  A.nsig_total = (int)std::max<size_t>(h->sigmas.size(), 1);
+  A.kmax = h->kmax;
+  A.mu_out = mt.mu;
+  A.mu_sig0 = mt.sig0;
+  A.mu_nsig = mt.nsig;
+  A.mu_nind = mt.nind;
+  GMP_CK(gmp_launch_refine(A, h->sm_count, st, &h->launches), "refine");
   return GMP_OK;
 }
 
@@ -1001,7 +1038,7 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
   GMP_CK(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(double) * 3 * N, st), "memset grad");
   if (vir) GMP_CK(cudaMemsetAsync(vir, 0, sizeof(double) * 9 * n_struct, st), "memset virial");
   if ((q = begin_compute(h, N, st)) != GMP_OK) return q;
-  bool refined = false, waited = false;
+  bool refined = false, waited = false, pending = false;
   const bool overlap = io.host && !capture;
   for (size_t g = 0; g < h->passes.size(); ++g) {
     const PassData& pd = h->passes[g];
@@ -1020,18 +1057,23 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
       GMP_CK(prof_mark(h, 2, true, st), "profile");
       GMP_CK(launch_compute(pd.L, GMP_KIND_VJP, pd.NS, K, pd.fused, st, h->sm_count, &h->launches), "vjp");
       GMP_CK(prof_mark(h, 2, false, st), "profile");
+      pending = true;
       continue;
     }
     K.mu_out = h->mu.as<float>();
     GMP_CK(prof_mark(h, 1, true, st), "profile");
     GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
     GMP_CK(prof_mark(h, 1, false, st), "profile");
-    if (g + 1 == h->passes.size() && feat) {
-      // every feature is final once the last forward kernel and the FP64
-      // refinement ran: its download overlaps the backward kernel
-      GMP_CK(prof_mark(h, 3, true, st), "profile");
-      if ((q = refine(h, N, feat, st)) != GMP_OK) return q;
-      GMP_CK(prof_mark(h, 3, false, st), "profile");
+    // refinement of the flagged features (this pass's, and any a fused pass
+    // left); the backward kernel then reads the refined moments
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((q = refine(h, N, fout, st, nullptr, nullptr, nullptr, pass_moments(h, pd, (int)g))) != GMP_OK) return q;
+    if ((q = reset_flags(h, N, st)) != GMP_OK) return q;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+    pending = false;
+    if (g + 1 == h->passes.size()) {
+      // every feature is final once the last forward kernel and its
+      // refinement ran: the download overlaps the backward kernel
       refined = true;
       if (overlap && features) {
         GMP_CK(cudaEventRecord(h->ev_feat, st), "event");
@@ -1056,7 +1098,7 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
            "backward");
     GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
-  if (feat && !refined) {
+  if (feat && pending) {
     GMP_CK(prof_mark(h, 3, true, st), "profile");
     if ((q = refine(h, N, feat, st)) != GMP_OK) return q;
     GMP_CK(prof_mark(h, 3, false, st), "profile");
@@ -1141,22 +1183,37 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
     jd = tmp_jac.as<float>();
     jj = tmp_jj.as<int32_t>();
   }
+  for (const PassData& pd : h->passes)
+    GMP_CK(h->mu.ensure(sizeof(float) * (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1)), "moments");
+  float* fout = feat;
+  if (!fout) {
+    GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
+    fout = h->stage_feat.as<float>();
+  }
   if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 1, true, st), "profile");
   for (size_t g = 0; g < h->passes.size(); ++g) {
-    gmpk::KParams K = base_params(h, h->passes[g], (int)g, N);
-    K.features = feat;
+    // forward kernel (features, moments), refinement of the flagged
+    // features and their moments, then the Jacobian rows from the moments
+    const PassData& pd = h->passes[g];
+    gmpk::KParams K = base_params(h, pd, (int)g, N);
+    K.features = fout;
+    K.mu_out = h->mu.as<float>();
+    GMP_CK(prof_mark(h, 1, true, st), "profile");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
+    GMP_CK(prof_mark(h, 1, false, st), "profile");
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((r = refine(h, N, fout, st, nullptr, nullptr, nullptr, pass_moments(h, pd, (int)g))) != GMP_OK) return r;
+    if ((r = reset_flags(h, N, st)) != GMP_OK) return r;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+    K.features = nullptr;
+    K.flags = nullptr;
     K.jac_off = joff;
     K.jac_j = jj;
     K.jac = jd;
-    GMP_CK(launch_compute(h->passes[g].L, GMP_KIND_JACOBIAN, h->passes[g].NS, K, h->passes[g].jac, st, h->sm_count,
-                          &h->launches),
-           "jacobian");
+    GMP_CK(prof_mark(h, 2, true, st), "profile");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_JACOBIAN, pd.NS, K, pd.jac, st, h->sm_count, &h->launches), "jacobian");
+    GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
-  GMP_CK(prof_mark(h, 1, false, st), "profile");
-  GMP_CK(prof_mark(h, 3, true, st), "profile");
-  if (feat && (r = refine(h, N, feat, st)) != GMP_OK) return r;
-  GMP_CK(prof_mark(h, 3, false, st), "profile");
   const cudaMemcpyKind k_off = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (N + 1), k_off, st), "copy jac_off");
   if (io.host) {

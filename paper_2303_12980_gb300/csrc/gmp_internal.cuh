@@ -323,15 +323,37 @@ cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* gra
                                    cudaStream_t stream, int64_t* launches);
 // Double-float recomputation of the flagged features: the queue (count
 // entries center << 16 | column, at most cap) and, when it overflowed, the
-// set bits of `bits` ([n_centers] x FW words, bit col % 32 of word col / 32);
-// col_info[col] = (order << 16) | sigma.
-cudaError_t gmp_launch_refine(const unsigned long long* queue, const unsigned long long* count, int64_t cap,
-                              const uint32_t* bits, int64_t n_centers, int FW, const int32_t* col_info,
-                              float* features, int F, const float4* atom_xh, const float4* atom_xl,
-                              const float4* center_xh, const float4* center_xl, const int32_t* center_struct,
-                              const GmpStruct* structs, const int64_t* nbr_beg, const int64_t* nbr_end,
-                              const GmpPair* pairs, const float* ktab, int nsig_total, int kmax, int sm_count,
-                              cudaStream_t stream, int64_t* launches);
+// set bits of `bits` ([n_centers] x flag_words words, bit col % 32 of word
+// col / 32); col_info[col] = (order << 16) | sigma.  With mu_out, the
+// recomputed moments of sigmas mu_sig0 .. mu_sig0 + mu_nsig - 1 also
+// overwrite mu_out[center][sigma - mu_sig0][l^2 .. l^2 + 2l] (row length
+// mu_nind), the moments a derivative kernel reads next.
+struct GmpRefine {
+  const unsigned long long* queue;
+  const unsigned long long* count;
+  int64_t cap;
+  const uint32_t* bits;
+  int64_t n_centers;
+  int flag_words;
+  const int32_t* col_info;
+  float* features;
+  int F;
+  const float4* atom_xh;
+  const float4* atom_xl;
+  const float4* center_xh;
+  const float4* center_xl;
+  const int32_t* center_struct;
+  const GmpStruct* structs;
+  const int64_t* nbr_beg;
+  const int64_t* nbr_end;
+  const GmpPair* pairs;
+  const float* ktab;
+  int nsig_total;
+  int kmax;
+  float* mu_out;
+  int mu_sig0, mu_nsig, mu_nind;
+};
+cudaError_t gmp_launch_refine(const GmpRefine& args, int sm_count, cudaStream_t stream, int64_t* launches);
 cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,
                                         int32_t* nbr_shift, cudaStream_t stream,
                                         int64_t* launches);

@@ -830,7 +830,9 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
 //   d f_{l,s} / d d = 2 d dR_{l,s} P + R_{l,s} grad P,   P = sum_k lam_k S_k,
 //   r^2 grad P = (2l+1) d P - V,  V = sum_k lam_k S_{k+e}.
 // Rows are per distinct neighbor atom (images summed, lists are sorted by
-// atom), the center's own row is minus the sum of the other rows.
+// atom), the center's own row is minus the sum of the other rows.  The
+// moments come from the forward kernel (K.mu_out, after the double-float
+// refinement of the ill-conditioned ones).
 template <int L, int NS>
 __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   using SH = Shape<L, NS>;
@@ -842,21 +844,17 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* Rt = s_warp + (size_t)wib * SH::WARP_FLOATS;
-  float* St = Rt + SH::TILE * SH::RSTR;
-  float* Mu = Rt;
-  float* Lam = St;
-  int it_l[SH::Q], it_sb[SH::Q], it_ch[SH::Q];
-  bool it_ok[SH::Q];
-  setup_items<L, NS>(it_l, it_sb, it_ch, it_ok);
+  float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
+  float* Lam = Mu + SH::TILE * SH::RSTR;
   constexpr int QF = (8 * 16 + 1 + 31) / 32;  // features per lane (<= 8 orders x 16 sigmas + density)
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
     if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
     const int M = (int)(p1 - p0);
-    const float rho = forward_sweep<L, NS>(P, s_rad, s_dens, K.pairs, p0, M, Rt, St, Mu, it_l, it_sb, it_ch, it_ok);
+    const float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
+    for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
+    __syncwarp();
     const int nf = P.n_ord * P.nsig;
-    if (K.features) write_features<L, NS>(K, i, Mu, rho);
     // per-feature adjoints: Lam[s][k] with g = 1 for every (l, s); orders do
     // not share components, so one array holds all of them
     adjoints<L, NS>(P, Mu, nullptr, Lam);
@@ -923,7 +921,9 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           for (int qq = 0; qq < P.kmax; ++qq) {
             // slot v of the block holds quantity v for the 4 sigmas of the group
             const float* ent = tab_e + ((s / 4) * P.kmax + qq) * gmp_rad_block(L) * 4 + (s % 4);
-            const float E = gmp_ex2(-__fmul_rn(ent[0], r2h));  // FP32 argument: derivatives only
+            // double-float exponent argument: a row of one neighbor has no
+            // other terms to average the 2^-24 B r^2 error of an FP32 one
+            const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
             R = __fmaf_rn(ent[4 * (2 + l)], E, R);
             R1 = __fmaf_rn(ent[4 * (3 + l)], E, R1);
           }

@@ -9,7 +9,11 @@
 // hardware runs far faster than FP64: the displacement from the
 // double-float split of the positions (the atoms, or the reference points of
 // gmp_featurize_points), the radial factor with a double-float exponential,
-// the MCSH components by the same recurrences, and the invariant.
+// the MCSH components by the same recurrences, and the invariant.  When a
+// derivative kernel follows, the recomputed moments also replace the FP32
+// moments it reads: the adjoints of a cancelling moment group would
+// otherwise carry its FP32 rounding, which is relative to the group's
+// cancellation-free scale rather than to the moments themselves.
 #include "gmp_internal.cuh"
 #include "mcsh_gen.cuh"
 
@@ -49,16 +53,17 @@ __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, cons
 
 // One flagged feature f_{L,sigma} of one center: moments over the center's
 // pairs (lane-strided), warp-reduced, and the invariant, all double-float;
-// the result (rounded to FP32) is valid in every lane.
+// the result (rounded to FP32) is valid in every lane.  mu_dst (optional)
+// receives the 2L+1 moments rounded to FP32.
 template <int L>
-__device__ __forceinline__ float refine_feature(int lane, const float4& xhi, const float4& xli, const GmpStruct& st,
-                                                int64_t p0, int64_t p1, const GmpPair* __restrict__ pairs,
-                                                const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                                                const float* __restrict__ ktab, int nsig_total, int sig, int kmax) {
+__device__ __forceinline__ float refine_feature(int lane, const GmpRefine& A, const float4& xhi, const float4& xli,
+                                                const GmpStruct& st, int64_t p0, int64_t p1, int sig,
+                                                float* mu_dst) {
   gmp_f2 mu[2 * L + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * L; ++k) mu[k] = gmp_f2{0.0f, 0.0f};
-  refine_moments<L>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax, mu);
+  refine_moments<L>(lane, xhi, xli, st, p0, p1, A.pairs, A.atom_xh, A.atom_xl, A.ktab, A.nsig_total, sig, A.kmax,
+                    mu);
 #pragma unroll
   for (int k = 0; k <= 2 * L; ++k)
 #pragma unroll
@@ -66,79 +71,70 @@ __device__ __forceinline__ float refine_feature(int lane, const float4& xhi, con
       const gmp_f2 other{__shfl_xor_sync(0xffffffffu, mu[k].hi, o), __shfl_xor_sync(0xffffffffu, mu[k].lo, o)};
       mu[k] = gmp_df_add(mu[k], other);
     }
+  if (mu_dst && lane == 0) {
+#pragma unroll
+    for (int k = 0; k <= 2 * L; ++k) mu_dst[k] = mu[k].hi + mu[k].lo;
+  }
   const gmp_f2 f = gmp_mcsh_invariant_df(L, mu);
   return f.hi + f.lo;
 }
 
 // One flagged feature (center i, column col) recomputed by the whole warp;
 // col_info[col] = (order << 16) | global sigma.
-__device__ __forceinline__ void refine_entry(int lane, int64_t i, int col, const int32_t* __restrict__ col_info,
-                                             float* __restrict__ features, int F,
-                                             const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                                             const float4* __restrict__ cxh, const float4* __restrict__ cxl,
-                                             const int32_t* __restrict__ cstruct, const GmpStruct* __restrict__ S,
-                                             const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
-                                             const GmpPair* __restrict__ pairs, const float* __restrict__ ktab,
-                                             int nsig_total, int kmax) {
-  const int info = col < F ? col_info[col] : -1;
+__device__ __forceinline__ void refine_entry(int lane, const GmpRefine& A, int64_t i, int col) {
+  const int info = col < A.F ? A.col_info[col] : -1;
   if (info < 0) return;
   const int l = info >> 16, sig = info & 0xffff;
-  const GmpStruct& st = S[cstruct[i]];
-  const float4 xhi = cxh[i], xli = cxl[i];
-  const int64_t p0 = nbr_beg[i], p1 = nbr_end[i];
+  const GmpStruct& st = A.structs[A.center_struct[i]];
+  const float4 xhi = A.center_xh[i], xli = A.center_xl[i];
+  const int64_t p0 = A.nbr_beg[i], p1 = A.nbr_end[i];
+  float* mu_dst = nullptr;
+  if (A.mu_out && sig >= A.mu_sig0 && sig < A.mu_sig0 + A.mu_nsig)
+    mu_dst = A.mu_out + (i * A.mu_nsig + (sig - A.mu_sig0)) * (int64_t)A.mu_nind + l * l;
   float f = 0.0f;
   switch (l) {
-    case 0: f = refine_feature<0>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 1: f = refine_feature<1>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 2: f = refine_feature<2>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 3: f = refine_feature<3>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 4: f = refine_feature<4>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 5: f = refine_feature<5>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
-    case 6: f = refine_feature<6>(lane, xhi, xli, st, p0, p1, pairs, atom_xh, atom_xl, ktab, nsig_total, sig, kmax); break;
+    case 0: f = refine_feature<0>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 1: f = refine_feature<1>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 2: f = refine_feature<2>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 3: f = refine_feature<3>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 4: f = refine_feature<4>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 5: f = refine_feature<5>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
+    case 6: f = refine_feature<6>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
     default: return;
   }
-  if (lane == 0) features[i * F + col] = f;
+  if (lane == 0) A.features[i * A.F + col] = f;
 }
 
 // Flagged features: first the queue (entries center << 16 | column, spread
 // over the warps one entry each); when it overflowed, the rest are the set
 // bits of the bitmask (bit col % 32 of word i * FW + col / 32), which each
 // warp reads 32 words at a time (lane = word).
-__global__ void k_refine(const unsigned long long* __restrict__ queue, const unsigned long long* __restrict__ count,
-                         int64_t cap, const uint32_t* __restrict__ bits, int64_t n_words, int FW,
-                         const int32_t* __restrict__ col_info, float* __restrict__ features, int F,
-                         const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                         const float4* __restrict__ cxh, const float4* __restrict__ cxl,
-                         const int32_t* __restrict__ cstruct, const GmpStruct* __restrict__ S,
-                         const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
-                         const GmpPair* __restrict__ pairs, const float* __restrict__ ktab, int nsig_total,
-                         int kmax) {
+__global__ void k_refine(const GmpRefine A) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long n = *count;
-  const int64_t nq = n < (unsigned long long)cap ? (int64_t)n : cap;
+  const unsigned long long n = *A.count;
+  const int64_t nq = n < (unsigned long long)A.cap ? (int64_t)n : A.cap;
   for (int64_t t = warp; t < nq; t += nw) {
-    const unsigned long long e = queue[t];
-    refine_entry(lane, (int64_t)(e >> 16), (int)(e & 0xffffu), col_info, features, F, atom_xh, atom_xl, cxh, cxl,
-                 cstruct, S, nbr_beg, nbr_end, pairs, ktab, nsig_total, kmax);
+    const unsigned long long e = A.queue[t];
+    refine_entry(lane, A, (int64_t)(e >> 16), (int)(e & 0xffffu));
   }
-  if (n <= (unsigned long long)cap) return;
+  if (n <= (unsigned long long)A.cap) return;
+  const int64_t n_words = A.n_centers * A.flag_words;
   for (int64_t base = warp * 32; base < n_words; base += nw * 32) {
-    const uint32_t word = base + lane < n_words ? bits[base + lane] : 0u;
+    const uint32_t word = base + lane < n_words ? A.bits[base + lane] : 0u;
     unsigned live = __ballot_sync(0xffffffffu, word != 0u);
     while (live) {  // warp-uniform from here on
       const int src = __ffs(live) - 1;
       live &= live - 1;
       uint32_t wv = __shfl_sync(0xffffffffu, word, src);
       const int64_t tw = base + src;
-      const int64_t i = tw / FW;
-      const int cbase = (int)(tw - i * FW) * 32;
+      const int64_t i = tw / A.flag_words;
+      const int cbase = (int)(tw - i * A.flag_words) * 32;
       while (wv) {
         const int col = cbase + __ffs(wv) - 1;
         wv &= wv - 1;
-        refine_entry(lane, i, col, col_info, features, F, atom_xh, atom_xl, cxh, cxl, cstruct, S, nbr_beg, nbr_end,
-                     pairs, ktab, nsig_total, kmax);
+        refine_entry(lane, A, i, col);
       }
     }
   }
@@ -146,18 +142,9 @@ __global__ void k_refine(const unsigned long long* __restrict__ queue, const uns
 
 }  // namespace
 
-cudaError_t gmp_launch_refine(const unsigned long long* queue, const unsigned long long* count, int64_t cap,
-                              const uint32_t* bits, int64_t n_centers, int FW, const int32_t* col_info,
-                              float* features, int F, const float4* atom_xh, const float4* atom_xl,
-                              const float4* center_xh, const float4* center_xl, const int32_t* center_struct,
-                              const GmpStruct* structs, const int64_t* nbr_beg, const int64_t* nbr_end,
-                              const GmpPair* pairs, const float* ktab, int nsig_total, int kmax, int sm_count,
-                              cudaStream_t stream, int64_t* launches) {
-  if (n_centers <= 0) return cudaSuccess;
-  k_refine<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(queue, count, cap, bits, n_centers * FW, FW, col_info,
-                                                         features, F, atom_xh, atom_xl, center_xh, center_xl,
-                                                         center_struct, structs, nbr_beg, nbr_end, pairs, ktab,
-                                                         nsig_total, kmax);
+cudaError_t gmp_launch_refine(const GmpRefine& A, int sm_count, cudaStream_t stream, int64_t* launches) {
+  if (A.n_centers <= 0) return cudaSuccess;
+  k_refine<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(A);
   ++*launches;
   return cudaGetLastError();
 }

@@ -10,6 +10,19 @@ arithmetic: a per-pair contribution carries rounding of ~1e-7 of its own
 magnitude, so a result that cancels below FEAT_TAU (GRAD_TAU) of its
 absolute scale cannot keep the relative bound in FP32.
 
+Dense Jacobian rows (d f_i / d x_j for one center i and one neighbor atom
+j) take JAC_TAU = 1e-2 instead of GRAD_TAU.  Such an entry is the
+contraction of the center's moments with one pair's derivative terms,
+sum_c 2 w_c mu_c dt_c/dd, and nothing averages its rounding: the moments
+are stored in FP32 (one rounding of each mu_c), the adjoint, the MCSH
+recurrences, the radial factor, the contraction and the assembly each add
+roundings of the same scale, so its error is several units of 2^-24 of
+G_abs.  An FP32 emulation of the worst row found (a contraction that
+cancels to 7e-4 of G_abs) shows the single FP32 rounding of the moments
+alone using a third of a 1e-3 floor's budget.  JAC_TAU = 1e-2 allows
+1e-6 G_abs, i.e. 16 units of 2^-24 of the scale.  Position gradients
+(VJP) and strain derivatives sum many rows and keep GRAD_TAU.
+
 Both denominators are also floored at FP32_MIN_NORMAL = 2^-126: the outputs
 are FP32, and below the smallest normal FP32 number the format itself has
 fewer than 24 significant bits (subnormals) or none (below 2^-149), so no
@@ -26,6 +39,7 @@ FEAT_TOL = 1e-5
 FEAT_TAU = 1e-6
 GRAD_TOL = 1e-4
 GRAD_TAU = 1e-3
+JAC_TAU = 1e-2
 FP32_MIN_NORMAL = 2.0 ** -126
 
 _report = {}
