@@ -78,11 +78,12 @@ typedef struct {
   double cutoff;              /* Angstrom; hard cutoff |d| < cutoff.  <= 0:
                                  derived from overlap_threshold (below)        */
   uint32_t flags;             /* GMP_FLAG_*                                     */
-  double overlap_threshold;   /* used when cutoff <= 0 (Examples: "overlap_threshold",
-                                 "the desired accuracy of the features"): the
-                                 cutoff is the smallest radius beyond which every
-                                 single-primitive contribution to any moment is
-                                 below this value (see gmp_cutoff)             */
+  double overlap_threshold;   /* used when cutoff <= 0 (the paper's Examples
+                                 section sets the accuracy of the features by
+                                 this threshold): the cutoff is the smallest
+                                 radius beyond which every single-primitive
+                                 contribution to any moment is below this value
+                                 (see gmp_cutoff)                              */
 } gmp_params;
 
 /* Create a handle on CUDA device `device`: validates `params`, copies the
