@@ -254,8 +254,9 @@ int64_t gmp_kernel_launches(gmp_handle h);
 /* Stage timing (diagnostics, not part of the method).  With enable != 0 the
  * featurize calls record CUDA events on the caller's stream around
  *   stage 0: neighbor search (binning, count, fill),
- *   stage 1: the feature kernel (forward, or Jacobian),
- *   stage 2: the backward kernel of gmp_featurize_vjp,
+ *   stage 1: the forward (feature) kernel,
+ *   stage 2: the backward kernel of gmp_featurize_vjp, or the Jacobian
+ *            kernel of gmp_featurize_grad,
  *   stage 3: double-float refinement of ill-conditioned features;
  * gmp_profile_read synchronises those events and writes, per stage, the
  * summed milliseconds and the number of stage executions since the last
@@ -265,6 +266,13 @@ gmp_status gmp_profile_read(gmp_handle h, double *ms, int64_t *count, int n_stag
 
 /* Release the handle and its device memory. */
 void gmp_destroy(gmp_handle h);
+
+/* Throughput probes of CUDA device `device` at its present clocks
+ * (diagnostics, about 30 ms): FP32 FMA rate with scalar FMAs and with packed
+ * FP32-pair FMAs (TFLOP/s, 2 FLOP per FMA), and the SFU's ex2 rate (10^12
+ * per second).  Each probe runs independent dependency chains on every
+ * resident thread.  Needs no handle; GMP_ERR_CUDA if a launch fails. */
+gmp_status gmp_probe_peaks(int device, double *fma_tflops, double *fma2_tflops, double *ex2_tops);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,7 @@ _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GM
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_vjp_virial",
            "gmp_featurize_grad", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
            "gmp_sync", "gmp_profile", "gmp_profile_read",
-           "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
+           "gmp_probe_peaks", "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
 TUNING_CACHE = os.environ.get("GMP_TUNING_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "gmp_gb300", "tuning.json"))
 
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         L.gmp_last_error.restype = C.c_char_p
         L.gmp_kernel_launches.argtypes = [vp]
         L.gmp_kernel_launches.restype = i64
+        L.gmp_probe_peaks.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.gmp_destroy.argtypes = [vp]
         L.gmp_destroy.restype = None
         for name in EXPORTS[:-3]:
@@ -455,6 +456,17 @@ def _make_function():
 
 
 _fn_cache = {}
+
+
+def probe_peaks(device: int = 0) -> dict:
+    """Measured FP32 FMA (scalar, packed pairs) and ex2 throughput of a GPU
+    at its present clocks (gmp_probe_peaks)."""
+    L = load_library()
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    st = L.gmp_probe_peaks(int(device), C.byref(a), C.byref(b), C.byref(c))
+    if st != GMP_OK:
+        raise GMPError(st, "gmp_probe_peaks failed")
+    return {"fp32_fma_tflops": a.value, "fp32_fma2_tflops": b.value, "ex2_tops": c.value}
 
 
 def gmp_features(pos, featurizer, species, atom_off, cell, pbc):

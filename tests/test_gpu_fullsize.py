@@ -145,3 +145,16 @@ def test_neighbor_image_limit(torch):
     ok = GMPFeaturizer.from_workload(w).featurize(pos, sp, w.atom_off, w.cells, w.pbc)
     torch.cuda.synchronize()
     assert torch.isfinite(ok).all()
+
+
+def test_throughput_probes(torch):
+    """The FP32 FMA probes land near the nominal rate (SMs x 128 lanes x 2
+    FLOP x clock, at most the maximum clock) and the ex2 probe reports a
+    positive rate."""
+    from paper_2303_12980_gb300.binding import probe_peaks
+    p = probe_peaks(0)
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sm * 128 * 2 * 2.07e9 / 1e12
+    assert 0.3 * nominal < p["fp32_fma_tflops"] < 1.05 * nominal, p
+    assert 0.3 * nominal < p["fp32_fma2_tflops"] < 2.1 * nominal, p
+    assert p["ex2_tops"] > 0.0, p
