@@ -201,33 +201,35 @@ def fnum(v):
     return f"{float(v)!r}f"
 
 
-def emit_eval(L, dtype="float"):
-    """Straight-line evaluation of the independent components of orders
-    0..L by the raising recurrences, every product and sum explicit
-    (the build disables implicit contraction)."""
-    d = dtype == "double"
-    name = f"gmp_mcsh_indep{'_d' if d else ''}_{L}"
-    T = "double" if d else "float"
-    mul = "__dmul_rn" if d else "__fmul_rn"
-    fma = "__fma_rn" if d else "__fmaf_rn"
-    lit = (lambda v: f"{float(v)!r}") if d else fnum
-    lines = [f"__device__ __forceinline__ void {name}({T} x, {T} y, {T} z, {T} r2, {T}* __restrict__ S) {{"]
+def emit_eval_scaled(L):
+    """The raising recurrences with the integer coefficient folded into the
+    coordinate once per pair (c*x, c*y, c*z, c*r^2 products computed first),
+    so that each term of a component costs one FMA: every product and sum
+    explicit (the build disables implicit contraction)."""
+    lines = [f"__device__ __forceinline__ void gmp_mcsh_indep_{L}(float x, float y, float z, float r2, "
+             f"float* __restrict__ S) {{"]
+    scaled = {}
+    body = []
     for l in range(L + 1):
         for t in indep_components(l):
             k = flat(t)
             rec = recurrence_terms(t)
             if rec[0][1] == "1":
-                lines.append(f"  S[{k}] = {lit(1)};")
+                body.append(f"  S[{k}] = 1.0f;")
                 continue
             expr = None
             for coef, kind, src in rec:
                 v = "r2" if kind == "r2" else kind
-                prod = f"{mul}({v}, S[{flat(src)}])"
-                if expr is None:
-                    expr = prod if coef == 1 else f"{mul}({lit(coef)}, {prod})"
+                if coef == 1:
+                    m = v
                 else:
-                    expr = f"{fma}({lit(coef)}, {prod}, {expr})"
-            lines.append(f"  S[{k}] = {expr};")
+                    m = f"{v}_{'m' if coef < 0 else ''}{abs(coef)}"
+                    scaled[m] = f"__fmul_rn({fnum(coef)}, {v})"
+                expr = f"__fmul_rn({m}, S[{flat(src)}])" if expr is None else f"__fmaf_rn({m}, S[{flat(src)}], {expr})"
+            body.append(f"  S[{k}] = {expr};")
+    for m, e in sorted(scaled.items()):
+        lines.append(f"  const float {m} = {e};")
+    lines += body
     lines.append("}")
     return "\n".join(lines)
 
@@ -396,7 +398,7 @@ def generate() -> str:
         "",
     ]
     for L in range(LMAX + 2):
-        out.append(emit_eval(L))
+        out.append(emit_eval_scaled(L))
     for L in range(LMAX + 1):
         out.append(emit_eval_df(L))
     for l in range(LMAX + 1):
