@@ -469,6 +469,23 @@ def test_vjp_probe_sets(torch, oracle_mod, orders, n_sig):
     atoms = synth.subset_centers(w.n_atoms, 16, seed=2)
     gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
     assert grad_errors(gp.cpu().numpy()[atoms], gref, gscale).max() <= GRAD_TOL
+    # the Jacobian rows and the strain derivative of the same probe set
+    # (one forward, refinement and derivative kernel per 16-sigma pass)
+    feat2, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    _, _, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert feature_errors(feat2.cpu().numpy(), ref, fabs).max() <= FEAT_TOL
+    joff, jj, jac = joff.cpu().numpy(), jj.cpu().numpy(), jac.cpu().numpy()
+    centers = synth.subset_centers(w.n_atoms, 16, seed=3)
+    ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+    for t, i in enumerate(centers):
+        a, b = joff[i], joff[i + 1]
+        assert np.array_equal(jj[a:b], oj[ooff[t]:ooff[t + 1]])
+        err = grad_errors(jac[a:b], ojac[ooff[t]:ooff[t + 1]], oabs[ooff[t]:ooff[t + 1]], tau=JAC_TAU)
+        assert err.max() <= GRAD_TOL, err.max()
+    W, Wa = oracle_mod.virial(w, g.astype(np.float64), want_abs=True)
+    verr = np.abs(vir.cpu().numpy() - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    assert verr.max() <= GRAD_TOL, verr.max()
 
 
 def test_jacobian_batched_clusters_and_cells(torch, oracle_mod):
