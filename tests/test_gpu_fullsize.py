@@ -158,3 +158,24 @@ def test_throughput_probes(torch):
     assert 0.3 * nominal < p["fp32_fma_tflops"] < 1.05 * nominal, p
     assert 0.3 * nominal < p["fp32_fma2_tflops"] < 2.1 * nominal, p
     assert p["ex2_tops"] > 0.0, p
+
+
+def test_sync_timeout_and_completion(torch):
+    """gmp_sync with a timeout shorter than the queued work returns
+    GMP_ERR_TIMEOUT (the work keeps running), and with a long one returns
+    once the stream is done; the features are then complete."""
+    from paper_2303_12980_gb300.binding import GMPError, GMPFeaturizer
+    w = synth.workload("random64_box")
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        f = F.featurize(pos, sp, w.atom_off, w.cells, w.pbc, stream=s)
+        a = torch.full((4096, 4096), 1e-3, device="cuda")
+        for _ in range(40):  # a few hundred ms of FP32 matrix products queued behind the call
+            a = a @ a
+    with pytest.raises(GMPError, match="TIMEOUT"):
+        F.sync(s, timeout_s=1e-4)
+    F.sync(s, timeout_s=60.0)
+    assert torch.isfinite(f).all()
