@@ -62,7 +62,8 @@ typedef enum {
   GMP_ERR_DEVICE = 6       /* a condition flagged by a kernel (see message)    */
 } gmp_status;
 
-/* Flags for gmp_params.flags. */
+/* Flags for gmp_params.flags (reserved: gmp_create rejects any other value
+ * with GMP_ERR_INVALID_ARG). */
 #define GMP_FLAG_NONE 0u
 
 /* Probe set and density tables (Examples: the GMPs dictionary). */

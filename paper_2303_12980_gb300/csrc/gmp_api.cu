@@ -715,6 +715,7 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
   if (p->n_elements < 1 || !p->n_gauss || !p->gauss_coef || !p->gauss_exp) return bad("density tables missing");
   if (p->n_orders < 1 || p->n_orders > 8 || !p->orders) return bad("orders: 1..8 entries required");
   if (!std::isfinite(p->cutoff)) return bad("cutoff must be finite");
+  if (p->flags != GMP_FLAG_NONE) return bad("unknown flags (only GMP_FLAG_NONE is defined)");
   if (!(p->cutoff > 0.0) && !(p->overlap_threshold > 0.0 && std::isfinite(p->overlap_threshold)))
     return bad("cutoff <= 0 needs overlap_threshold > 0");
   h->n_el = p->n_elements;

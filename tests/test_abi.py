@@ -46,3 +46,32 @@ def test_generated_mcsh_header_is_current():
         out = os.path.join(d, "mcsh_gen.cuh")
         subprocess.run([sys.executable, os.path.join(csrc, "gen_mcsh.py"), out], check=True)
         assert open(out).read() == open(os.path.join(csrc, "mcsh_gen.cuh")).read()
+
+
+def test_create_rejects_invalid_parameters_before_the_device():
+    """Host-side validation of gmp_params runs before any CUDA call: these
+    fail with GMP_ERR_INVALID_ARG on a machine without a GPU too."""
+    import ctypes as C
+    from paper_2303_12980_gb300 import build
+    from paper_2303_12980_gb300.binding import _Params, load_library
+    build.build()
+    L = load_library()
+    n_gauss = (C.c_int32 * 1)(1)
+    coef = (C.c_double * 1)(1.0)
+    expo = (C.c_double * 1)(1.0)
+    orders = (C.c_int32 * 2)(0, 0)
+    sig = (C.c_double * 1)(0.5)
+    def create(**kw):
+        args = dict(n_elements=1, n_gauss=C.addressof(n_gauss), gauss_coef=C.addressof(coef),
+                    gauss_exp=C.addressof(expo), n_orders=1, orders=C.addressof(orders), n_sigmas=1,
+                    sigmas=C.addressof(sig), cutoff=5.0, flags=0, overlap_threshold=1e-16)
+        args.update(kw)
+        h = C.c_void_p()
+        return L.gmp_create(C.byref(_Params(**args)), 0, C.byref(h))
+    INVALID = 1
+    assert create(flags=1) == INVALID
+    assert create(n_orders=2) == INVALID            # repeated order
+    assert create(cutoff=float("inf")) == INVALID
+    assert create(cutoff=0.0, overlap_threshold=0.0) == INVALID
+    expo[0] = -1.0
+    assert create() == INVALID                      # exponent <= 0
