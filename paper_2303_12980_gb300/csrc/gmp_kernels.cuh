@@ -825,6 +825,18 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
   }
 }
 
+// gmp_mcsh_shift_contract_order_<l> by a compile-time order.
+template <int l>
+__device__ __forceinline__ void shift_contract_order(const float* lam, const float* S1, float* V) {
+  if constexpr (l == 0) gmp_mcsh_shift_contract_order_0(lam, S1, V);
+  else if constexpr (l == 1) gmp_mcsh_shift_contract_order_1(lam, S1, V);
+  else if constexpr (l == 2) gmp_mcsh_shift_contract_order_2(lam, S1, V);
+  else if constexpr (l == 3) gmp_mcsh_shift_contract_order_3(lam, S1, V);
+  else if constexpr (l == 4) gmp_mcsh_shift_contract_order_4(lam, S1, V);
+  else if constexpr (l == 5) gmp_mcsh_shift_contract_order_5(lam, S1, V);
+  else gmp_mcsh_shift_contract_order_6(lam, S1, V);
+}
+
 // ------------------------------------------------------------------------
 // Jacobian: lane = feature (order slot, sigma); per pair
 //   d f_{l,s} / d d = 2 d dR_{l,s} P + R_{l,s} grad P,   P = sum_k lam_k S_k,
@@ -929,9 +941,18 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           }
           const float Rd = f_nb[q] * R1;  // dR_l/dr^2 = -beta R_{l+1}
           const float* lam = Lam + s * SH::NINDP;
-          float Pv = 0.0f, V[3];
-          for (int k = l * l; k < (l + 1) * (l + 1); ++k) Pv = __fmaf_rn(lam[k], S1[k], Pv);
-          gmp_mcsh_shift_contract_order(l, lam, S1, V);
+          float Pv = 0.0f, V[3] = {0.0f, 0.0f, 0.0f};
+          // per order with compile-time indices, so that S1 stays in registers
+          static_for<L + 1>([&](auto ll) {
+            constexpr int lc = decltype(ll)::value;
+            if (l == lc) {
+              float pv = 0.0f;
+#pragma unroll
+              for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam[k], S1[k], pv);
+              Pv = pv;
+              shift_contract_order<lc>(lam, S1, V);
+            }
+          });
           if (r2h > 0.0f) {
             const float inv = 1.0f / r2h;
             const float c = 2.0f * Rd * Pv + R * (float)(2 * l + 1) * Pv * inv;
