@@ -95,7 +95,7 @@ struct gmp_ctx {
   DevBuf structs, grid, atom_off, struct_of, bbox, atom_xh, atom_xl, atom_u, atom_bin, atom_rng, atom_y;
   DevBuf bin_count, bin_cursor, bin_start, bin_y, bin_je, counts, nbr_off, scan_tmp, pairs;
   DevBuf scalars;  // err word, maxm, counter
-  DevBuf grad_acc, jac_counts;
+  DevBuf grad_acc, jac_counts, jac_rows;
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
   DevBuf flagq;     // queued ill-conditioned features (center << 16 | column)
@@ -1161,8 +1161,9 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
   GMP_CK(h->jac_counts.ensure(sizeof(int64_t) * (2 * N + 1)), "jac counts");
   int64_t* cnt = h->jac_counts.as<int64_t>();
   int64_t* joff = cnt + N;
-  GMP_CK(gmp_launch_jacobian_count(N, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), cnt, st, h->sm_count,
-                                   &h->launches), "jac count");
+  GMP_CK(h->jac_rows.ensure(sizeof(int32_t) * std::max<int64_t>(h->P, 1)), "jac rows");
+  GMP_CK(gmp_launch_jacobian_count(N, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), cnt,
+                                   h->jac_rows.as<int32_t>(), st, h->sm_count, &h->launches), "jac count");
   GMP_CK(gmp_exclusive_scan_i64(cnt, joff, N, h->scan_tmp.p, st, &h->launches), "jac scan");
   GMP_CK(cudaMemcpyAsync(h->h_small, joff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read nnz");
   GMP_CK(cudaStreamSynchronize(st), "jac sync");
@@ -1209,6 +1210,7 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
     K.features = nullptr;
     K.flags = nullptr;
     K.jac_off = joff;
+    K.jac_row = h->jac_rows.as<int32_t>();
     K.jac_j = jj;
     K.jac = jd;
     GMP_CK(prof_mark(h, 2, true, st), "profile");

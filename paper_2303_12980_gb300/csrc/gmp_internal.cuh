@@ -316,8 +316,10 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      GmpPair* pairs, int64_t pair_cap, int max_keys, int32_t* d_maxm,
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches,
                                      unsigned long long* cursor = nullptr, int64_t* rng = nullptr);
+// Distinct neighbor atoms per center (counts [N]) and each pair's row
+// among them (local_row [P]); lists sorted by atom.
 cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
-                                      int64_t* counts, cudaStream_t stream, int sm_count,
+                                      int64_t* counts, int32_t* local_row, cudaStream_t stream, int sm_count,
                                       int64_t* launches);
 cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,
                                    cudaStream_t stream, int64_t* launches);

@@ -138,6 +138,7 @@ struct KParams {
   const float* grad_feat; // [N, F] (vjp)
   double* grad_acc;       // [N, 3] (vjp)
   const int64_t* jac_off; // [N+1] (jacobian)
+  const int32_t* jac_row; // [P] row of each pair within its center (jacobian)
   int32_t* jac_j;
   float* jac;             // [nnz, F, 3]
   int32_t* counter;
@@ -838,16 +839,32 @@ __device__ __forceinline__ void shift_contract_order(const float* lam, const flo
 }
 
 // ------------------------------------------------------------------------
-// Jacobian: lane = feature (order slot, sigma); per pair
+// Jacobian: lanes = (pair group, sigma), NS lanes per group and 32 / NS
+// groups per warp.  The center's rows (distinct neighbor atoms; the pairs
+// of one atom, its images, are consecutive) are split evenly among the
+// groups, and each group walks the pairs of its rows with one lane per
+// sigma, looping over the orders with compile-time contractions.  Per pair
 //   d f_{l,s} / d d = 2 d dR_{l,s} P + R_{l,s} grad P,   P = sum_k lam_k S_k,
 //   r^2 grad P = (2l+1) d P - V,  V = sum_k lam_k S_{k+e}.
-// Rows are per distinct neighbor atom (images summed, lists are sorted by
-// atom), the center's own row is minus the sum of the other rows.  The
-// moments come from the forward kernel (K.mu_out, after the double-float
-// refinement of the ill-conditioned ones).
+// The center's own row is minus the sum over the pairs of other atoms (its
+// own images do not move relative to it).  The moments come from the
+// forward kernel (K.mu_out, after the double-float refinement of the
+// ill-conditioned ones); K.jac_row holds each pair's row within its center.
+__device__ __forceinline__ int64_t first_pair_of_row(const int32_t* __restrict__ row_of, int64_t lo, int64_t hi,
+                                                    int row) {
+  while (lo < hi) {  // lower bound: row_of is non-decreasing over a center's pairs
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (row_of[mid] < row) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <int L, int NS>
 __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   using SH = Shape<L, NS>;
+  constexpr int G = 32 / NS;  // pair groups per warp
+  constexpr int NO = L + 1;   // at most L + 1 orders >= 0 per pass
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
   float* s_rad = smem;
@@ -856,134 +873,151 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   load_tables<L>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int pg = lane / NS, s = lane % NS;
+  const bool s_ok = s < P.nsig;
+  const bool dens_lane = P.want_density && s == 0;
+  const float nb = P.nbeta[s];
   float* Mu = s_warp + (size_t)wib * SH::WARP_FLOATS;
   float* Lam = Mu + SH::TILE * SH::RSTR;
-  constexpr int QF = (8 * 16 + 1 + 31) / 32;  // features per lane (<= 8 orders x 16 sigmas + density)
+  const float* lam_s = Lam + s * SH::NINDP;
   for (int64_t i = next_center(K.counter); i < K.N; i = next_center(K.counter)) {
     const int64_t p0 = K.nbr_beg[i], p1 = K.nbr_end[i];
     if (p1 > K.pair_cap) continue;  // over capacity: flagged by the fill pass
-    const int M = (int)(p1 - p0);
     const float* mrow = K.mu_out + i * (int64_t)P.nsig * SH::NIND;
     for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
     __syncwarp();
-    const int nf = P.n_ord * P.nsig;
-    // per-feature adjoints: Lam[s][k] with g = 1 for every (l, s); orders do
-    // not share components, so one array holds all of them
-    adjoints<L, NS>(P, Mu, nullptr, Lam);
-    // this lane's features
-    int f_col[QF], f_l[QF], f_s[QF];
-    float f_nb[QF];  // -beta of the feature's sigma
-    bool f_ok[QF];
-#pragma unroll
-    for (int q = 0; q < QF; ++q) {
-      const int t = lane + 32 * q;
-      f_ok[q] = t < nf || (P.want_density && t == nf);
-      if (t < nf) {
-        const int o = t / P.nsig;
-        f_s[q] = t - o * P.nsig;
-        f_l[q] = P.ord_l[o];
-        f_col[q] = P.ord_col[o] + f_s[q];
-      } else {
-        f_s[q] = 0; f_l[q] = -1; f_col[q] = P.dens_col;
-      }
-      f_nb[q] = P.nbeta[f_s[q]];
+    adjoints<L, NS>(P, Mu, nullptr, Lam);  // g = 1 per feature: lam = d f / d mu
+    const int64_t r0 = K.jac_off[i];
+    const int R = (int)(K.jac_off[i + 1] - r0);
+    // the center's own row: the rank of atom i among its neighbor atoms
+    int64_t lo = p0, hi = p1;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (K.pairs[mid].j < (int32_t)i) lo = mid + 1;
+      else hi = mid;
     }
-    float self[QF][3], acc[QF][3];
+    // (the self pair, j = i with no shift, is always in the list)
+    const int r_self = (lo < p1 && K.pairs[lo].j == (int32_t)i) ? K.jac_row[lo] : -1;
+    // this group's rows [ra, rb) and their pairs [pa, pb)
+    const int ra = (int)((int64_t)R * pg / G), rb = (int)((int64_t)R * (pg + 1) / G);
+    const int64_t pa = first_pair_of_row(K.jac_row, p0, p1, ra);
+    const int64_t pb = first_pair_of_row(K.jac_row, pa, p1, rb);
+    float acc[NO][3], self[NO][3], dacc[3] = {0.0f, 0.0f, 0.0f}, dself[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < QF; ++q)
+    for (int o = 0; o < NO; ++o)
 #pragma unroll
-      for (int v = 0; v < 3; ++v) { self[q][v] = 0.0f; acc[q][v] = 0.0f; }
-    int64_t row = K.jac_off[i] - 1;
-    int64_t self_row = -1;
-    int prev_j = -1;
-    for (int pp = 0; pp < M; ++pp) {
+      for (int v = 0; v < 3; ++v) { acc[o][v] = 0.0f; self[o][v] = 0.0f; }
+    int cur = -1;  // row being accumulated
+    auto flush = [&]() {
+      if (cur < 0 || cur == r_self) return;  // the own row is written below
+      const int64_t row = r0 + cur;
+      if (s_ok) {
+        static_for<NO>([&](auto oo) {
+          constexpr int o = decltype(oo)::value;
+          if (o < P.n_ord) {
+            float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
+            dst[0] = acc[o][0]; dst[1] = acc[o][1]; dst[2] = acc[o][2];
+          }
+        });
+      }
+      if (dens_lane) {
+        float* dst = K.jac + (row * P.F + P.dens_col) * 3;
+        dst[0] = dacc[0]; dst[1] = dacc[1]; dst[2] = dacc[2];
+      }
+    };
+    for (int64_t p = pa; p < pb; ++p) {
       float dx, dy, dz, r2h, r2l;
       int e, j;
-      load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
-      if (j != prev_j) {
-        if (prev_j >= 0) {
+      load_pair(K.pairs, p, dx, dy, dz, r2h, r2l, e, j);
+      const int row = K.jac_row[p];
+      if (row != cur) {
+        flush();
 #pragma unroll
-          for (int q = 0; q < QF; ++q)
-            if (f_ok[q]) {
-              float* dst = K.jac + (row * P.F + f_col[q]) * 3;
-              dst[0] = acc[q][0]; dst[1] = acc[q][1]; dst[2] = acc[q][2];
-              acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
-            }
-        }
-        ++row;
-        if (lane == 0) K.jac_j[row] = j;
-        if (j == i) self_row = row;
-        prev_j = j;
+        for (int o = 0; o < NO; ++o) acc[o][0] = acc[o][1] = acc[o][2] = 0.0f;
+        dacc[0] = dacc[1] = dacc[2] = 0.0f;
+        if (s == 0) K.jac_j[r0 + row] = j;
+        cur = row;
       }
-      // radial factors of this pair for every sigma (all lanes need their own)
-      float S1[SH::NIND1];
-      GmpMcsh<L + 1>::eval(dx, dy, dz, r2h, S1);
-      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
+      const bool other = j != (int32_t)i;
+      if (s_ok) {
+        float S1[SH::NIND1];
+        GmpMcsh<L + 1>::eval(dx, dy, dz, r2h, S1);
+        // radial factors of this lane's sigma, orders 0..L+1 (double-float
+        // exponent argument: a row of one neighbor averages no other terms)
+        float Rl[L + 2];
 #pragma unroll
-      for (int q = 0; q < QF; ++q) {
-        if (!f_ok[q]) continue;
-        float g[3];
-        if (f_l[q] < 0) {
-          float drho;
-          density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
-          g[0] = 2.0f * drho * dx; g[1] = 2.0f * drho * dy; g[2] = 2.0f * drho * dz;
-        } else {
-          const int l = f_l[q], s = f_s[q];
-          float R = 0.0f, R1 = 0.0f;
-          for (int qq = 0; qq < P.kmax; ++qq) {
-            // slot v of the block holds quantity v for the 4 sigmas of the group
-            const float* ent = tab_e + ((s / 4) * P.kmax + qq) * gmp_rad_block(L) * 4 + (s % 4);
-            // double-float exponent argument: a row of one neighbor has no
-            // other terms to average the 2^-24 B r^2 error of an FP32 one
-            const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
-            R = __fmaf_rn(ent[4 * (2 + l)], E, R);
-            R1 = __fmaf_rn(ent[4 * (3 + l)], E, R1);
-          }
-          const float Rd = f_nb[q] * R1;  // dR_l/dr^2 = -beta R_{l+1}
-          const float* lam = Lam + s * SH::NINDP;
-          float Pv = 0.0f, V[3] = {0.0f, 0.0f, 0.0f};
-          // per order with compile-time indices, so that S1 stays in registers
-          static_for<L + 1>([&](auto ll) {
-            constexpr int lc = decltype(ll)::value;
-            if (l == lc) {
-              float pv = 0.0f;
+        for (int l = 0; l < L + 2; ++l) Rl[l] = 0.0f;
+        const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
+        for (int q = 0; q < P.kmax; ++q) {
+          const float* ent = tab_e + ((s / 4) * P.kmax + q) * gmp_rad_block(L) * 4 + (s % 4);
+          const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
 #pragma unroll
-              for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam[k], S1[k], pv);
-              Pv = pv;
-              shift_contract_order<lc>(lam, S1, V);
-            }
-          });
-          if (r2h > 0.0f) {
-            const float inv = 1.0f / r2h;
-            const float c = 2.0f * Rd * Pv + R * (float)(2 * l + 1) * Pv * inv;
-            g[0] = dx * c - R * V[0] * inv;
-            g[1] = dy * c - R * V[1] * inv;
-            g[2] = dz * c - R * V[2] * inv;
-          } else if (l == 1) {
-            g[0] = R * lam[3]; g[1] = R * lam[1]; g[2] = R * lam[2];
-          } else {
-            g[0] = g[1] = g[2] = 0.0f;
-          }
+          for (int l = 0; l < L + 2; ++l) Rl[l] = __fmaf_rn(ent[4 * (2 + l)], E, Rl[l]);
         }
-        acc[q][0] += g[0]; acc[q][1] += g[1]; acc[q][2] += g[2];
-        if (j != i) { self[q][0] -= g[0]; self[q][1] -= g[1]; self[q][2] -= g[2]; }
+        const float inv = r2h > 0.0f ? 1.0f / r2h : 0.0f;
+        static_for<NO>([&](auto oo) {
+          constexpr int o = decltype(oo)::value;
+          if (o < P.n_ord) {
+            const int l = P.ord_l[o];
+            float g[3] = {0.0f, 0.0f, 0.0f};
+            static_for<L + 1>([&](auto ll) {
+              constexpr int lc = decltype(ll)::value;
+              if (l == lc) {
+                float pv = 0.0f, V[3];
+#pragma unroll
+                for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam_s[k], S1[k], pv);
+                shift_contract_order<lc>(lam_s, S1, V);
+                const float Rv = Rl[lc], Rd = nb * Rl[lc + 1];  // dR_l/dr^2 = -beta R_{l+1}
+                if (r2h > 0.0f) {
+                  const float c = 2.0f * Rd * pv + Rv * (float)(2 * lc + 1) * pv * inv;
+                  g[0] = dx * c - Rv * V[0] * inv;
+                  g[1] = dy * c - Rv * V[1] * inv;
+                  g[2] = dz * c - Rv * V[2] * inv;
+                } else if (lc == 1) {  // d = 0: only order 1 has a gradient
+                  g[0] = Rv * lam_s[3]; g[1] = Rv * lam_s[1]; g[2] = Rv * lam_s[2];
+                }
+              }
+            });
+            acc[o][0] += g[0]; acc[o][1] += g[1]; acc[o][2] += g[2];
+            if (other) { self[o][0] -= g[0]; self[o][1] -= g[1]; self[o][2] -= g[2]; }
+          }
+        });
+      }
+      if (dens_lane) {
+        float drho;
+        density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
+        const float g[3] = {2.0f * drho * dx, 2.0f * drho * dy, 2.0f * drho * dz};
+        dacc[0] += g[0]; dacc[1] += g[1]; dacc[2] += g[2];
+        if (other) { dself[0] -= g[0]; dself[1] -= g[1]; dself[2] -= g[2]; }
       }
     }
-    if (prev_j >= 0) {
+    flush();
+    // own row: the groups' sums of minus the other atoms' terms
 #pragma unroll
-      for (int q = 0; q < QF; ++q)
-        if (f_ok[q]) {
-          float* dst = K.jac + (row * P.F + f_col[q]) * 3;
-          dst[0] = acc[q][0]; dst[1] = acc[q][1]; dst[2] = acc[q][2];
-        }
-    }
-    if (self_row >= 0) {
+    for (int o = 0; o < NO; ++o)
 #pragma unroll
-      for (int q = 0; q < QF; ++q)
-        if (f_ok[q]) {
-          float* dst = K.jac + (self_row * P.F + f_col[q]) * 3;
-          dst[0] = self[q][0]; dst[1] = self[q][1]; dst[2] = self[q][2];
-        }
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int k = NS; k < 32; k <<= 1) self[o][v] += __shfl_xor_sync(0xffffffffu, self[o][v], k);
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int k = NS; k < 32; k <<= 1) dself[v] += __shfl_xor_sync(0xffffffffu, dself[v], k);
+    if (pg == 0 && r_self >= 0) {
+      const int64_t row = r0 + r_self;
+      if (s_ok) {
+        static_for<NO>([&](auto oo) {
+          constexpr int o = decltype(oo)::value;
+          if (o < P.n_ord) {
+            float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
+            dst[0] = self[o][0]; dst[1] = self[o][1]; dst[2] = self[o][2];
+          }
+        });
+      }
+      if (dens_lane) {
+        float* dst = K.jac + (row * P.F + P.dens_col) * 3;
+        dst[0] = dself[0]; dst[1] = dself[1]; dst[2] = dself[2];
+      }
     }
     __syncwarp();
   }

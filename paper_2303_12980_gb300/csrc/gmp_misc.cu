@@ -11,19 +11,25 @@ __global__ void k_struct_of(const int64_t* __restrict__ atom_off, int n_struct,
   }
 }
 
-// Distinct neighbor atoms per center (lists are sorted by atom).
+// Distinct neighbor atoms per center (lists are sorted by atom), and for
+// every pair the rank of its atom among them (the pair's Jacobian row
+// within the center's rows).
 __global__ void k_jac_count(int64_t N, const int64_t* __restrict__ nbr_off,
-                            const GmpPair* __restrict__ pairs, int64_t* __restrict__ counts) {
+                            const GmpPair* __restrict__ pairs, int64_t* __restrict__ counts,
+                            int32_t* __restrict__ local_row) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= N) return;
   const int64_t p0 = nbr_off[i], p1 = nbr_off[i + 1];
-  int c = 0;
-  for (int64_t p = p0 + lane; p < p1; p += 32) {
-    const int j = pairs[p].j;
-    if (p == p0 || pairs[p - 1].j != j) ++c;
+  int c = 0;  // rows so far (warp-uniform)
+  for (int64_t base = p0; base < p1; base += 32) {
+    const int64_t p = base + lane;
+    const bool in = p < p1;
+    const bool first = in && (p == p0 || pairs[p - 1].j != pairs[p].j);
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    if (in) local_row[p] = c + __popc(m & ((2u << lane) - 1u)) - 1;
+    c += __popc(m);
   }
-  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if (lane == 0) counts[i] = c;
 }
 
@@ -44,12 +50,12 @@ cudaError_t gmp_launch_struct_of(const int64_t* d_atom_off, int n_struct, int32_
 }
 
 cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
-                                      int64_t* counts, cudaStream_t stream, int sm_count,
+                                      int64_t* counts, int32_t* local_row, cudaStream_t stream, int sm_count,
                                       int64_t* launches) {
   (void)sm_count;
   if (N <= 0) return cudaSuccess;
   const int64_t threads = N * 32;
-  k_jac_count<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(N, nbr_off, pairs, counts);
+  k_jac_count<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(N, nbr_off, pairs, counts, local_row);
   ++*launches;
   return cudaGetLastError();
 }
