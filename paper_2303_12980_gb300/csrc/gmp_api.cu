@@ -504,7 +504,7 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
 // Features below this fraction of their FP32 resolution bound are recomputed
 // in double-float arithmetic (see gmp_refine.cu and the flag test in
 // write_features).
-constexpr float kFlagTau = 1e-4f;
+constexpr float kFlagTau = 3e-4f;
 
 int64_t flag_capacity(int64_t N) { return 4 * N + 1024; }
 // 64-bit count of flagged features (bytes 24..31 of the scalar block)
