@@ -596,7 +596,10 @@ gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const
   A.mu_sig0 = mt.sig0;
   A.mu_nsig = mt.nsig;
   A.mu_nind = mt.nind;
-  GMP_CK(gmp_launch_refine(A, h->sm_count, st, &h->launches), "refine");
+  unsigned order_mask = 0;
+  for (int l : h->orders)
+    if (l >= 0) order_mask |= 1u << l;
+  GMP_CK(gmp_launch_refine(A, order_mask, h->sm_count, st, &h->launches), "refine");
   return GMP_OK;
 }
 

@@ -355,7 +355,9 @@ struct GmpRefine {
   float* mu_out;
   int mu_sig0, mu_nsig, mu_nind;
 };
-cudaError_t gmp_launch_refine(const GmpRefine& args, int sm_count, cudaStream_t stream, int64_t* launches);
+// One launch per order set in order_mask (bit l: order l >= 0 requested).
+cudaError_t gmp_launch_refine(const GmpRefine& args, unsigned order_mask, int sm_count, cudaStream_t stream,
+                              int64_t* launches);
 cudaError_t gmp_launch_unpack_neighbors(int64_t P, const GmpPair* pairs, int32_t* nbr_j,
                                         int32_t* nbr_shift, cudaStream_t stream,
                                         int64_t* launches);

@@ -79,36 +79,32 @@ __device__ __forceinline__ float refine_feature(int lane, const GmpRefine& A, co
   return f.hi + f.lo;
 }
 
-// One flagged feature (center i, column col) recomputed by the whole warp;
+// One flagged feature (center i, column col) of order LO recomputed by the
+// whole warp (entries of other orders are left to that order's launch);
 // col_info[col] = (order << 16) | global sigma.
+template <int LO>
 __device__ __forceinline__ void refine_entry(int lane, const GmpRefine& A, int64_t i, int col) {
   const int info = col < A.F ? A.col_info[col] : -1;
-  if (info < 0) return;
-  const int l = info >> 16, sig = info & 0xffff;
+  if (info < 0 || (info >> 16) != LO) return;
+  const int sig = info & 0xffff;
   const GmpStruct& st = A.structs[A.center_struct[i]];
   const float4 xhi = A.center_xh[i], xli = A.center_xl[i];
   const int64_t p0 = A.nbr_beg[i], p1 = A.nbr_end[i];
   float* mu_dst = nullptr;
   if (A.mu_out && sig >= A.mu_sig0 && sig < A.mu_sig0 + A.mu_nsig)
-    mu_dst = A.mu_out + (i * A.mu_nsig + (sig - A.mu_sig0)) * (int64_t)A.mu_nind + l * l;
-  float f = 0.0f;
-  switch (l) {
-    case 0: f = refine_feature<0>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 1: f = refine_feature<1>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 2: f = refine_feature<2>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 3: f = refine_feature<3>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 4: f = refine_feature<4>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 5: f = refine_feature<5>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    case 6: f = refine_feature<6>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst); break;
-    default: return;
-  }
+    mu_dst = A.mu_out + (i * A.mu_nsig + (sig - A.mu_sig0)) * (int64_t)A.mu_nind + LO * LO;
+  const float f = refine_feature<LO>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst);
   if (lane == 0) A.features[i * A.F + col] = f;
 }
 
-// Flagged features: first the queue (entries center << 16 | column, spread
-// over the warps one entry each); when it overflowed, the rest are the set
-// bits of the bitmask (bit col % 32 of word i * FW + col / 32), which each
-// warp reads 32 words at a time (lane = word).
+// Flagged features of order LO (one launch per order, so that every warp of
+// a launch runs the same instantiation: the per-order code is large, and
+// warps mixing orders thrash the instruction cache).  First the queue
+// (entries center << 16 | column, spread over the warps one entry each);
+// when it overflowed, the rest are the set bits of the bitmask (bit
+// col % 32 of word i * FW + col / 32), which each warp reads 32 words at a
+// time (lane = word).
+template <int LO>
 __global__ void k_refine(const GmpRefine A) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -117,7 +113,7 @@ __global__ void k_refine(const GmpRefine A) {
   const int64_t nq = n < (unsigned long long)A.cap ? (int64_t)n : A.cap;
   for (int64_t t = warp; t < nq; t += nw) {
     const unsigned long long e = A.queue[t];
-    refine_entry(lane, A, (int64_t)(e >> 16), (int)(e & 0xffffu));
+    refine_entry<LO>(lane, A, (int64_t)(e >> 16), (int)(e & 0xffffu));
   }
   if (n <= (unsigned long long)A.cap) return;
   const int64_t n_words = A.n_centers * A.flag_words;
@@ -134,7 +130,7 @@ __global__ void k_refine(const GmpRefine A) {
       while (wv) {
         const int col = cbase + __ffs(wv) - 1;
         wv &= wv - 1;
-        refine_entry(lane, A, i, col);
+        refine_entry<LO>(lane, A, i, col);
       }
     }
   }
@@ -142,9 +138,17 @@ __global__ void k_refine(const GmpRefine A) {
 
 }  // namespace
 
-cudaError_t gmp_launch_refine(const GmpRefine& A, int sm_count, cudaStream_t stream, int64_t* launches) {
+cudaError_t gmp_launch_refine(const GmpRefine& A, unsigned order_mask, int sm_count, cudaStream_t stream,
+                              int64_t* launches) {
   if (A.n_centers <= 0) return cudaSuccess;
-  k_refine<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(A);
-  ++*launches;
-  return cudaGetLastError();
+  void (*const kernels[7])(GmpRefine) = {k_refine<0>, k_refine<1>, k_refine<2>, k_refine<3>,
+                                         k_refine<4>, k_refine<5>, k_refine<6>};
+  for (int l = 0; l < 7; ++l) {
+    if (!(order_mask & (1u << l))) continue;
+    kernels[l]<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(A);
+    ++*launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
