@@ -98,6 +98,7 @@ struct gmp_ctx {
   DevBuf grad_acc, jac_counts, jac_rows;
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
+  DevBuf exptab; // [64] 2^(-j/64) as double-floats (the refinement's exponential)
   DevBuf flagq;     // queued ill-conditioned features (center << 16 | column)
   DevBuf flagbits;  // the rest when the queue is full: [N][flag_words] bitmask
   DevBuf colinfo;   // per feature column: (order << 16) | sigma, -1 for the density
@@ -590,6 +591,7 @@ gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const
   A.nbr_end = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
   A.pairs = h->pairs.as<GmpPair>();
   A.ktab = h->ktab.as<float>();
+  A.exp_tab = h->exptab.as<float2>();
   A.nsig_total = (int)std::max<size_t>(h->sigmas.size(), 1);
   A.kmax = h->kmax;
   A.mu_out = mt.mu;
@@ -895,7 +897,11 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       if (h->orders[o] >= 0)
         for (int s = 0; s < (int)h->sigmas.size(); ++s) ci[col[o] + s] = (h->orders[o] << 16) | s;
     h->flag_words = (std::max(h->F, 1) + 31) / 32;
-    if (h->ktab.ensure(kt.size() * sizeof(float)) != cudaSuccess ||
+    float et[128];
+    for (int j = 0; j < 64; ++j) split(std::exp2(-j / 64.0), et + 2 * j);
+    if (h->exptab.ensure(sizeof(et)) != cudaSuccess ||
+        cudaMemcpy(h->exptab.p, et, sizeof(et), cudaMemcpyHostToDevice) != cudaSuccess ||
+        h->ktab.ensure(kt.size() * sizeof(float)) != cudaSuccess ||
         cudaMemcpy(h->ktab.p, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         h->colinfo.ensure(ci.size() * sizeof(int32_t)) != cudaSuccess ||
         cudaMemcpy(h->colinfo.p, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||

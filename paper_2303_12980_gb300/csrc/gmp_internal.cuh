@@ -145,40 +145,6 @@ __device__ __forceinline__ gmp_f2 gmp_df_add_sloppy(gmp_f2 a, gmp_f2 b) {
   return gmp_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 
-// exp(-x) for a double-float x >= 0 to about 1e-14 relative, in FP32
-// arithmetic only: x = k ln2 + r with |r| <= ln2/2 (ln2 as a double-float,
-// k ln2 formed exactly enough by two products), exp(-r) by Horner's rule on
-// its Taylor series through degree 13 (the first omitted term is below
-// 4e-18), then the exact scaling by 2^-k.  Results below the FP32 normal
-// range (x > 87) are returned as 0.
-__device__ __forceinline__ gmp_f2 gmp_df_exp_neg(gmp_f2 x) {
-  if (!(x.hi <= 87.0f)) return gmp_f2{0.0f, 0.0f};
-  // (-1)^n / n!, n = 0..13, as double-floats (hi, lo)
-  constexpr float C[14][2] = {{1.0f, 0.0f},
-                              {-1.0f, 0.0f},
-                              {0.5f, 0.0f},
-                              {-0.1666666716337204f, 4.967053879312289e-09f},
-                              {0.0416666679084301f, -1.2417634698280722e-09f},
-                              {-0.008333333767950535f, 4.34617203337595e-10f},
-                              {0.0013888889225199819f, -3.3631094437103215e-11f},
-                              {-0.00019841270113829523f, 2.725596874933456e-12f},
-                              {2.4801587642286904e-05f, -3.40699609366682e-13f},
-                              {-2.7557318844628753e-06f, -3.793571224297229e-14f},
-                              {2.755731998149713e-07f, -7.575112209051195e-15f},
-                              {-2.5052107943679403e-08f, -4.4176230446483665e-16f},
-                              {2.0876755879584152e-09f, 1.1082839147459852e-16f},
-                              {-1.6059044372074283e-10f, 5.352526511562726e-18f}};
-  const float LN2_HI = 0.6931471824645996f, LN2_LO = -1.9046542121259336e-09f;
-  const float k = rintf(__fmul_rn(x.hi, 1.4426950408889634f));
-  const gmp_f2 kl = gmp_df_add(gmp_two_prod(k, LN2_HI), gmp_two_prod(k, LN2_LO));
-  const gmp_f2 r = gmp_df_add(x, gmp_df_neg(kl));
-  gmp_f2 p{C[13][0], C[13][1]};
-#pragma unroll
-  for (int n = 12; n >= 0; --n) p = gmp_df_add_sloppy(gmp_df_mul(p, r), gmp_f2{C[n][0], C[n][1]});
-  const int ki = (int)k;
-  return gmp_f2{ldexpf(p.hi, -ki), ldexpf(p.lo, -ki)};
-}
-
 // Integer (|n| < 2^24) times double-float, exact product of the high part.
 __device__ __forceinline__ gmp_f2 gmp_df_mul_int(int n, gmp_f2 a) {
   float fn = (float)n;
@@ -350,6 +316,7 @@ struct GmpRefine {
   const int64_t* nbr_end;
   const GmpPair* pairs;
   const float* ktab;
+  const float2* exp_tab;  // [64] 2^(-j/64) as double-floats
   int nsig_total;
   int kmax;
   float* mu_out;
