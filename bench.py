@@ -141,7 +141,12 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
-        Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
+        if args.call == "grad":  # dense Jacobian (diagnostics and profiling of that kernel)
+            Fz.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+        elif args.call == "features":
+            Fz.featurize(pos, sp, w.atom_off, w.cells, w.pbc, out=feat)
+        else:
+            Fz.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(feat, gp))
 
     tuning = Fz.tune(pos, sp, w.atom_off, w.cells, w.pbc, reps=2) if not args.no_tune else None
     try:  # FP32 FMA / packed-FMA / ex2 throughput at the present clocks (before the timed region)
@@ -209,7 +214,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.call == "vjp":
         pos_h = torch.from_numpy(w.positions).pin_memory()
         sp_h = torch.from_numpy(w.species).pin_memory()
         g_h = torch.from_numpy(g_np).pin_memory()
@@ -232,15 +237,19 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "atoms": N, "structures": w.n_struct, "features": F_,
                    "orders": w.orders, "n_sigmas": len(w.sigmas), "cutoff": w.cutoff, "pairs": pairs,
-                   "step": "neighbors + features + VJP (forces), gmp_featurize_vjp",
+                   "step": {"vjp": "neighbors + features + VJP (forces), gmp_featurize_vjp",
+                            "grad": "neighbors + features + dense Jacobian, gmp_featurize_grad",
+                            "features": "neighbors + features, gmp_featurize"}[args.call],
                    "l2": "256 MB buffer written between timed steps (outside the step events)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_jacobian" if (args.call == "grad" and dom == "backward") else f"k_{dom}",
+                     "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": TRAFFIC_PER_PAIR.get(dom, 0) * pairs if dom in TRAFFIC_PER_PAIR else None,
+                     "traffic": (TRAFFIC_PER_PAIR[dom] * pairs
+                                 if dom in TRAFFIC_PER_PAIR and args.call == "vjp" else None),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
                      "kernels": kern, "ex2_per_step": wm["ex2_step"], "measured_peaks": measured,
                      "stage_ms": stage},
@@ -249,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0 and args.batched:
         out["batched"] = batched_comparison(args)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.call == "vjp":
         out["cpu_baseline"], acc = cpu_baseline(w, feat, gp, g_np, budget_s=args.cpu_budget)
         out["accuracy"] = acc
     return out
@@ -536,6 +545,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="add the 10,000-structure batched / graph / per-structure comparison")
     ap.add_argument("--ref-step-s", type=float, default=4.0)
+    ap.add_argument("--call", default="vjp", choices=["vjp", "grad", "features"],
+                    help="the timed call (default: features + VJP, the headline step)")
     ap.add_argument("--configs", action="store_true",
                     help="measure every workload of the baseline table (one JSON object) instead")
     args = ap.parse_args()
