@@ -24,6 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgmp.so")
 
 GMP_OK = 0
+GMP_ERR_CAPACITY = 4
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_vjp_virial",
@@ -160,6 +161,9 @@ class GMPFeaturizer:
         F = C.c_int32()
         self._check(self._L.gmp_num_features(self._h, C.byref(F)))
         self.num_features = int(F.value)
+        # output rows of the last featurize_grad / neighbors call: the next
+        # call allocates that many first and re-runs only when it needs more
+        self._rows = {"grad": 0, "neighbors": 0}
 
     @classmethod
     def from_workload(cls, w, device: int = 0):
@@ -283,19 +287,21 @@ class GMPFeaturizer:
         feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos)
         joff = self._alloc((N + 1,), torch.int64, on_dev, pos)
         nnz = C.c_int64()
-        st = self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
-                                            pbc.ctypes.data, _ptr(species), _ptr(feat), _ptr(joff), None, None,
-                                            0, C.byref(nnz), _stream_ptr(stream, on_dev))
-        if st not in (GMP_OK, 4):
+        cap = self._rows["grad"]
+        while True:
+            jj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
+            jac = self._alloc((max(cap, 1), self.num_features, 3), torch.float32, on_dev, pos)
+            st = self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                            pbc.ctypes.data, _ptr(species), _ptr(feat), _ptr(joff), _ptr(jj),
+                                            _ptr(jac), max(cap, 1), C.byref(nnz), _stream_ptr(stream, on_dev))
+            n = int(nnz.value)
+            if st == GMP_ERR_CAPACITY and n > max(cap, 1):
+                cap = n  # the call reported the rows it needs
+                continue
             self._check(st)
-        cap = int(nnz.value)
-        jj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
-        jac = self._alloc((max(cap, 1), self.num_features, 3), torch.float32, on_dev, pos)
-        self._check(self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos),
-                                                   cell.ctypes.data, pbc.ctypes.data, _ptr(species), _ptr(feat),
-                                                   _ptr(joff), _ptr(jj), _ptr(jac), cap, C.byref(nnz),
-                                                   _stream_ptr(stream, on_dev)))
-        return feat, joff, jj[:cap], jac[:cap]
+            break
+        self._rows["grad"] = n
+        return feat, joff, jj[:n], jac[:n]
 
     def featurize_points(self, pos, species, atom_off, cell, pbc, points, point_off, stream=None):
         """Features [n_points, F] float32 with the probes centred on reference
@@ -331,18 +337,21 @@ class GMPFeaturizer:
         N = int(off[-1])
         noff = self._alloc((N + 1,), torch.int64, on_dev, pos)
         nnz = C.c_int64()
-        st = self._L.gmp_neighbors(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
-                                   pbc.ctypes.data, _ptr(species), _ptr(noff), None, None, 0, C.byref(nnz),
-                                   _stream_ptr(stream, on_dev))
-        if st not in (GMP_OK, 4):
+        cap = self._rows["neighbors"]
+        while True:
+            nj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
+            ns = self._alloc((max(cap, 1), 3), torch.int32, on_dev, pos)
+            st = self._L.gmp_neighbors(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
+                                       pbc.ctypes.data, _ptr(species), _ptr(noff), _ptr(nj), _ptr(ns), max(cap, 1),
+                                       C.byref(nnz), _stream_ptr(stream, on_dev))
+            n = int(nnz.value)
+            if st == GMP_ERR_CAPACITY and n > max(cap, 1):
+                cap = n
+                continue
             self._check(st)
-        cap = int(nnz.value)
-        nj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
-        ns = self._alloc((max(cap, 1), 3), torch.int32, on_dev, pos)
-        self._check(self._L.gmp_neighbors(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
-                                          pbc.ctypes.data, _ptr(species), _ptr(noff), _ptr(nj), _ptr(ns), cap,
-                                          C.byref(nnz), _stream_ptr(stream, on_dev)))
-        return noff, nj[:cap], ns[:cap]
+            break
+        self._rows["neighbors"] = n
+        return noff, nj[:n], ns[:n]
 
     def profile(self, enable: bool = True):
         """Per-stage CUDA-event timing on the caller's stream (diagnostics)."""

@@ -396,9 +396,10 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
   // the error word is cleared after it is read (below), so a condition
   // raised after the read of the previous call is reported here
   GMP_CK(cudaMemsetAsync(d_maxm, 0, 4, st), "memset maxm");
-  if (single_ok && !sorted && !capture && h->last_nc == NC && h->last_gen == h->struct_gen && h->P > 0) {
+  if (single_ok && !capture && h->last_nc == NC && h->last_gen == h->struct_gen && h->P > 0) {
     // Repeated batch: one enumeration pass, each center allocating its
-    // block of records, with capacities from the last build + 12.5%.
+    // block of records, with capacities from the last build + 12.5%
+    // (blocks in allocation order: no CSR offsets, ranges in nbr_rng).
     const int64_t cap = h->P + h->P / 8 + 4096;
     int keys = 32;
     while (keys < h->max_m + h->max_m / 8 + 8) keys <<= 1;
@@ -406,7 +407,7 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
       GMP_CK(h->pairs.ensure(sizeof(GmpPair) * cap), "pairs");
       GMP_CK(h->nbr_rng.ensure(sizeof(int64_t) * 2 * NC), "nbr_rng");
       GMP_CK(cudaMemsetAsync(d_cursor, 0, 8, st), "memset cursor");
-      GMP_CK(gmp_launch_neighbor_pass(1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
+      GMP_CK(gmp_launch_neighbor_pass(sorted ? 2 : 1, h->structs.as<GmpStruct>(), h->grid.as<GmpGrid>(), C, NC, h->cutoff, pos,
                                       h->atom_xh.as<float4>(), h->atom_xl.as<float4>(), h->bin_start.as<int32_t>(),
                                       h->bin_y.as<float4>(), h->bin_je.as<int2>(), h->n_el, nullptr, nullptr,
                                       h->pairs.as<GmpPair>(), cap, keys, d_maxm, d_err, st, h->sm_count, L, d_cursor,
@@ -490,14 +491,14 @@ gmp_status neighbor_lists(gmp_ctx* h, const GmpCenters& C, int64_t NC, const dou
 // Binning + exact neighbor lists of every atom into h->pairs / h->nbr_off.
 // Synchronises `st` once (to size the pair buffer) unless capturing.
 gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32_t* species,
-                           int64_t N, cudaStream_t st, bool sorted, bool capture = false) {
+                           int64_t N, cudaStream_t st, bool sorted, bool capture = false, bool need_csr = false) {
   if (!capture) h->graph_valid = false;  // buffers may move: a captured graph is stale
   GMP_CK(prof_mark(h, 0, true, st), "profile");
   gmp_status r = bin_atoms(h, S, pos, species, N, N, st);
   if (r != GMP_OK) return r;
   const GmpCenters C{h->struct_of.as<int32_t>(), pos, h->atom_xh.as<float4>(), h->atom_xl.as<float4>(),
                      h->atom_rng.as<int4>(), h->atom_y.as<float4>()};
-  if ((r = neighbor_lists(h, C, N, pos, st, sorted, capture, true)) != GMP_OK) return r;
+  if ((r = neighbor_lists(h, C, N, pos, st, sorted, capture, !need_csr)) != GMP_OK) return r;
   GMP_CK(prof_mark(h, 0, false, st), "profile");
   return GMP_OK;
 }
@@ -1171,7 +1172,9 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
   int64_t* cnt = h->jac_counts.as<int64_t>();
   int64_t* joff = cnt + N;
   GMP_CK(h->jac_rows.ensure(sizeof(int32_t) * std::max<int64_t>(h->P, 1)), "jac rows");
-  GMP_CK(gmp_launch_jacobian_count(N, h->nbr_off.as<int64_t>(), h->pairs.as<GmpPair>(), cnt,
+  const int64_t* nbeg = h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>();
+  const int64_t* nend = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
+  GMP_CK(gmp_launch_jacobian_count(N, nbeg, nend, h->pairs.as<GmpPair>(), cnt,
                                    h->jac_rows.as<int32_t>(), st, h->sm_count, &h->launches), "jac count");
   GMP_CK(gmp_exclusive_scan_i64(cnt, joff, N, h->scan_tmp.p, st, &h->launches), "jac scan");
   GMP_CK(cudaMemcpyAsync(h->h_small, joff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read nnz");
@@ -1327,7 +1330,7 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t* atom_off
   if (!nbr_off) return fail(h, GMP_ERR_INVALID_ARG, "nbr_off is required");
   Io io;
   if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true, false, true)) != GMP_OK) return r;
   *nnz_out = h->P;
   if (h->P > cap) return fail(h, GMP_ERR_CAPACITY, "neighbor list needs " + std::to_string(h->P) + " entries");
   if (h->P > 0 && (!nbr_j || !nbr_shift)) return fail(h, GMP_ERR_INVALID_ARG, "nbr_j and nbr_shift are required");

@@ -271,7 +271,7 @@ cudaError_t gmp_launch_point_prepare(const GmpStruct* d_structs, const GmpGrid* 
 // fill: 0 = count only, 1 = records grouped by species (deterministic),
 // 2 = records sorted by (neighbor atom, image).  Centers C [N]; neighbors
 // are the binned atoms (pos, atom_xh, atom_xl).  Records go to the CSR
-// offsets (from a count pass), or, with cursor (fill 1 only), to blocks
+// offsets (from a count pass), or, with cursor (fill 1 or 2), to blocks
 // allocated from *cursor whose ranges are written to rng[i], rng[N + i].
 // Over-capacity blocks set GMP_DEV_CAPACITY.
 cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const GmpGrid* d_grid,
@@ -283,8 +283,9 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches,
                                      unsigned long long* cursor = nullptr, int64_t* rng = nullptr);
 // Distinct neighbor atoms per center (counts [N]) and each pair's row
-// among them (local_row [P]); lists sorted by atom.
-cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
+// among them (local_row [P]); center i's pairs are [nbr_beg[i], nbr_end[i]),
+// sorted by atom.
+cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_beg, const int64_t* nbr_end, const GmpPair* pairs,
                                       int64_t* counts, int32_t* local_row, cudaStream_t stream, int sm_count,
                                       int64_t* launches);
 cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,

@@ -183,6 +183,9 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
 __device__ __forceinline__ void prefetch_pair(const GmpPair* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // Radial factors of one pair for a group of 4 sigmas, orders 0..NL-1 (the
 // forward needs L+1 orders; the backward one more, for the derivative
@@ -926,6 +929,10 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
       }
     };
     for (int64_t p = pa; p < pb; ++p) {
+      // the group walks its pairs one at a time: pull the record four ahead
+      // (the next 128-byte line) and the row ranks 32 ahead into L1
+      if (p + 4 < pb) prefetch_pair(K.pairs + p + 4);
+      if (((p - pa) & 31) == 0 && p + 32 < pb) prefetch_l1(K.jac_row + p + 32);
       float dx, dy, dz, r2h, r2l;
       int e, j;
       load_pair(K.pairs, p, dx, dy, dz, r2h, r2l, e, j);

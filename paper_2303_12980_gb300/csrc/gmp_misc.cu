@@ -14,13 +14,13 @@ __global__ void k_struct_of(const int64_t* __restrict__ atom_off, int n_struct,
 // Distinct neighbor atoms per center (lists are sorted by atom), and for
 // every pair the rank of its atom among them (the pair's Jacobian row
 // within the center's rows).
-__global__ void k_jac_count(int64_t N, const int64_t* __restrict__ nbr_off,
+__global__ void k_jac_count(int64_t N, const int64_t* __restrict__ nbr_beg, const int64_t* __restrict__ nbr_end,
                             const GmpPair* __restrict__ pairs, int64_t* __restrict__ counts,
                             int32_t* __restrict__ local_row) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= N) return;
-  const int64_t p0 = nbr_off[i], p1 = nbr_off[i + 1];
+  const int64_t p0 = nbr_beg[i], p1 = nbr_end[i];
   int c = 0;  // rows so far (warp-uniform)
   for (int64_t base = p0; base < p1; base += 32) {
     const int64_t p = base + lane;
@@ -49,13 +49,13 @@ cudaError_t gmp_launch_struct_of(const int64_t* d_atom_off, int n_struct, int32_
   return cudaGetLastError();
 }
 
-cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_off, const GmpPair* pairs,
+cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_beg, const int64_t* nbr_end, const GmpPair* pairs,
                                       int64_t* counts, int32_t* local_row, cudaStream_t stream, int sm_count,
                                       int64_t* launches) {
   (void)sm_count;
   if (N <= 0) return cudaSuccess;
   const int64_t threads = N * 32;
-  k_jac_count<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(N, nbr_off, pairs, counts, local_row);
+  k_jac_count<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(N, nbr_beg, nbr_end, pairs, counts, local_row);
   ++*launches;
   return cudaGetLastError();
 }

@@ -812,7 +812,7 @@ cudaError_t gmp_launch_neighbor_pass(int fill, const GmpStruct* d_structs, const
                                      uint32_t* d_err, cudaStream_t stream, int sm_count, int64_t* launches,
                                      unsigned long long* cursor, int64_t* rng) {
   (void)sm_count;
-  if (fill < 0 || fill > 2 || (cursor && fill != 1)) return cudaErrorInvalidValue;
+  if (fill < 0 || fill > 2 || (cursor && fill == 0)) return cudaErrorInvalidValue;
   const double rc2 = cutoff * cutoff;
   const float rc2hi = (float)rc2;
   const float rc2lo = (float)(rc2 - (double)rc2hi);

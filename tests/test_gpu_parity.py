@@ -453,6 +453,28 @@ def test_repeated_calls_single_pass_neighbors(torch):
         assert torch.allclose(g1, g0, rtol=1e-6, atol=1e-6 * float(g0.abs().max())), k
 
 
+def test_repeated_jacobian_calls_single_pass_neighbors(torch):
+    """Repeated featurize_grad calls build their atom-sorted neighbor records
+    in one pass (blocks per center in allocation order) and reuse the last
+    call's row capacity; each call equals a fresh handle's first call bit for
+    bit, and the CSR neighbor lists of gmp_neighbors are unaffected."""
+    w = wl("fcc4096")
+    F = _featurizer(w)
+    pos, sp = _dev(torch, w)
+    for k, scale in enumerate([1.0, 1.0, 0.98, 0.8, 1.0]):
+        p = (pos * scale).contiguous()
+        a = F.featurize_grad(p, sp, w.atom_off, w.cells, w.pbc)
+        b = _featurizer(w).featurize_grad(p, sp, w.atom_off, w.cells, w.pbc)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert x.shape == y.shape and torch.equal(x, y), k
+        n1 = F.neighbors(p, sp, w.atom_off, w.cells, w.pbc)
+        n0 = _featurizer(w).neighbors(p, sp, w.atom_off, w.cells, w.pbc)
+        torch.cuda.synchronize()
+        for x, y in zip(n1, n0):
+            assert torch.equal(x, y), k
+
+
 @pytest.mark.parametrize("orders,n_sig", [([0, 1, 2, 3], 21), ([-1], 1), ([0], 3), ([-1, 5], 2), ([6, 1, -1], 17)])
 def test_vjp_probe_sets(torch, oracle_mod, orders, n_sig):
     """Probe sets beyond the workloads': more than 16 sigmas (several kernel
