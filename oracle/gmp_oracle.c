@@ -607,7 +607,7 @@ int oracle_jacobian_counts(const oracle_problem *P, int64_t n_centers, const int
  * jac_abs (optional) [., F]: the cancellation-free scale of each block,
  * sum over the block's pairs and components of 2 w_c A_c |d t_c / d d|
  * with A_c = sum over pairs of |t_c| (same for the center's own block,
- * summed over the other atoms' pairs); used to judge near-zero entries. */
+ * summed over the other atoms' pairs); the scale against which an entry counts as near zero. */
 int oracle_jacobian_rows(const oracle_problem *P, int64_t n_centers, const int64_t *centers,
                          const int64_t *offsets, int32_t *j_out, double *jac, double *jac_abs) {
   octx X;
