@@ -368,6 +368,15 @@ gmp_status bin_atoms(gmp_ctx* h, int32_t S, const double* pos, const int32_t* sp
   const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(N, n_centers), h->n_bins);
   GMP_CK(h->scan_tmp.ensure(gmp_scan_tmp_bytes(scan_n)), "scan_tmp");
 
+  if (gmp_bin_small_fits(N, h->n_bins, S)) {
+    GMP_CK(gmp_launch_bin_small(h->structs.as<GmpStruct>(), S, h->struct_of.as<int32_t>(), N, h->cutoff, pos, species,
+                                h->n_el, h->grid.as<GmpGrid>(), h->n_bins, h->atom_xh.as<float4>(),
+                                h->atom_xl.as<float4>(), h->atom_u.as<GmpD4>(), h->atom_bin.as<int32_t>(),
+                                h->bin_start.as<int32_t>(), h->bin_y.as<float4>(), h->bin_je.as<int2>(),
+                                h->atom_rng.as<int4>(), h->atom_y.as<float4>(), d_err, st, L),
+           "bins (one block)");
+    return GMP_OK;
+  }
   GMP_CK(gmp_launch_neighbors_prepare(h->structs.as<GmpStruct>(), S, h->struct_of.as<int32_t>(), N, h->cutoff,
                                       pos, species, h->n_el, h->grid.as<GmpGrid>(), h->atom_xh.as<float4>(),
                                       h->atom_xl.as<float4>(), h->atom_u.as<GmpD4>(), h->atom_bin.as<int32_t>(),

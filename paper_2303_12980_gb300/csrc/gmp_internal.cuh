@@ -232,6 +232,23 @@ __device__ __forceinline__ void gmp_df_disp(const float4& xhi, const float4& xli
 struct GmpWorkspace;
 
 // Launchers implemented in the .cu files (all asynchronous on `stream`).
+// Binning of a small batch (at most kSmallBinAtoms atoms, 256 structures)
+// in one launch of one CTA: the outputs of gmp_launch_neighbors_prepare +
+// gmp_launch_bins (atom_xh/xl/u/bin/rng/y, grid, pre-screen bounds,
+// bin_start/bin_y/bin_je), bit for bit.  gmp_bin_small_fits says whether
+// a batch qualifies (shared memory for its bins and slots).
+// One SM runs the batch's FP64 set-up (GB300: 1/64 of the FP32 rate), so
+// the single CTA wins only for small batches: on a GB300, 64 atoms took
+// 0.054 ms against 0.088 for the multi-kernel path, 4096 atoms 0.34 against
+// 0.17.
+constexpr int64_t kSmallBinAtoms = 1024;
+bool gmp_bin_small_fits(int64_t N, int64_t n_bins, int n_struct);
+cudaError_t gmp_launch_bin_small(GmpStruct* d_structs, int n_struct, const int32_t* d_struct_of, int64_t N,
+                                 double cutoff, const double* pos, const int32_t* species, int n_el,
+                                 GmpGrid* d_grid, int64_t n_bins, float4* atom_xh, float4* atom_xl, GmpD4* atom_u,
+                                 int32_t* atom_bin, int32_t* bin_start, float4* bin_y, int2* bin_je,
+                                 int4* atom_rng, float4* atom_y, uint32_t* d_err, cudaStream_t stream,
+                                 int64_t* launches);
 cudaError_t gmp_launch_neighbors_prepare(const GmpStruct* d_structs, int n_struct,
                                          const int32_t* d_struct_of, int64_t N, double cutoff,
                                          const double* pos, const int32_t* species, int n_el,

@@ -54,7 +54,6 @@ __device__ __forceinline__ void sort_key_image(unsigned long long key, int* n) {
   n[2] = (int)(key & 1023) - 512;
 }
 
-// Per atom: checks, fractional coordinates, wrap, double-float split, bbox.
 // Reference cell of a structure: the cell index of its first atom along
 // each periodic axis (0 when it has no atoms or that position is not
 // finite).  Atoms and reference points store their cell index relative to
@@ -92,6 +91,49 @@ __device__ inline int wrap_axis(double& u, double f0, uint32_t* err) {
   return w;
 }
 
+// Per atom: checks, fractional coordinates, wrap, double-float split, bbox.
+// bbox (6 keys per structure: min and complemented max of each
+// non-periodic fractional axis) may be global or shared memory.
+__device__ __forceinline__ void prepare_atom(const GmpStruct* S, const int32_t* __restrict__ struct_of, int64_t a,
+                                             const double* __restrict__ pos, const int32_t* __restrict__ species,
+                                             int n_el, float4* __restrict__ atom_xh, float4* __restrict__ atom_xl,
+                                             GmpD4* __restrict__ atom_u, unsigned long long* bbox,
+                                             uint32_t* __restrict__ err) {
+  const int s = struct_of[a];
+  const GmpStruct& st = S[s];
+  double x[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
+  int e = species[a];
+  if (e < 0 || e >= n_el) {
+    atomicOr(err, GMP_DEV_BAD_SPECIES);
+    e = 0;
+  }
+  if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+    atomicOr(err, GMP_DEV_NONFINITE);
+    x[0] = x[1] = x[2] = 0.0;
+  }
+  double u[3], f0[3];
+  int w[3] = {0, 0, 0};
+  struct_ref_cell(st, pos, f0);
+  for (int k = 0; k < 3; ++k) {
+    u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
+    if (st.periodic[k]) {
+      w[k] = wrap_axis(u[k], f0[k], err);
+    } else {
+      // both slots start at all-ones; the max slot stores the complemented key
+      atomicMin(&bbox[6 * s + 2 * k], order_key(u[k]));
+      atomicMin(&bbox[6 * s + 2 * k + 1], ~order_key(u[k]));
+    }
+  }
+  float h[3], l[3];
+  for (int k = 0; k < 3; ++k) {
+    h[k] = (float)x[k];
+    l[k] = (float)(x[k] - (double)h[k]);
+  }
+  atom_xh[a] = make_float4(h[0], h[1], h[2], __int_as_float(e));
+  atom_xl[a] = make_float4(l[0], l[1], l[2], __int_as_float(pack_wrap(w[0], w[1], w[2])));
+  atom_u[a] = GmpD4{u[0], u[1], u[2], 0.0};
+}
+
 __global__ void k_prepare(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
                           int64_t N, const double* __restrict__ pos,
                           const int32_t* __restrict__ species, int n_el,
@@ -99,49 +141,14 @@ __global__ void k_prepare(const GmpStruct* __restrict__ S, const int32_t* __rest
                           GmpD4* __restrict__ atom_u, unsigned long long* __restrict__ bbox,
                           uint32_t* __restrict__ err) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
-       a += (int64_t)gridDim.x * blockDim.x) {
-    const int s = struct_of[a];
-    const GmpStruct& st = S[s];
-    double x[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
-    int e = species[a];
-    if (e < 0 || e >= n_el) {
-      atomicOr(err, GMP_DEV_BAD_SPECIES);
-      e = 0;
-    }
-    if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
-      atomicOr(err, GMP_DEV_NONFINITE);
-      x[0] = x[1] = x[2] = 0.0;
-    }
-    double u[3], f0[3];
-    int w[3] = {0, 0, 0};
-    struct_ref_cell(st, pos, f0);
-    for (int k = 0; k < 3; ++k) {
-      u[k] = x[0] * st.Ainv[k] + x[1] * st.Ainv[3 + k] + x[2] * st.Ainv[6 + k];
-      if (st.periodic[k]) {
-        w[k] = wrap_axis(u[k], f0[k], err);
-      } else {
-        // both slots start at all-ones; the max slot stores the complemented key
-        atomicMin(&bbox[6 * s + 2 * k], order_key(u[k]));
-        atomicMin(&bbox[6 * s + 2 * k + 1], ~order_key(u[k]));
-      }
-    }
-    float h[3], l[3];
-    for (int k = 0; k < 3; ++k) {
-      h[k] = (float)x[k];
-      l[k] = (float)(x[k] - (double)h[k]);
-    }
-    atom_xh[a] = make_float4(h[0], h[1], h[2], __int_as_float(e));
-    atom_xl[a] = make_float4(l[0], l[1], l[2], __int_as_float(pack_wrap(w[0], w[1], w[2])));
-    atom_u[a] = GmpD4{u[0], u[1], u[2], 0.0};
-  }
+       a += (int64_t)gridDim.x * blockDim.x)
+    prepare_atom(S, struct_of, a, pos, species, n_el, atom_xh, atom_xl, atom_u, bbox, err);
 }
 
-// Per structure: bin grid and the FP32 pre-screen bound.
-__global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
-                       const unsigned long long* __restrict__ bbox, GmpGrid* __restrict__ G,
-                       double cutoff) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_struct) return;
+// Per structure: bin grid and the FP32 pre-screen bound.  bbox may be
+// global or shared memory.
+__device__ inline void grid_struct(GmpStruct* S, int s, const unsigned long long* bbox, GmpGrid* G,
+                                   double cutoff) {
   const GmpStruct& st = S[s];
   GmpGrid g;
   double umax[3], ext[3];
@@ -217,30 +224,50 @@ __global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
   S[s].inside2 = fmaxf(nextafterf(q2, 0.0f), 0.0f);
 }
 
+__global__ void k_grid(GmpStruct* __restrict__ S, int n_struct,
+                       const unsigned long long* __restrict__ bbox, GmpGrid* __restrict__ G,
+                       double cutoff) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n_struct) grid_struct(S, s, bbox, G, cutoff);
+}
+
+// Bin of an atom at wrapped fractional coordinates u4 in structure s.
+__device__ __forceinline__ int32_t bin_of(const GmpStruct* S, const GmpGrid* G, int s, const GmpD4& u4) {
+  const GmpGrid& g = G[s];
+  const double u[3] = {u4.x, u4.y, u4.z};
+  int b[3];
+  for (int k = 0; k < 3; ++k) {
+    double t = floor((u[k] - g.umin[k]) * g.inv_binw[k]);  // as center_range scales
+    t = fmin(fmax(t, 0.0), (double)(g.nb[k] - 1));
+    b[k] = (int)t;
+  }
+  return (int32_t)(S[s].bin_base + b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]));
+}
+
+// Bin slot of atom a: bin_y = (wrapped FP32 position, packed wrap of the
+// atom), bin_je = (atom index, species).
+// (wrap = atom_xl[a].w, spec = atom_xh[a].w: packed wrap and species bits)
+__device__ __forceinline__ void write_slot(const GmpStruct& st, int64_t a, int32_t slot, const GmpD4& u4,
+                                           float spec, float wrap, float4* __restrict__ bin_y,
+                                           int2* __restrict__ bin_je) {
+  float y[3];
+  for (int c = 0; c < 3; ++c) y[c] = (float)(u4.x * st.A[c] + u4.y * st.A[3 + c] + u4.z * st.A[6 + c]);
+  bin_y[slot] = make_float4(y[0], y[1], y[2], wrap);
+  bin_je[slot] = make_int2((int32_t)a, __float_as_int(spec));
+}
+
 __global__ void k_bin_assign(const GmpStruct* __restrict__ S, const GmpGrid* __restrict__ G,
                              const int32_t* __restrict__ struct_of, int64_t N,
                              const GmpD4* __restrict__ atom_u, int32_t* __restrict__ atom_bin,
                              int32_t* __restrict__ bin_count) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
        a += (int64_t)gridDim.x * blockDim.x) {
-    const int s = struct_of[a];
-    const GmpGrid& g = G[s];
-    GmpD4 u4 = atom_u[a];
-    double u[3] = {u4.x, u4.y, u4.z};
-    int b[3];
-    for (int k = 0; k < 3; ++k) {
-      double t = floor((u[k] - g.umin[k]) / g.binw[k]);
-      t = fmin(fmax(t, 0.0), (double)(g.nb[k] - 1));
-      b[k] = (int)t;
-    }
-    int64_t bin = S[s].bin_base + b[0] + (int64_t)g.nb[0] * (b[1] + (int64_t)g.nb[1] * b[2]);
-    atom_bin[a] = (int32_t)bin;
+    const int32_t bin = bin_of(S, G, struct_of[a], atom_u[a]);
+    atom_bin[a] = bin;
     atomicAdd(&bin_count[bin], 1);
   }
 }
 
-// Bin slots: bin_y = (wrapped FP32 position, packed wrap of the atom),
-// bin_je = (atom index, species).
 __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
                               int64_t N, const int32_t* __restrict__ atom_bin,
                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ bin_cursor,
@@ -249,16 +276,9 @@ __global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __
                               int2* __restrict__ bin_je) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
        a += (int64_t)gridDim.x * blockDim.x) {
-    const int s = struct_of[a];
-    const GmpStruct& st = S[s];
     const int32_t bin = atom_bin[a];
     const int32_t slot = bin_start[bin] + atomicAdd(&bin_cursor[bin], 1);
-    GmpD4 u4 = atom_u[a];
-    float y[3];
-    for (int c = 0; c < 3; ++c)
-      y[c] = (float)(u4.x * st.A[c] + u4.y * st.A[3 + c] + u4.z * st.A[6 + c]);
-    bin_y[slot] = make_float4(y[0], y[1], y[2], atom_xl[a].w);
-    bin_je[slot] = make_int2((int32_t)a, __float_as_int(atom_xh[a].w));
+    write_slot(S[struct_of[a]], a, slot, atom_u[a], atom_xh[a].w, atom_xl[a].w, bin_y, bin_je);
   }
 }
 
@@ -360,6 +380,106 @@ __global__ void k_bin_sort(int64_t n_bins, const int32_t* __restrict__ bin_start
       bin_y[u + 1] = v;
       bin_je[u + 1] = je;
     }
+  }
+}
+
+// Small batches: the whole binning (k_prepare, k_grid, k_bin_assign, the
+// scan, k_bin_scatter, k_bin_sort, k_ranges) in one CTA, the bin counts,
+// offsets and slot lists in shared memory; same outputs as those kernels
+// (bins hold their atoms in index order).  A batch of a few thousand atoms
+// spends most of its binning time in launch and tail latency, not work.
+// The pointers written here and read back by other threads are plain
+// (no __restrict__), so those reads see the writes after __syncthreads().
+__host__ __device__ inline size_t small_bin_smem(int64_t N, int64_t n_bins, int n_struct) {
+  return sizeof(unsigned long long) * 6 * (size_t)n_struct + sizeof(int32_t) * (size_t)(2 * n_bins + 1 + N);
+}
+
+__global__ void __launch_bounds__(1024) k_bin_small(GmpStruct* S, int n_struct, const int32_t* __restrict__ struct_of,
+                                                   int64_t N, double cutoff, const double* __restrict__ pos,
+                                                   const int32_t* __restrict__ species, int n_el, GmpGrid* G,
+                                                   int64_t n_bins, float4* atom_xh, float4* atom_xl, GmpD4* atom_u,
+                                                   int32_t* atom_bin, int32_t* __restrict__ bin_start,
+                                                   float4* __restrict__ bin_y, int2* __restrict__ bin_je,
+                                                   int4* __restrict__ atom_rng, float4* __restrict__ atom_y,
+                                                   uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char sm_small[];
+  __shared__ int32_t warp_tot[32];
+  unsigned long long* bbox = reinterpret_cast<unsigned long long*>(sm_small);
+  int32_t* cnt = reinterpret_cast<int32_t*>(bbox + 6 * n_struct);  // [n_bins] counts, then cursors
+  int32_t* start = cnt + n_bins;                                    // [n_bins + 1] exclusive offsets
+  int32_t* slot_atom = start + n_bins + 1;                          // [N] atom of each slot
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int t = tid; t < 6 * n_struct; t += nt) bbox[t] = ~0ull;
+  for (int64_t b = tid; b < n_bins; b += nt) cnt[b] = 0;
+  __syncthreads();
+  for (int64_t a = tid; a < N; a += nt)
+    prepare_atom(S, struct_of, a, pos, species, n_el, atom_xh, atom_xl, atom_u, bbox, err);
+  __syncthreads();
+  for (int s = tid; s < n_struct; s += nt) grid_struct(S, s, bbox, G, cutoff);
+  __syncthreads();
+  for (int64_t a = tid; a < N; a += nt) {
+    const int32_t b = bin_of(S, G, struct_of[a], atom_u[a]);
+    atom_bin[a] = b;
+    atomicAdd(&cnt[b], 1);
+  }
+  __syncthreads();
+  // exclusive scan of the counts: a contiguous chunk per thread, then the
+  // chunk totals across the block
+  const int64_t chunk = (n_bins + nt - 1) / nt;
+  const int64_t c0 = min((int64_t)tid * chunk, n_bins), c1 = min(c0 + chunk, n_bins);
+  int32_t run = 0;
+  for (int64_t b = c0; b < c1; ++b) run += cnt[b];
+  int32_t incl = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = lane < (nt >> 5) ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    warp_tot[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  int32_t off = incl - run + (wid > 0 ? warp_tot[wid - 1] : 0);
+  for (int64_t b = c0; b < c1; ++b) {
+    const int32_t c = cnt[b];
+    start[b] = off;
+    cnt[b] = off;  // cursor
+    off += c;
+  }
+  if (tid == 0) start[n_bins] = (int32_t)N;
+  __syncthreads();
+  for (int64_t a = tid; a < N; a += nt) slot_atom[atomicAdd(&cnt[atom_bin[a]], 1)] = (int32_t)a;
+  __syncthreads();
+  // each bin's atoms in index order (insertion sort; a bin holds few atoms)
+  for (int64_t b = tid; b < n_bins; b += nt) {
+    const int b0 = start[b], b1 = start[b + 1];
+    for (int t = b0 + 1; t < b1; ++t) {
+      const int32_t v = slot_atom[t];
+      int u = t - 1;
+      while (u >= b0 && slot_atom[u] > v) {
+        slot_atom[u + 1] = slot_atom[u];
+        --u;
+      }
+      slot_atom[u + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int64_t t = tid; t < N; t += nt) {
+    const int64_t a = slot_atom[t];
+    write_slot(S[struct_of[a]], a, (int32_t)t, atom_u[a], atom_xh[a].w, atom_xl[a].w, bin_y, bin_je);
+  }
+  for (int64_t b = tid; b <= n_bins; b += nt) bin_start[b] = start[b];
+  for (int64_t a = tid; a < N; a += nt) {
+    const int s = struct_of[a];
+    const GmpD4 u4 = atom_u[a];
+    const double u[3] = {u4.x, u4.y, u4.z};
+    center_range(S[s], G[s], u, atom_rng[a], atom_y[a]);
   }
 }
 
@@ -787,6 +907,29 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
   ++*launches;
   k_ranges<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, d_struct_of, N, atom_u, atom_rng,
                                                            atom_y);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+bool gmp_bin_small_fits(int64_t N, int64_t n_bins, int n_struct) {
+  return N > 0 && N <= kSmallBinAtoms && n_struct <= 256 && small_bin_smem(N, n_bins, n_struct) <= 200 * 1024;
+}
+
+cudaError_t gmp_launch_bin_small(GmpStruct* d_structs, int n_struct, const int32_t* d_struct_of, int64_t N,
+                                 double cutoff, const double* pos, const int32_t* species, int n_el,
+                                 GmpGrid* d_grid, int64_t n_bins, float4* atom_xh, float4* atom_xl, GmpD4* atom_u,
+                                 int32_t* atom_bin, int32_t* bin_start, float4* bin_y, int2* bin_je,
+                                 int4* atom_rng, float4* atom_y, uint32_t* d_err, cudaStream_t stream,
+                                 int64_t* launches) {
+  if (!gmp_bin_small_fits(N, n_bins, n_struct)) return cudaErrorInvalidValue;
+  const size_t smem = small_bin_smem(N, n_bins, n_struct);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_bin_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_bin_small<<<1, 1024, smem, stream>>>(d_structs, n_struct, d_struct_of, N, cutoff, pos, species, n_el, d_grid,
+                                         n_bins, atom_xh, atom_xl, atom_u, atom_bin, bin_start, bin_y, bin_je,
+                                         atom_rng, atom_y, d_err);
   ++*launches;
   return cudaGetLastError();
 }

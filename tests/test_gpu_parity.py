@@ -453,6 +453,29 @@ def test_repeated_calls_single_pass_neighbors(torch):
         assert torch.allclose(g1, g0, rtol=1e-6, atol=1e-6 * float(g0.abs().max())), k
 
 
+def test_small_batch_binning_matches_multi_kernel_binning(torch):
+    """A batch of at most 1024 atoms is binned by one single-CTA kernel, a
+    larger one by the multi-kernel path.  Both put each bin's atoms in index
+    order, so a 512-atom crystal's features come out bit-identical alone and
+    as each structure of a batch of three jittered copies (1536 atoms)."""
+    w = wl("fcc4096")  # its probe set and element table
+    F = _featurizer(w)
+    rng = np.random.default_rng(23)
+    pos0, cell = synth.fcc_supercell(rng, 3.6, (4, 4, 8), 0.1)
+    n = pos0.shape[0]
+    sp = rng.integers(0, 3, n).astype(np.int32)
+    P = [pos0] + [pos0 + rng.normal(0.0, 0.05, pos0.shape) for _ in range(2)]
+    off1 = np.array([0, n], np.int64)
+    pbc1 = np.ones((1, 3), np.uint8)
+    sp_d = torch.from_numpy(sp).cuda()
+    f_big = F.featurize(torch.from_numpy(np.concatenate(P)).cuda(), torch.from_numpy(np.concatenate([sp] * 3)).cuda(),
+                        np.arange(4, dtype=np.int64) * n, np.stack([cell] * 3), np.ones((3, 3), np.uint8))
+    for k, p in enumerate(P):
+        f_one = F.featurize(torch.from_numpy(p).cuda(), sp_d, off1, cell[None], pbc1)
+        torch.cuda.synchronize()
+        assert torch.equal(f_one, f_big[k * n:(k + 1) * n]), k
+
+
 def test_repeated_jacobian_calls_single_pass_neighbors(torch):
     """Repeated featurize_grad calls build their atom-sorted neighbor records
     in one pass (blocks per center in allocation order) and reuse the last
