@@ -268,17 +268,35 @@ __global__ void k_bin_assign(const GmpStruct* __restrict__ S, const GmpGrid* __r
   }
 }
 
-__global__ void k_bin_scatter(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of,
-                              int64_t N, const int32_t* __restrict__ atom_bin,
+// Slot lists in arbitrary order: slot_atom[bin_start[b] + k] = the k-th
+// atom to arrive in bin b.
+__global__ void k_bin_scatter(int64_t N, const int32_t* __restrict__ atom_bin,
                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ bin_cursor,
-                              const GmpD4* __restrict__ atom_u, const float4* __restrict__ atom_xh,
-                              const float4* __restrict__ atom_xl, float4* __restrict__ bin_y,
-                              int2* __restrict__ bin_je) {
+                              int32_t* __restrict__ slot_atom) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < N;
        a += (int64_t)gridDim.x * blockDim.x) {
     const int32_t bin = atom_bin[a];
-    const int32_t slot = bin_start[bin] + atomicAdd(&bin_cursor[bin], 1);
-    write_slot(S[struct_of[a]], a, slot, atom_u[a], atom_xh[a].w, atom_xl[a].w, bin_y, bin_je);
+    slot_atom[bin_start[bin] + atomicAdd(&bin_cursor[bin], 1)] = (int32_t)a;
+  }
+}
+
+// Per slot: the atom's rank by index within its bin gives its final slot
+// (bins in atom-index order, which makes neighbor enumeration
+// deterministic); the bin's slot list is read in parallel, not sorted in
+// place.
+__global__ void k_bin_place(const GmpStruct* __restrict__ S, const int32_t* __restrict__ struct_of, int64_t N,
+                            const int32_t* __restrict__ atom_bin, const int32_t* __restrict__ bin_start,
+                            const int32_t* __restrict__ slot_atom, const GmpD4* __restrict__ atom_u,
+                            const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
+                            float4* __restrict__ bin_y, int2* __restrict__ bin_je) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = slot_atom[t];
+    const int32_t bin = atom_bin[a];
+    const int32_t b0 = bin_start[bin], b1 = bin_start[bin + 1];
+    int32_t rank = 0;
+    for (int32_t u = b0; u < b1; ++u) rank += slot_atom[u] < a ? 1 : 0;
+    write_slot(S[struct_of[a]], a, b0 + rank, atom_u[a], atom_xh[a].w, atom_xl[a].w, bin_y, bin_je);
   }
 }
 
@@ -361,30 +379,8 @@ __global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* 
   }
 }
 
-// Orders each bin's atoms by index (the scatter above fills bins in
-// arbitrary order), which makes neighbor enumeration deterministic.
-__global__ void k_bin_sort(int64_t n_bins, const int32_t* __restrict__ bin_start, float4* __restrict__ bin_y,
-                           int2* __restrict__ bin_je) {
-  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n_bins;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    const int b0 = bin_start[b], b1 = bin_start[b + 1];
-    for (int t = b0 + 1; t < b1; ++t) {
-      const float4 v = bin_y[t];
-      const int2 je = bin_je[t];
-      int u = t - 1;
-      while (u >= b0 && bin_je[u].x > je.x) {
-        bin_y[u + 1] = bin_y[u];
-        bin_je[u + 1] = bin_je[u];
-        --u;
-      }
-      bin_y[u + 1] = v;
-      bin_je[u + 1] = je;
-    }
-  }
-}
-
 // Small batches: the whole binning (k_prepare, k_grid, k_bin_assign, the
-// scan, k_bin_scatter, k_bin_sort, k_ranges) in one CTA, the bin counts,
+// scan, k_bin_scatter, k_bin_place, k_ranges) in one CTA, the bin counts,
 // offsets and slot lists in shared memory; same outputs as those kernels
 // (bins hold their atoms in index order).  A batch of a few thousand atoms
 // spends most of its binning time in launch and tail latency, not work.
@@ -899,11 +895,11 @@ cudaError_t gmp_launch_bins(const GmpStruct* d_structs, const GmpGrid* d_grid,
   ++*launches;
   e = exclusive_scan<int32_t>(bin_count, bin_start, n_bins, scan_tmp, stream, launches);
   if (e != cudaSuccess) return e;
-  k_bin_scatter<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, atom_bin,
-                                                                bin_start, bin_cursor, atom_u, atom_xh, atom_xl,
-                                                                bin_y, bin_je);
+  // bin_count is free once scanned: it holds the slot lists (n_bins >= N)
+  k_bin_scatter<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(N, atom_bin, bin_start, bin_cursor, bin_count);
   ++*launches;
-  k_bin_sort<<<grid_for(n_bins, 256, sm_count), 256, 0, stream>>>(n_bins, bin_start, bin_y, bin_je);
+  k_bin_place<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_struct_of, N, atom_bin, bin_start,
+                                                              bin_count, atom_u, atom_xh, atom_xl, bin_y, bin_je);
   ++*launches;
   k_ranges<<<grid_for(N, 256, sm_count), 256, 0, stream>>>(d_structs, d_grid, d_struct_of, N, atom_u, atom_rng,
                                                            atom_y);
