@@ -476,6 +476,33 @@ def test_small_batch_binning_matches_multi_kernel_binning(torch):
         assert torch.equal(f_one, f_big[k * n:(k + 1) * n]), k
 
 
+def test_jacobian_capacity_contract(torch):
+    """gmp_featurize_grad through the C ABI with a row buffer that is too
+    short: status GMP_ERR_CAPACITY, *nnz_out = the rows needed, and no
+    output buffer touched; the binding's call then returns exactly that
+    many rows."""
+    import ctypes as C
+    w = wl("random64_box")
+    F = _featurizer(w)
+    pos, sp = _dev(torch, w)
+    off, cell, pbc = F._struct(w.atom_off, w.cells, w.pbc)
+    N, nf = w.n_atoms, F.num_features
+    feat = torch.full((N, nf), -7.0, device="cuda")
+    joff = torch.full((N + 1,), -5, dtype=torch.int64, device="cuda")
+    jj = torch.full((8,), -3, dtype=torch.int32, device="cuda")
+    jac = torch.full((8, nf, 3), -9.0, device="cuda")
+    nnz = C.c_int64(-1)
+    st = F._L.gmp_featurize_grad(F._h, 1, off.ctypes.data, pos.data_ptr(), cell.ctypes.data, pbc.ctypes.data,
+                                 sp.data_ptr(), feat.data_ptr(), joff.data_ptr(), jj.data_ptr(), jac.data_ptr(), 8,
+                                 C.byref(nnz), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == 4 and nnz.value > 8, (st, nnz.value)
+    assert (feat == -7.0).all() and (joff == -5).all() and (jj == -3).all() and (jac == -9.0).all()
+    f2, joff2, jj2, jac2 = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    assert int(joff2[-1]) == nnz.value == jj2.shape[0] == jac2.shape[0]
+
+
 def test_repeated_jacobian_calls_single_pass_neighbors(torch):
     """Repeated featurize_grad calls build their atom-sorted neighbor records
     in one pass (blocks per center in allocation order) and reuse the last
