@@ -154,6 +154,11 @@ def run_ours(args, rank, world, local_rank):
         measured = probe_peaks(local_rank)
     except Exception as exc:  # diagnostics only
         measured = {"error": str(exc)}
+    try:  # the moment contraction, packed FP32 (as run) against a TF32x3 tensor-core version
+        from paper_2303_12980_gb300.binding import probe_contraction
+        contraction = probe_contraction(local_rank)
+    except Exception as exc:  # diagnostics only
+        contraction = {"error": str(exc)}
 
     for _ in range(args.warmup):
         step()
@@ -252,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
                                  if dom in TRAFFIC_PER_PAIR and args.call == "vjp" else None),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
                      "kernels": kern, "ex2_per_step": wm["ex2_step"], "measured_peaks": measured,
-                     "stage_ms": stage},
+                     "contraction_probe": contraction, "stage_ms": stage},
         "wall_s_timed": wall,
         "tuning": tuning,
     }

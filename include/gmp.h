@@ -275,6 +275,26 @@ void gmp_destroy(gmp_handle h);
  * resident thread.  Needs no handle; GMP_ERR_CUDA if a launch fails. */
 gmp_status gmp_probe_peaks(int device, double *fma_tflops, double *fma2_tflops, double *ex2_tops);
 
+/* Measured evaluation of a tensor-core recast of the moment contraction
+ * (the per-center sum over pairs of R_{l,sigma} S_c, section Overview's
+ * multipole moments; diagnostics, about 100 ms): the same 16-sigma x
+ * 64-slot contraction over 16-pair shared-memory tiles (orders 0..6) run
+ * (a) as the forward kernel runs it, packed FP32-pair FMAs with a TwoSum
+ * fold per tile, and (b) on the tensor cores, mma.sync m16n8k8 with TF32
+ * operands split hi + lo and three products per tile (hi*hi, hi*lo,
+ * lo*hi), FP32 accumulators folded by TwoSum per tile.  result[n_result],
+ * n_result >= GMP_PROBE_CONTRACT_N, host array, four versions v =
+ * FP32 (16 warps per SM), TF32x3 (16 warps per SM, 128 registers),
+ * TF32x3 (8 warps per SM, up to 255 registers), TF32x3 on tiles stored
+ * already split (16 warps per SM):
+ *   [v]      10^9 pairs/s
+ *   [4 + v]  largest error of a 144-pair sum relative to its
+ *            cancellation-free scale (sum of |R S|), against FP64
+ *   [8 + v]  registers per thread
+ * Needs no handle; GMP_ERR_CUDA if a launch fails. */
+#define GMP_PROBE_CONTRACT_N 12
+gmp_status gmp_probe_contraction(int device, double *result, int32_t n_result);
+
 #ifdef __cplusplus
 }
 #endif

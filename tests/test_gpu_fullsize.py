@@ -160,6 +160,19 @@ def test_throughput_probes(torch):
     assert p["ex2_tops"] > 0.0, p
 
 
+def test_contraction_probe(torch):
+    """The moment-contraction probe: the forward kernel's packed-FP32 scheme
+    and the TF32x3 tensor-core version sum 144 pairs to within their
+    rounding of the cancellation-free scale, and both report a rate."""
+    from paper_2303_12980_gb300.binding import probe_contraction
+    r = probe_contraction(0)
+    assert r["fp32"]["max_rel_err"] < 2e-6, r
+    for k in ("tf32x3_16w", "tf32x3_8w", "tf32x3_presplit_16w"):
+        assert r[k]["max_rel_err"] < 1e-5, r
+    for v in r.values():
+        assert v["gpairs_per_s"] > 0.0 and v["registers"] > 0, r
+
+
 def test_sync_timeout_and_completion(torch):
     """gmp_sync with a timeout shorter than the queued work returns
     GMP_ERR_TIMEOUT (the work keeps running), and with a long one returns
