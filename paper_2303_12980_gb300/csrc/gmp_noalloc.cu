@@ -1,7 +1,9 @@
 // Allocation-free neighbor counting for one structure.
 //
 // gmp_neighbor_counts_noalloc runs the same binning and exact neighbor-count
-// kernels as gmp_neighbors, but every scratch buffer they need (per-atom
+// kernels as gmp_neighbors (always the multi-kernel binning, whose bins equal
+// those of the single-CTA binning gmp_neighbors uses for small batches), but
+// every scratch buffer they need (per-atom
 // fractional coordinates, the bin grid, bin counts and offsets, the scan
 // workspace, the error word) lives in one file-scope device array of fixed
 // size instead of memory obtained from cudaMalloc.  It exists for callers
