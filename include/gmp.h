@@ -191,8 +191,8 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t *atom_off
  * memory-pool callbacks, loops that cannot afford cudaMalloc's implicit
  * device-wide synchronisation, processes that reserve all device memory up
  * front.  It runs the same binning (the multi-kernel path) and exact count
- * kernels as gmp_neighbors
- * and needs no handle: all scratch lives in a fixed static device array
+ * kernels as gmp_neighbors and needs no handle: all scratch lives in a
+ * fixed static device array
  * (about 5 MB, held by every GPU that loads the library until the process
  * exits), sized for at most 32768 atoms; larger n_atoms returns
  * GMP_ERR_CAPACITY with a message on stderr before any GPU work.
