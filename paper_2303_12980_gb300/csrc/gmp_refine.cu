@@ -172,7 +172,14 @@ cudaError_t gmp_launch_refine(const GmpRefine& A, unsigned order_mask, int sm_co
                                          k_refine<4>, k_refine<5>, k_refine<6>};
   for (int l = 0; l < 7; ++l) {
     if (!(order_mask & (1u << l))) continue;
-    kernels[l]<<<(unsigned)(sm_count * 4), 256, 0, stream>>>(A);
+    // as many CTAs as can be resident: the warps take fixed strides of the
+    // flagged entries, so a second partial wave would leave most of each
+    // SM idle while it runs
+    int per_sm = 0;
+    const cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernels[l], 256, 0);
+    if (eo != cudaSuccess) return eo;
+    if (per_sm < 1) per_sm = 1;
+    kernels[l]<<<(unsigned)(sm_count * per_sm), 256, 0, stream>>>(A);
     ++*launches;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
