@@ -39,6 +39,18 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+// floor(a / b) for |a| < 2^20 and 1 <= b <= 1024 without an integer
+// division: the single-precision quotient (approximate reciprocal, error
+// well below 2^-20 relative) is within one of the true one, and the
+// remainder test corrects it.
+__device__ __forceinline__ int floor_div_small(int a, int b) {
+  int q = __float2int_rd(__fmul_rn(__int2float_rn(a), __fdividef(1.0f, __int2float_rn(b))));
+  const int r = a - q * b;
+  if (r < 0) --q;
+  else if (r >= b) ++q;
+  return q;
+}
+
 __device__ __forceinline__ int32_t pack_wrap(int w0, int w1, int w2) {
   return gmp_pack_shift(w0, w1, w2);
 }
@@ -628,15 +640,26 @@ __global__ void __launch_bounds__(128, 6) k_neighbors(const GmpStruct* __restric
     int b0 = 0, b1 = 0;
     float sh[3] = {0.0f, 0.0f, 0.0f};
     if (cidx < total) {
-      const int c0 = cidx % span[0];
-      const int c1 = (cidx / span[0]) % span[1];
-      const int c2 = cidx / (span[0] * span[1]);
+      // cell (c0, c1, c2) of the box and its bin; all operands are below
+      // 2^20 in magnitude unless the box is huge (then integer division)
+      int c0, c1, c2;
+      const bool small = total < (1 << 20);
+      if (small) {
+        const int t01 = floor_div_small(cidx, span[0]);
+        c0 = cidx - t01 * span[0];
+        c2 = floor_div_small(t01, span[1]);
+        c1 = t01 - c2 * span[1];
+      } else {
+        c0 = cidx % span[0];
+        c1 = (cidx / span[0]) % span[1];
+        c2 = cidx / (span[0] * span[1]);
+      }
       const int bb[3] = {lo[0] + c0, lo[1] + c1, lo[2] + c2};
       int bw[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         if (per[k]) {
-          m[k] = floor_div(bb[k], nb[k]);
+          m[k] = small ? floor_div_small(bb[k], nb[k]) : floor_div(bb[k], nb[k]);
           bw[k] = bb[k] - m[k] * nb[k];
         } else {
           bw[k] = bb[k];
