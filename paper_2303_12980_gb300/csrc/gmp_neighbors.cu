@@ -641,7 +641,9 @@ __global__ void __launch_bounds__(128, 6) k_neighbors(const GmpStruct* __restric
     float sh[3] = {0.0f, 0.0f, 0.0f};
     if (cidx < total) {
       // cell (c0, c1, c2) of the box and its bin; all operands are below
-      // 2^20 in magnitude unless the box is huge (then integer division)
+      // 2^20 in magnitude unless the box is huge (then integer division:
+      // a cutoff of over 50 cell widths along periodic axes reaches it, and
+      // its image count then exceeds the per-center limit)
       int c0, c1, c2;
       const bool small = total < (1 << 20);
       if (small) {

@@ -147,6 +147,28 @@ def test_neighbor_image_limit(torch):
     assert torch.isfinite(ok).all()
 
 
+def test_huge_search_box(torch):
+    """A search box of more than 2^20 cells (one atom in a 1 A periodic cube,
+    cutoff 52 A: 105^3 image cells) takes the enumeration's integer-division
+    path; its ~590,000 images per center end in the capacity error, and the
+    handle's next call succeeds."""
+    from paper_2303_12980_gb300.binding import GMPError, GMPFeaturizer
+    w = synth.workload("random64_box")
+    tiny = w.replace(positions=np.array([[0.3, 0.4, 0.5]]), species=np.array([0], np.int32),
+                     atom_off=np.array([0, 1], np.int64), cells=np.eye(3)[None].copy(),
+                     pbc=np.ones((1, 3), np.uint8), cutoff=52.0, orders=[0], sigmas=[0.5])
+    F = GMPFeaturizer.from_workload(tiny)
+    with pytest.raises(GMPError, match="neighbor images"):
+        F.featurize(torch.from_numpy(tiny.positions).cuda(), torch.from_numpy(tiny.species).cuda(),
+                    tiny.atom_off, tiny.cells, tiny.pbc)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    ok = GMPFeaturizer.from_workload(w.replace(orders=[0], sigmas=[0.5])).featurize(pos, sp, w.atom_off,
+                                                                                   w.cells, w.pbc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ok).all()
+
+
 def test_throughput_probes(torch):
     """The FP32 FMA probes land near the nominal rate (SMs x 128 lanes x 2
     FLOP x clock, at most the maximum clock) and the ex2 probe reports a
