@@ -394,8 +394,9 @@ __global__ void k_point_prepare(const GmpStruct* __restrict__ S, const GmpGrid* 
 // Small batches: the whole binning (k_prepare, k_grid, k_bin_assign, the
 // scan, k_bin_scatter, k_bin_place, k_ranges) in one CTA, the bin counts,
 // offsets and slot lists in shared memory; same outputs as those kernels
-// (bins hold their atoms in index order).  A batch of a few thousand atoms
-// spends most of its binning time in launch and tail latency, not work.
+// (bins hold their atoms in index order).  A batch of up to about a
+// thousand atoms spends most of its multi-kernel binning time in launch and
+// tail latency, not work; past that the one SM's FP64 set-up dominates.
 // The pointers written here and read back by other threads are plain
 // (no __restrict__), so those reads see the writes after __syncthreads().
 __host__ __device__ inline size_t small_bin_smem(int64_t N, int64_t n_bins, int n_struct) {
