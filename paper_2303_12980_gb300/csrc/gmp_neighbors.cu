@@ -687,7 +687,8 @@ __global__ void __launch_bounds__(128, 6) k_neighbors(const GmpStruct* __restric
         const float dx = (yj.x - yi[0]) + sh[0];
         const float dy = (yj.y - yi[1]) + sh[1];
         const float dz = (yj.z - yi[2]) + sh[2];
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        // three roundings of non-negative terms: within 3 x 2^-24 relative
+        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
         if (r2 <= p2) {
           int wj[3];
           gmp_unpack_shift(__float_as_int(yj.w), wj);
