@@ -155,6 +155,21 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t *ato
                                   int32_t *jac_j, float *jac, int64_t cap, int64_t *nnz_out,
                                   void *stream);
 
+/* The same for the centers center_begin .. center_end-1 of the batch only
+ * (0 <= begin <= end <= N, else GMP_ERR_INVALID_ARG): a Jacobian too large
+ * for memory at once (262,144 slab atoms: ~37 M rows, ~50 GB) is taken in
+ * center chunks, each with its own capacity.  Rows and values equal those
+ * of gmp_featurize_grad for these centers; outputs are relative to the
+ * range:
+ *   features [end-begin, F] (optional, may be null), jac_off [end-begin+1]
+ *   (jac_off[0] = 0), jac_j [cap], jac [cap, F, 3].
+ * The neighbor lists are built for the whole batch on every call. */
+gmp_status gmp_featurize_grad_centers(gmp_handle h, int32_t n_struct, const int64_t *atom_off,
+                                      const double *pos, const double *cell, const uint8_t *pbc,
+                                      const int32_t *species, int64_t center_begin, int64_t center_end,
+                                      float *features, int64_t *jac_off, int32_t *jac_j, float *jac,
+                                      int64_t cap, int64_t *nnz_out, void *stream);
+
 /* Features at reference points (the paper's Overview section: features are
  * defined around arbitrary points of a structure, not only around its
  * atoms).  The probes are centred on each point; the neighbor set is every

@@ -28,7 +28,7 @@ GMP_ERR_CAPACITY = 4
 _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GMP_ERR_CAPACITY",
            5: "GMP_ERR_TIMEOUT", 6: "GMP_ERR_DEVICE"}
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_vjp_virial",
-           "gmp_featurize_grad", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
+           "gmp_featurize_grad", "gmp_featurize_grad_centers", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
            "gmp_sync", "gmp_profile", "gmp_profile_read",
            "gmp_probe_peaks", "gmp_probe_contraction", "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
 TUNING_CACHE = os.environ.get("GMP_TUNING_CACHE",
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         L.gmp_featurize_vjp.argtypes = common + [vp, vp, vp, vp]
         L.gmp_featurize_vjp_virial.argtypes = common + [vp, vp, vp, vp, vp]
         L.gmp_featurize_grad.argtypes = common + [vp, vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.gmp_featurize_grad_centers.argtypes = common + [i64, i64, vp, vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_neighbors.argtypes = common + [vp, vp, vp, i64, C.POINTER(i64), vp]
         L.gmp_featurize_points.argtypes = common + [vp, vp, vp, vp]
         L.gmp_set_graph.argtypes = [vp, C.c_int]
@@ -278,23 +279,33 @@ class GMPFeaturizer:
                                                      _stream_ptr(stream, on_dev)))
         return feat, gp, vir
 
-    def featurize_grad(self, pos, species, atom_off, cell, pbc, stream=None):
+    def featurize_grad(self, pos, species, atom_off, cell, pbc, stream=None, centers=None):
         """(features [N,F], jac_off [N+1] int64, jac_j [nnz] int32, jac [nnz,F,3] float32):
-        jac[r] = d features[i] / d pos[jac_j[r]] for r in jac_off[i]:jac_off[i+1]."""
+        jac[r] = d features[i] / d pos[jac_j[r]] for r in jac_off[i]:jac_off[i+1].
+        centers=(begin, end): only those centers (gmp_featurize_grad_centers);
+        features, jac_off and rows are then relative to the range."""
         torch = _torch()
         off, cell, pbc = self._struct(atom_off, cell, pbc)
         pos, species, on_dev = self._inputs(pos, species)
         N = int(off[-1])
-        feat = self._alloc((N, self.num_features), torch.float32, on_dev, pos)
-        joff = self._alloc((N + 1,), torch.int64, on_dev, pos)
+        b, e = (0, N) if centers is None else (int(centers[0]), int(centers[1]))
+        if not 0 <= b <= e <= N:
+            raise ValueError("centers must satisfy 0 <= begin <= end <= number of atoms")
+        feat = self._alloc((e - b, self.num_features), torch.float32, on_dev, pos)
+        joff = self._alloc((e - b + 1,), torch.int64, on_dev, pos)
         nnz = C.c_int64()
         cap = self._rows["grad"]
         while True:
             jj = self._alloc((max(cap, 1),), torch.int32, on_dev, pos)
             jac = self._alloc((max(cap, 1), self.num_features, 3), torch.float32, on_dev, pos)
-            st = self._L.gmp_featurize_grad(self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data,
-                                            pbc.ctypes.data, _ptr(species), _ptr(feat), _ptr(joff), _ptr(jj),
-                                            _ptr(jac), max(cap, 1), C.byref(nnz), _stream_ptr(stream, on_dev))
+            head = (self._h, off.size - 1, off.ctypes.data, _ptr(pos), cell.ctypes.data, pbc.ctypes.data,
+                    _ptr(species))
+            tail = (_ptr(feat), _ptr(joff), _ptr(jj), _ptr(jac), max(cap, 1), C.byref(nnz),
+                    _stream_ptr(stream, on_dev))
+            if centers is None:
+                st = self._L.gmp_featurize_grad(*head, *tail)
+            else:
+                st = self._L.gmp_featurize_grad_centers(*head, b, e, *tail)
             n = int(nnz.value)
             if st == GMP_ERR_CAPACITY and n > max(cap, 1):
                 cap = n  # the call reported the rows it needs

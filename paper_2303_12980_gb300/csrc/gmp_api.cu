@@ -713,6 +713,101 @@ gmp_status capture_graph(gmp_ctx* h, const std::vector<uintptr_t>& key, cudaStre
   return GMP_OK;
 }
 
+// Features and Jacobian rows of centers c0 .. c1-1 (all of them for
+// gmp_featurize_grad).  The neighbor lists and the work buffers cover the
+// whole batch; the compute kernels run over the range only.
+gmp_status grad_impl(gmp_ctx* h, int32_t n_struct, const int64_t* atom_off, const double* pos, const double* cell,
+                     const uint8_t* pbc, const int32_t* species, int64_t c0, int64_t c1, bool ranged,
+                     float* features, int64_t* jac_off, int32_t* jac_j, float* jac, int64_t cap, int64_t* nnz_out,
+                     cudaStream_t st) {
+  int64_t N = 0;
+  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
+  if (r != GMP_OK) return r;
+  if (!nnz_out) return fail(h, GMP_ERR_INVALID_ARG, "nnz_out is required");
+  *nnz_out = 0;
+  if (!ranged) c1 = N;
+  if (c0 < 0 || c1 < c0 || c1 > N) return fail(h, GMP_ERR_INVALID_ARG, "center range must satisfy 0 <= begin <= end <= N");
+  if (N == 0) return GMP_OK;
+  if (!jac_off) return fail(h, GMP_ERR_INVALID_ARG, "jac_off is required");
+  const int64_t n = c1 - c0;
+  const bool whole = c0 == 0 && c1 == N;
+  Io io;
+  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
+  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true)) != GMP_OK) return r;
+  GMP_CK(h->jac_counts.ensure(sizeof(int64_t) * (2 * n + 1)), "jac counts");
+  int64_t* cnt = h->jac_counts.as<int64_t>();
+  int64_t* joff = cnt + n;
+  GMP_CK(h->jac_rows.ensure(sizeof(int32_t) * std::max<int64_t>(h->P, 1)), "jac rows");
+  const int64_t* nbeg = h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>();
+  const int64_t* nend = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
+  GMP_CK(gmp_launch_jacobian_count(n, nbeg + c0, nend + c0, h->pairs.as<GmpPair>(), cnt,
+                                   h->jac_rows.as<int32_t>(), st, h->sm_count, &h->launches), "jac count");
+  GMP_CK(gmp_exclusive_scan_i64(cnt, joff, n, h->scan_tmp.p, st, &h->launches), "jac scan");
+  GMP_CK(cudaMemcpyAsync(h->h_small, joff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read nnz");
+  GMP_CK(cudaStreamSynchronize(st), "jac sync");
+  const int64_t nnz = h->h_small[0];
+  *nnz_out = nnz;
+  if (nnz > cap) return fail(h, GMP_ERR_CAPACITY, "jacobian needs " + std::to_string(nnz) + " rows, cap is " + std::to_string(cap));
+  if (nnz > 0 && (!jac_j || !jac)) return fail(h, GMP_ERR_INVALID_ARG, "jac_j and jac are required");
+  // features: straight into a device output of the whole batch, else into
+  // the [N, F] scratch and the range's rows copied out at the end
+  float* jd = jac;
+  int32_t* jj = jac_j;
+  DevBuf tmp_jac, tmp_jj;
+  if (io.host && nnz > 0) {
+    GMP_CK(tmp_jac.ensure(sizeof(float) * nnz * h->F * 3), "stage jac");
+    GMP_CK(tmp_jj.ensure(sizeof(int32_t) * nnz), "stage jac_j");
+    jd = tmp_jac.as<float>();
+    jj = tmp_jj.as<int32_t>();
+  }
+  for (const PassData& pd : h->passes)
+    GMP_CK(h->mu.ensure(sizeof(float) * (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1)), "moments");
+  float* fout = (whole && features && !io.host) ? features : nullptr;
+  if (!fout) {
+    GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
+    fout = h->stage_feat.as<float>();
+  }
+  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
+  for (size_t g = 0; g < h->passes.size(); ++g) {
+    // forward kernel (features, moments), refinement of the flagged
+    // features and their moments, then the Jacobian rows from the moments
+    const PassData& pd = h->passes[g];
+    gmpk::KParams K = base_params(h, pd, (int)g, N);
+    K.N = c1;
+    K.center0 = c0;
+    K.features = fout;
+    K.mu_out = h->mu.as<float>();
+    GMP_CK(prof_mark(h, 1, true, st), "profile");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
+    GMP_CK(prof_mark(h, 1, false, st), "profile");
+    GMP_CK(prof_mark(h, 3, true, st), "profile");
+    if ((r = refine(h, N, fout, st, nullptr, nullptr, nullptr, pass_moments(h, pd, (int)g))) != GMP_OK) return r;
+    if ((r = reset_flags(h, N, st)) != GMP_OK) return r;
+    GMP_CK(prof_mark(h, 3, false, st), "profile");
+    K.features = nullptr;
+    K.flags = nullptr;
+    K.jac_off = joff;
+    K.jac_row = h->jac_rows.as<int32_t>();
+    K.jac_j = jj;
+    K.jac = jd;
+    GMP_CK(prof_mark(h, 2, true, st), "profile");
+    GMP_CK(launch_compute(pd.L, GMP_KIND_JACOBIAN, pd.NS, K, pd.jac, st, h->sm_count, &h->launches), "jacobian");
+    GMP_CK(prof_mark(h, 2, false, st), "profile");
+  }
+  const cudaMemcpyKind k_out = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (n + 1), k_out, st), "copy jac_off");
+  if (features && fout != features)
+    GMP_CK(cudaMemcpyAsync(features, fout + c0 * h->F, sizeof(float) * n * h->F, k_out, st), "copy features");
+  if (io.host) {
+    if (nnz > 0) {
+      GMP_CK(cudaMemcpyAsync(jac, jd, sizeof(float) * nnz * h->F * 3, cudaMemcpyDeviceToHost, st), "d2h jac");
+      GMP_CK(cudaMemcpyAsync(jac_j, jj, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st), "d2h jac_j");
+    }
+    GMP_CK(cudaStreamSynchronize(st), "sync");
+  }
+  return GMP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1166,89 +1261,16 @@ gmp_status gmp_featurize_grad(gmp_handle h, int32_t n_struct, const int64_t* ato
                                   const double* cell, const uint8_t* pbc, const int32_t* species, float* features,
                                   int64_t* jac_off, int32_t* jac_j, float* jac, int64_t cap, int64_t* nnz_out,
                                   void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  int64_t N = 0;
-  gmp_status r = common_checks(h, n_struct, atom_off, pos, cell, pbc, species, st, N);
-  if (r != GMP_OK) return r;
-  if (!nnz_out) return fail(h, GMP_ERR_INVALID_ARG, "nnz_out is required");
-  *nnz_out = 0;
-  if (N == 0) return GMP_OK;
-  if (!jac_off) return fail(h, GMP_ERR_INVALID_ARG, "jac_off is required");
-  Io io;
-  if ((r = stage_inputs(h, N, pos, species, io, st)) != GMP_OK) return r;
-  if ((r = build_neighbors(h, n_struct, io.pos, io.species, N, st, true)) != GMP_OK) return r;
-  GMP_CK(h->jac_counts.ensure(sizeof(int64_t) * (2 * N + 1)), "jac counts");
-  int64_t* cnt = h->jac_counts.as<int64_t>();
-  int64_t* joff = cnt + N;
-  GMP_CK(h->jac_rows.ensure(sizeof(int32_t) * std::max<int64_t>(h->P, 1)), "jac rows");
-  const int64_t* nbeg = h->rng_mode ? h->nbr_rng.as<int64_t>() : h->nbr_off.as<int64_t>();
-  const int64_t* nend = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
-  GMP_CK(gmp_launch_jacobian_count(N, nbeg, nend, h->pairs.as<GmpPair>(), cnt,
-                                   h->jac_rows.as<int32_t>(), st, h->sm_count, &h->launches), "jac count");
-  GMP_CK(gmp_exclusive_scan_i64(cnt, joff, N, h->scan_tmp.p, st, &h->launches), "jac scan");
-  GMP_CK(cudaMemcpyAsync(h->h_small, joff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read nnz");
-  GMP_CK(cudaStreamSynchronize(st), "jac sync");
-  const int64_t nnz = h->h_small[0];
-  *nnz_out = nnz;
-  if (nnz > cap) return fail(h, GMP_ERR_CAPACITY, "jacobian needs " + std::to_string(nnz) + " rows, cap is " + std::to_string(cap));
-  if (!jac_j || !jac) return fail(h, GMP_ERR_INVALID_ARG, "jac_j and jac are required");
-  float* feat = features;
-  float* jd = jac;
-  int32_t* jj = jac_j;
-  DevBuf tmp_feat, tmp_jac, tmp_jj;
-  if (io.host) {
-    if (features) {
-      GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "stage features");
-      feat = h->stage_feat.as<float>();
-    }
-    GMP_CK(tmp_jac.ensure(sizeof(float) * nnz * h->F * 3), "stage jac");
-    GMP_CK(tmp_jj.ensure(sizeof(int32_t) * nnz), "stage jac_j");
-    jd = tmp_jac.as<float>();
-    jj = tmp_jj.as<int32_t>();
-  }
-  for (const PassData& pd : h->passes)
-    GMP_CK(h->mu.ensure(sizeof(float) * (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1)), "moments");
-  float* fout = feat;
-  if (!fout) {
-    GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
-    fout = h->stage_feat.as<float>();
-  }
-  if ((r = begin_compute(h, N, st)) != GMP_OK) return r;
-  for (size_t g = 0; g < h->passes.size(); ++g) {
-    // forward kernel (features, moments), refinement of the flagged
-    // features and their moments, then the Jacobian rows from the moments
-    const PassData& pd = h->passes[g];
-    gmpk::KParams K = base_params(h, pd, (int)g, N);
-    K.features = fout;
-    K.mu_out = h->mu.as<float>();
-    GMP_CK(prof_mark(h, 1, true, st), "profile");
-    GMP_CK(launch_compute(pd.L, GMP_KIND_FORWARD, pd.NS, K, pd.fwd, st, h->sm_count, &h->launches), "forward");
-    GMP_CK(prof_mark(h, 1, false, st), "profile");
-    GMP_CK(prof_mark(h, 3, true, st), "profile");
-    if ((r = refine(h, N, fout, st, nullptr, nullptr, nullptr, pass_moments(h, pd, (int)g))) != GMP_OK) return r;
-    if ((r = reset_flags(h, N, st)) != GMP_OK) return r;
-    GMP_CK(prof_mark(h, 3, false, st), "profile");
-    K.features = nullptr;
-    K.flags = nullptr;
-    K.jac_off = joff;
-    K.jac_row = h->jac_rows.as<int32_t>();
-    K.jac_j = jj;
-    K.jac = jd;
-    GMP_CK(prof_mark(h, 2, true, st), "profile");
-    GMP_CK(launch_compute(pd.L, GMP_KIND_JACOBIAN, pd.NS, K, pd.jac, st, h->sm_count, &h->launches), "jacobian");
-    GMP_CK(prof_mark(h, 2, false, st), "profile");
-  }
-  const cudaMemcpyKind k_off = io.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  GMP_CK(cudaMemcpyAsync(jac_off, joff, sizeof(int64_t) * (N + 1), k_off, st), "copy jac_off");
-  if (io.host) {
-    if (features) GMP_CK(cudaMemcpyAsync(features, feat, sizeof(float) * N * h->F, cudaMemcpyDeviceToHost, st), "d2h features");
-    GMP_CK(cudaMemcpyAsync(jac, jd, sizeof(float) * nnz * h->F * 3, cudaMemcpyDeviceToHost, st), "d2h jac");
-    GMP_CK(cudaMemcpyAsync(jac_j, jj, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st), "d2h jac_j");
-    GMP_CK(cudaStreamSynchronize(st), "sync");
-    tmp_jac.release();
-    tmp_jj.release();
-  }
-  return GMP_OK;
+  return grad_impl(h, n_struct, atom_off, pos, cell, pbc, species, 0, 0, false, features, jac_off, jac_j, jac, cap,
+                   nnz_out, (cudaStream_t)stream);
+}
+
+gmp_status gmp_featurize_grad_centers(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,
+                                      const double* cell, const uint8_t* pbc, const int32_t* species,
+                                      int64_t center_begin, int64_t center_end, float* features, int64_t* jac_off,
+                                      int32_t* jac_j, float* jac, int64_t cap, int64_t* nnz_out, void* stream) {
+  return grad_impl(h, n_struct, atom_off, pos, cell, pbc, species, center_begin, center_end, true, features, jac_off,
+                   jac_j, jac, cap, nnz_out, (cudaStream_t)stream);
 }
 
 gmp_status gmp_featurize_points(gmp_handle h, int32_t n_struct, const int64_t* atom_off, const double* pos,

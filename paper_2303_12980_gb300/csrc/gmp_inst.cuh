@@ -7,6 +7,9 @@
 
 namespace gmpk {
 
+// The work counter of a launch over centers center0 .. N-1.
+static __global__ void k_counter_start(int32_t* counter, int32_t v) { *counter = v; }
+
 template <int L, int NS, int TILE>
 size_t smem_bytes(const GmpPass& P, int warps, int extra_per_warp) {
   return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax) +
@@ -44,10 +47,16 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t blocks = (int64_t)sm_count * per_sm;
-  const int64_t need = (K.N + warps - 1) / warps;
+  const int64_t need = (K.N - K.center0 + warps - 1) / warps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  e = cudaMemsetAsync(K.counter, 0, sizeof(int32_t), st);
+  if (K.center0 == 0) {
+    e = cudaMemsetAsync(K.counter, 0, sizeof(int32_t), st);
+  } else {
+    k_counter_start<<<1, 1, 0, st>>>(K.counter, (int32_t)K.center0);
+    ++*launches;
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)blocks, warps * 32, smem, st>>>(K);
   ++*launches;

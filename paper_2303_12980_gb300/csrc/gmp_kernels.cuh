@@ -142,6 +142,8 @@ struct KParams {
   int32_t* jac_j;
   float* jac;             // [nnz, F, 3]
   int32_t* counter;
+  int64_t center0;        // centers center0 .. N-1 (the work counter starts there);
+                          // jac_off row 0 belongs to center center0 (jacobian)
   const int32_t* center_struct;  // [N] structure of each center (virial)
   double* virial;                // [S, 3, 3] strain derivative accumulators (virial)
   // features too ill-conditioned for FP32 (recomputed in double-float
@@ -890,8 +892,8 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
     for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
     __syncwarp();
     adjoints<L, NS>(P, Mu, nullptr, Lam);  // g = 1 per feature: lam = d f / d mu
-    const int64_t r0 = K.jac_off[i];
-    const int R = (int)(K.jac_off[i + 1] - r0);
+    const int64_t r0 = K.jac_off[i - K.center0];
+    const int R = (int)(K.jac_off[i - K.center0 + 1] - r0);
     // the center's own row: the rank of atom i among its neighbor atoms
     int64_t lo = p0, hi = p1;
     while (lo < hi) {

@@ -476,6 +476,30 @@ def test_small_batch_binning_matches_multi_kernel_binning(torch):
         assert torch.equal(f_one, f_big[k * n:(k + 1) * n]), k
 
 
+def test_jacobian_center_chunks(torch):
+    """gmp_featurize_grad_centers: the Jacobian taken in center chunks (one
+    of them empty; one with host buffers) equals the whole-batch call row
+    for row, bit for bit."""
+    w = wl("fcc4096")
+    F = _featurizer(w)
+    pos, sp = _dev(torch, w)
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    for b, e in [(0, 1000), (1000, 1000), (1000, 2731), (2731, 4096)]:
+        f2, jo2, jj2, jac2 = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc, centers=(b, e))
+        torch.cuda.synchronize()
+        r0, r1 = int(joff[b]), int(joff[e])
+        assert torch.equal(f2, feat[b:e]), (b, e)
+        assert torch.equal(jo2, joff[b:e + 1] - r0), (b, e)
+        assert torch.equal(jj2, jj[r0:r1]) and torch.equal(jac2, jac[r0:r1]), (b, e)
+    fh, joh, jjh, jach = F.featurize_grad(w.positions, w.species, w.atom_off, w.cells, w.pbc, centers=(1000, 2731))
+    r0, r1 = int(joff[1000]), int(joff[2731])
+    assert torch.equal(fh, feat[1000:2731].cpu()) and torch.equal(joh, (joff[1000:2732] - r0).cpu())
+    assert torch.equal(jjh, jj[r0:r1].cpu()) and torch.equal(jach, jac[r0:r1].cpu())
+    with pytest.raises(ValueError):
+        F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc, centers=(10, 5))
+
+
 def test_jacobian_capacity_contract(torch):
     """gmp_featurize_grad through the C ABI with a row buffer that is too
     short: status GMP_ERR_CAPACITY, *nnz_out = the rows needed, and no
