@@ -6,7 +6,7 @@ import pytest
 
 from paper_2303_12980_gb300 import synth
 
-from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors, record
+from parity import FEAT_TOL, GRAD_TOL, JAC_TAU, feature_errors, grad_errors, record
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +54,36 @@ def test_full_size_sampled(torch, oracle_mod, name, n_centers, n_atoms):
     cnt = (noff[1:] - noff[:-1]).cpu().numpy()[centers]
     ooff, _, _, _ = oracle_mod.neighbors(w, centers)
     assert np.array_equal(cnt, np.diff(ooff))
+
+
+def test_full_size_jacobian_chunk(torch, oracle_mod):
+    """The slab's dense Jacobian (about 37 M rows, 50 GB in all) taken as one
+    chunk of 32,768 centers through gmp_featurize_grad_centers: the rows and
+    features of 8 sampled centers of the chunk against the FP64 oracle
+    (floors JAC_TAU G_abs and 1e-6 F_abs)."""
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    w = _w("fcc_slab262k")
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    b, e = 100000, 100000 + 32768
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc, centers=(b, e))
+    torch.cuda.synchronize()
+    assert feat.shape == (e - b, w.n_features) and joff.shape == (e - b + 1,)
+    joff, jj = joff.cpu().numpy(), jj.cpu().numpy()
+    local = synth.subset_centers(e - b, 8, seed=33)
+    ref, fabs = oracle_mod.features(w, local + b, want_abs=True)
+    assert feature_errors(feat.cpu().numpy()[local], ref, fabs).max() <= FEAT_TOL
+    ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, local + b, want_abs=True)
+    worst = 0.0
+    for t, c in enumerate(local):
+        r0, r1 = joff[c], joff[c + 1]
+        assert np.array_equal(jj[r0:r1], oj[ooff[t]:ooff[t + 1]])
+        err = grad_errors(jac[r0:r1].cpu().numpy(), ojac[ooff[t]:ooff[t + 1]], oabs[ooff[t]:ooff[t + 1]],
+                          tau=JAC_TAU)
+        worst = max(worst, float(err.max()))
+    record("fullsize/jacobian_chunk", max_rel_err=worst, rows=int(joff[-1]))
+    assert worst <= GRAD_TOL, worst
 
 
 def test_edge_cases(torch, oracle_mod):
