@@ -38,9 +38,26 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
   if (warps > 16) warps = 16;
   if (shape.warps > 0 && shape.warps < warps) warps = shape.warps;
   while (warps > 1 && smem_of(warps) > 227 * 1024) --warps;
+  cudaError_t e = cudaSuccess;
+  if (kind == GMP_KIND_JACOBIAN && shape.warps <= 0) {
+    // untuned Jacobian launch: the CTA size with the most resident warps
+    // (at order 6 the kernel takes 165 registers: one 8-warp CTA per SM,
+    // or three 4-warp CTAs)
+    int best_w = warps, best_res = 0;
+    for (int w = warps; w >= 1; w >>= 1) {
+      if (smem_of(w) > 227 * 1024) continue;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(w));
+      if (e != cudaSuccess) return e;
+      int ps = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, fn, w * 32, smem_of(w));
+      if (e != cudaSuccess) return e;
+      if (ps * w > best_res) { best_res = ps * w; best_w = w; }
+    }
+    warps = best_w;
+  }
   const size_t smem = smem_of(warps);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
