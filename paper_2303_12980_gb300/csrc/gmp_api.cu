@@ -916,6 +916,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       P.ord_col[P.n_ord] = col[o] + s0;
       ++P.n_ord;
     }
+    P.ord_dense = 1;
+    for (int o = 0; o < P.n_ord; ++o) P.ord_dense &= P.ord_l[o] == o ? 1 : 0;
     const int RB = gmp_rad_block(L), NSB = pd.NS / 4;
     std::vector<float> tab((size_t)h->n_el * NSB * h->kmax * RB * 4, 0.0f);
     int64_t off = 0;

@@ -90,6 +90,7 @@ struct GmpPass {
   int ord_l[8];        // orders written
   int ord_col[8];      // feature column of (order, sigma 0) for this pass
   int dens_col;        // column of order -1 or -1
+  int ord_dense;       // 1 when ord_l[o] == o for every o (orders 0 .. n_ord-1 in order)
   const float* rad;    // [n_el][nsig_pad / 4][kmax][gmp_rad_block(lmax)] float4
   float nbeta[16];     // -beta = -1/(2 sigma^2) per sigma of the pass (0 for padding)
   const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]

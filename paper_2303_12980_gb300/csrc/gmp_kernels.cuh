@@ -964,33 +964,49 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           for (int l = 0; l < L + 2; ++l) Rl[l] = __fmaf_rn(ent[4 * (2 + l)], E, Rl[l]);
         }
         const float inv = r2h > 0.0f ? 1.0f / r2h : 0.0f;
-        static_for<NO>([&](auto oo) {
-          constexpr int o = decltype(oo)::value;
-          if (o < P.n_ord) {
-            const int l = P.ord_l[o];
-            float g[3] = {0.0f, 0.0f, 0.0f};
-            static_for<L + 1>([&](auto ll) {
-              constexpr int lc = decltype(ll)::value;
-              if (l == lc) {
-                float pv = 0.0f, V[3];
+        // d f_{lc,s} / d d of this pair for a compile-time order lc
+        auto order_term = [&](auto ll, float (&g)[3]) {
+          constexpr int lc = decltype(ll)::value;
+          float pv = 0.0f, V[3];
 #pragma unroll
-                for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam_s[k], S1[k], pv);
-                shift_contract_order<lc>(lam_s, S1, V);
-                const float Rv = Rl[lc], Rd = nb * Rl[lc + 1];  // dR_l/dr^2 = -beta R_{l+1}
-                if (r2h > 0.0f) {
-                  const float c = 2.0f * Rd * pv + Rv * (float)(2 * lc + 1) * pv * inv;
-                  g[0] = dx * c - Rv * V[0] * inv;
-                  g[1] = dy * c - Rv * V[1] * inv;
-                  g[2] = dz * c - Rv * V[2] * inv;
-                } else if (lc == 1) {  // d = 0: only order 1 has a gradient
-                  g[0] = Rv * lam_s[3]; g[1] = Rv * lam_s[1]; g[2] = Rv * lam_s[2];
-                }
-              }
-            });
-            acc[o][0] += g[0]; acc[o][1] += g[1]; acc[o][2] += g[2];
-            if (other) { self[o][0] -= g[0]; self[o][1] -= g[1]; self[o][2] -= g[2]; }
+          for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam_s[k], S1[k], pv);
+          shift_contract_order<lc>(lam_s, S1, V);
+          const float Rv = Rl[lc], Rd = nb * Rl[lc + 1];  // dR_l/dr^2 = -beta R_{l+1}
+          if (r2h > 0.0f) {
+            const float c = 2.0f * Rd * pv + Rv * (float)(2 * lc + 1) * pv * inv;
+            g[0] = dx * c - Rv * V[0] * inv;
+            g[1] = dy * c - Rv * V[1] * inv;
+            g[2] = dz * c - Rv * V[2] * inv;
+          } else if (lc == 1) {  // d = 0: only order 1 has a gradient
+            g[0] = Rv * lam_s[3]; g[1] = Rv * lam_s[1]; g[2] = Rv * lam_s[2];
           }
-        });
+        };
+        auto accumulate = [&](int o, const float (&g)[3]) {
+          acc[o][0] += g[0]; acc[o][1] += g[1]; acc[o][2] += g[2];
+          if (other) { self[o][0] -= g[0]; self[o][1] -= g[1]; self[o][2] -= g[2]; }
+        };
+        if (P.ord_dense) {  // orders 0, 1, ... in order: one block per order
+          static_for<NO>([&](auto oo) {
+            constexpr int o = decltype(oo)::value;
+            if (o < P.n_ord) {
+              float g[3] = {0.0f, 0.0f, 0.0f};
+              order_term(oo, g);
+              accumulate(o, g);
+            }
+          });
+        } else {
+          static_for<NO>([&](auto oo) {
+            constexpr int o = decltype(oo)::value;
+            if (o < P.n_ord) {
+              const int l = P.ord_l[o];
+              float g[3] = {0.0f, 0.0f, 0.0f};
+              static_for<L + 1>([&](auto ll) {
+                if (l == decltype(ll)::value) order_term(ll, g);
+              });
+              accumulate(o, g);
+            }
+          });
+        }
       }
       if (dens_lane) {
         float drho;
