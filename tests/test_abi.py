@@ -75,3 +75,22 @@ def test_create_rejects_invalid_parameters_before_the_device():
     assert create(cutoff=0.0, overlap_threshold=0.0) == INVALID
     expo[0] = -1.0
     assert create() == INVALID                      # exponent <= 0
+
+
+def test_entry_points_reject_a_null_handle():
+    """Every featurize entry point returns GMP_ERR_INVALID_ARG for a null
+    handle before touching the device (runs without a GPU)."""
+    import ctypes as C
+    from paper_2303_12980_gb300 import build
+    from paper_2303_12980_gb300.binding import load_library
+    build.build()
+    L = load_library()
+    nnz = C.c_int64(-1)
+    off = (C.c_int64 * 2)(0, 1)
+    INVALID = 1
+    common = (None, 1, C.addressof(off), None, None, None, None)
+    assert L.gmp_featurize(*common, None, None) == INVALID
+    assert L.gmp_featurize_vjp(*common, None, None, None, None) == INVALID
+    assert L.gmp_featurize_grad(*common, None, None, None, None, 0, C.byref(nnz), None) == INVALID
+    assert L.gmp_featurize_grad_centers(*common, 0, 1, None, None, None, None, 0, C.byref(nnz), None) == INVALID
+    assert L.gmp_neighbors(*common, None, None, None, 0, C.byref(nnz), None) == INVALID
