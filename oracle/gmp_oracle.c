@@ -37,6 +37,14 @@
  *      atom are summed, and the center's own block is minus the sum of the
  *      others (images of the center do not move relative to it).
  * Build with -ffp-contract=off (no FMA contraction) so step 1 is bit-stable.
+ *
+ * Accuracy of step 3: the monomial sum cancels when the product Gaussian's
+ * variance 1/(2 gamma) is large against its centre P = (alpha/gamma) d
+ * (narrow probes, small density exponents, high orders): the moments are
+ * ~var^(l/2) while the harmonic combination leaves ~|P|^l.  The FP64 error
+ * of a moment is then a few units of 2^-53 of the sum of the magnitudes it
+ * adds (K |coef| a_p a_q a_s, a_n the moments of the same recursion with
+ * |P|), not of its own value.
  */
 #include <math.h>
 #include <stdint.h>

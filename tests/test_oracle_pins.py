@@ -154,11 +154,96 @@ def test_moments_match_3d_quadrature(oracle_mod):
             col += 1
 
 
-def test_factorised_route_agrees(oracle_mod):
+def _grid_moments(pos, coef, expo, sig, orders, center, h, half):
+    """Moments mu_{l,abc} = sum over a grid of N_s S_abc(r) exp(-beta r^2)
+    rho(r + center) h^3, every component of the listed orders, and the
+    matching sums of |S| (the scale the comparison is relative to).  The
+    trapezoid rule on these Gaussian integrands converges spectrally: at
+    h = 0.2 A and alpha + beta <= 4.1 A^-2 the aliasing error is of the
+    order of exp(-pi^2 / (h^2 (alpha + beta))) < 1e-26 of the integral."""
+    import oracle.oracle as O
+    g = np.arange(-half, half + h / 2, h)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    beta = 1.0 / (2 * sig * sig)
+    Ns = (2 * math.pi * sig * sig) ** -1.5
+    rho = np.zeros_like(X)
+    for p in np.asarray(pos) - center:
+        R2 = (X - p[0]) ** 2 + (Y - p[1]) ** 2 + (Z - p[2]) ** 2
+        for c, a in zip(coef, expo):
+            rho += c * np.exp(-a * R2)
+    base = Ns * np.exp(-beta * (X * X + Y * Y + Z * Z)) * rho * h ** 3
+    lmax = max(orders)
+    Xp, Yp, Zp = [np.ones_like(X)], [np.ones_like(X)], [np.ones_like(X)]
+    for _ in range(lmax):
+        Xp.append(Xp[-1] * X)
+        Yp.append(Yp[-1] * Y)
+        Zp.append(Zp[-1] * Z)
+    mu, scale = [], []
+    for l in orders:
+        for (a, b, c) in O.components(l):
+            S = np.zeros_like(X)
+            for (pp, qq, ss), k in O.mcsh_poly(a, b, c).items():
+                S += k * Xp[pp] * Yp[qq] * Zp[ss]
+            mu.append(float(np.sum(S * base)))
+            scale.append(float(np.sum(np.abs(S) * base)))
+    return np.array(mu), np.array(scale)
+
+
+@pytest.mark.parametrize("sig", [0.45, 0.8])
+def test_high_order_moments_match_3d_quadrature(oracle_mod, sig):
+    # orders 4, 5, 6 (every component): the oracle's 1-D moment route at the
+    # orders the slab workload runs, against the defining integral on a grid
+    pos = np.array([[0.0, 0.0, 0.0], [0.9, -0.6, 0.5], [-0.5, 0.8, -0.7], [1.2, 0.4, 1.0]])
+    coef, expo = [0.7, 0.4], [1.6, 0.6]
+    w = _cluster(pos, [0, 0, 0, 0], [4, 5, 6], [sig], coef, expo, [2])
+    mu = oracle_mod.features(w, [0], want_mu=True)[1][0]
+    want, scale = _grid_moments(pos, coef, expo, sig, [4, 5, 6], np.zeros(3), 0.2, 7.0)
+    assert mu.shape == want.shape
+    assert np.all(np.abs(mu - want) <= 1e-12 * scale), np.max(np.abs(mu - want) / scale)
+
+
+def test_high_order_point_features_match_3d_quadrature(oracle_mod):
+    # features (weighted sums of squares over all components) of orders 4-6
+    # at a point that is not an atom
+    pos = np.array([[0.0, 0.0, 0.0], [0.9, -0.6, 0.5], [-0.5, 0.8, -0.7]])
+    coef, expo = [0.7, 0.4], [1.6, 0.6]
+    sig = 0.6
+    p = np.array([0.35, 0.2, -0.15])
+    w = _cluster(pos, [0, 0, 0], [4, 5, 6], [sig], coef, expo, [2])
+    f = oracle_mod.point_features(w, p[None, :], [0])[0]
+    mu, mu_abs = _grid_moments(pos, coef, expo, sig, [4, 5, 6], p, 0.2, 7.0)
+    k = 0
+    for col, l in enumerate([4, 5, 6]):
+        want = scale = 0.0
+        for (a, b, c) in oracle_mod.components(l):
+            wt = math.factorial(l) / (math.factorial(a) * math.factorial(b) * math.factorial(c))
+            want += wt * mu[k] * mu[k]
+            scale += wt * mu_abs[k] * mu_abs[k]
+            k += 1
+        assert abs(f[col] - want) <= 1e-11 * scale, (l, f[col], want)
+
+
+@pytest.mark.parametrize("orders,sigmas", [
+    ([0, 1, 2], None),
+    # the slab's probe set: orders 0-6, 16 sigmas log-spaced in 0.05-1.5 A
+    ([0, 1, 2, 3, 4, 5, 6], list(np.geomspace(0.05, 1.5, 16))),
+])
+def test_factorised_route_agrees(oracle_mod, orders, sigmas):
     # Mean-value property: the Gaussian average of a harmonic polynomial is
     # its value at the Gaussian's centre, so each overlap integral equals
     # c N_s (pi/g)^1.5 (alpha/g)^l exp(-(alpha beta/g) r^2) S_abc(d).
-    w = synth.workload("random64_box")
+    # The oracle instead sums the polynomial's monomials against 1-D
+    # Gaussian moments, and that sum cancels: for a narrow probe and a small
+    # density exponent the product Gaussian's variance 1/(2g) dwarfs its
+    # centre P = (alpha/g) d, the monomial moments are ~var^(l/2) while the
+    # harmonic combination leaves ~|P|^l.  Its FP64 rounding error is then
+    # bounded by a few units of 2^-53 times the sum of the magnitudes it
+    # adds, K |coef| a_p a_q a_s with a_n the moments of the same recursion
+    # taken with |P| (every term non-negative): the tolerance below is
+    # 1e-12 of the factorised scale plus 2^-46 of that summation scale.
+    w = synth.workload("random64_box").replace(orders=orders)
+    if sigmas is not None:
+        w = w.replace(sigmas=sigmas)
     centers = np.array([0, 5, 17, 40])
     f, mu = oracle_mod.features(w, centers, want_mu=True)
     off, j, sh, d = oracle_mod.neighbors(w, centers)
@@ -169,26 +254,41 @@ def test_factorised_route_agrees(oracle_mod):
         for s in range(len(w.sigmas)):
             for abc in oracle_mod.components(l):
                 cols.append((l, s, abc))
+    lmax = max(w.orders)
     for t in range(len(centers)):
         dd = d[off[t]:off[t + 1]]
         r2 = (dd * dd).sum(1)
         ee = w.species[j[off[t]:off[t + 1]]]
-        for col, (l, s, abc) in enumerate(cols):
+        # per (sigma, primitive): K per pair and the |P| moments a_n per axis
+        cache = {}
+        for s in range(len(w.sigmas)):
             sig = w.sigmas[s]
             beta = 1 / (2 * sig * sig)
-            P = oracle_mod.mcsh_poly(*abc)
-            S = sum(k * dd[:, 0] ** p * dd[:, 1] ** q * dd[:, 2] ** r for (p, q, r), k in P.items())
-            R = np.zeros_like(r2)
             for e in range(w.n_elements):
                 m = ee == e
                 for k in range(go[e], go[e + 1]):
                     a, c = w.gauss_exp[k], w.gauss_coef[k]
                     gm = a + beta
-                    R[m] += c * (2 * math.pi * sig * sig) ** -1.5 * (math.pi / gm) ** 1.5 * (a / gm) ** l * \
-                        np.exp(-(a * beta / gm) * r2[m])
+                    K = c * (2 * math.pi * sig * sig) ** -1.5 * (math.pi / gm) ** 1.5 * np.exp(-(a * beta / gm) * r2[m])
+                    Pa = np.abs(dd[m]) * (a / gm)
+                    mom = [np.ones_like(Pa), Pa]
+                    for n in range(1, lmax):
+                        mom.append(Pa * mom[n] + n * (0.5 / gm) * mom[n - 1])
+                    cache[(s, k)] = (m, a / gm, K, mom)
+        for col, (l, s, abc) in enumerate(cols):
+            P = oracle_mod.mcsh_poly(*abc)
+            S = sum(k * dd[:, 0] ** p * dd[:, 1] ** q * dd[:, 2] ** r for (p, q, r), k in P.items())
+            R = np.zeros_like(r2)
+            cscale = 0.0
+            for e in range(w.n_elements):
+                for k in range(go[e], go[e + 1]):
+                    m, ratio, K, mom = cache[(s, k)]
+                    R[m] += K * ratio ** l
+                    summed = sum(abs(kk) * mom[p][:, 0] * mom[q][:, 1] * mom[r][:, 2] for (p, q, r), kk in P.items())
+                    cscale += float(np.sum(np.abs(K) * summed))
             want = float(np.sum(R * S))
             scale = float(np.sum(np.abs(R * S)))
-            assert abs(mu[t, col] - want) <= 1e-12 * scale + 1e-300
+            assert abs(mu[t, col] - want) <= 1e-12 * scale + 2.0 ** -46 * cscale + 1e-300, (t, l, s, abc)
 
 
 def test_density_order_matches_direct_sum(oracle_mod):
@@ -287,8 +387,9 @@ def test_supercell_replication(oracle_mod):
 
 
 # ------------------------------------------------------------ gradients
-def test_jacobian_matches_central_differences(oracle_mod):
-    w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2])
+@pytest.mark.parametrize("orders", [[-1, 0, 1, 2], [-1, 3, 4, 5, 6]])
+def test_jacobian_matches_central_differences(oracle_mod, orders):
+    w = synth.workload("random64_box").replace(orders=orders)
     atoms = [2, 33]
     h = 1e-4
     centers = np.arange(w.n_atoms)
@@ -409,13 +510,15 @@ def _strained_loss(oracle_mod, w, g, eps):
     return float((oracle_mod.features(w2) * g).sum())
 
 
-@pytest.mark.parametrize("kind", ["periodic", "cluster", "triclinic"])
+@pytest.mark.parametrize("kind", ["periodic", "periodic_high", "cluster", "triclinic"])
 def test_virial_matches_strained_central_differences(oracle_mod, kind):
     # W_ab = dL/d eps_ab with positions and lattice vectors strained alike,
     # against central differences of the oracle's own features (h = 1e-5;
     # the neighbor lists at +-h are checked to be the same)
     if kind == "periodic":
         w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2])
+    elif kind == "periodic_high":
+        w = synth.workload("random64_box").replace(orders=[0, 4, 5, 6])
     elif kind == "cluster":
         b = synth.batched10k(n_struct=2)
         a0, a1 = int(b.atom_off[1]), int(b.atom_off[2])
@@ -453,3 +556,85 @@ def test_virial_is_symmetric(oracle_mod):
     W, Wa = oracle_mod.virial(w, g, want_abs=True)
     for s in range(w.n_struct):
         assert np.abs(W[s] - W[s].T).max() <= 1e-12 * max(Wa[s].max(), 1e-300)
+
+
+# ------------------------------------------------------------ tolerance scales
+# Every parity floor is a fraction of a cancellation-free scale that the
+# oracle computes beside its result: F_abs (features: the same reduction
+# applied to sums of |per-pair contribution|) and jac_abs (derivatives: sum
+# over pairs and components of 2 w_c A_c |d t_c / d d|, A_c = sum of |t_c|).
+# An inflated scale would silently loosen every GPU test, so the scales are
+# pinned here: they equal the value where nothing can cancel and bound it
+# everywhere.
+def _lone_pair_workload(orders, sigmas):
+    # one element with three primitives; atom 1 is far beyond the cutoff of
+    # every point used below, so a point near atom 0 has exactly one pair
+    coef, expo = [0.6, 0.3, 0.2], [0.5, 1.1, 2.0]
+    return _cluster([[0.0, 0.0, 0.0], [40.0, 0.0, 0.0]], [0, 0], orders, sigmas, coef, expo, [3], cutoff=6.0)
+
+
+def test_single_pair_scale_equals_feature_and_closed_form(oracle_mod):
+    # With one pair, F_abs = f exactly (|t|^2 = t^2), and by the sum rule
+    # sum_c w_c S_c(d)^2 = l! (2l-1)!! |d|^(2l) each feature of order l is
+    # f = R_{l,s}(r^2)^2 r^(2l) l! (2l-1)!!, R the Gaussian-product radial
+    # factor (mean-value route), for every order 0..6.
+    orders, sigmas = [-1, 0, 1, 2, 3, 4, 5, 6], [0.3, 0.7, 1.2]
+    w = _lone_pair_workload(orders, sigmas)
+    p = np.array([[0.8, -0.5, 0.9]])
+    f, fa = oracle_mod.point_features(w, p, [0], want_abs=True)
+    f, fa = f[0], fa[0]
+    d = -p[0]
+    r2 = float(d @ d)
+    assert np.all(np.abs(f - fa) <= 1e-15 * fa)
+    rho = sum(c * math.exp(-a * r2) for c, a in zip(w.gauss_coef, w.gauss_exp))
+    assert abs(f[0] - rho) <= 1e-15 * rho
+    col = 1
+    for l in orders[1:]:
+        dfact = math.prod(range(2 * l - 1, 0, -2)) if l > 0 else 1
+        for sig in sigmas:
+            beta = 1 / (2 * sig * sig)
+            R = 0.0
+            for c, a in zip(w.gauss_coef, w.gauss_exp):
+                g = a + beta
+                R += c * (2 * math.pi * sig * sig) ** -1.5 * (math.pi / g) ** 1.5 * (a / g) ** l * \
+                    math.exp(-(a * beta / g) * r2)
+            want = R * R * r2 ** l * math.factorial(l) * dfact
+            assert abs(f[col] - want) <= 1e-12 * want, (l, sig, f[col], want)
+            col += 1
+
+
+def test_scales_bound_features_and_derivatives(oracle_mod):
+    w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2, 3, 4, 5, 6])
+    f, fa = oracle_mod.features(w, want_abs=True)
+    assert np.all(f[:, 1:] >= 0.0) and np.all(f <= fa * (1 + 1e-13))
+    # density coefficients are all positive: nothing cancels in order -1 and
+    # order 0 (every per-pair term is positive), so there the scale is the value
+    assert np.all(np.abs(f[:, :1 + len(w.sigmas)] - fa[:, :1 + len(w.sigmas)]) <= 1e-13 * fa[:, :1 + len(w.sigmas)])
+    off, jj, jac, jab = oracle_mod.jacobian_rows(w, np.arange(w.n_atoms), want_abs=True)
+    assert np.all(np.linalg.norm(jac, axis=-1) <= jab * (1 + 1e-12) + 1e-300)
+    # the VJP scale bounds the VJP
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=19).astype(np.float64)
+    atoms = np.arange(0, w.n_atoms, 7)
+    v, vs = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    assert np.all(np.linalg.norm(v, axis=1) <= vs * (1 + 1e-12))
+    # mixed-sign density tables: the bounds still hold
+    coef = np.array(w.gauss_coef)
+    coef[1] *= -0.5
+    coef[6] *= -0.3
+    wm = w.replace(gauss_coef=coef)
+    f, fa = oracle_mod.features(wm, want_abs=True)
+    assert np.all(np.abs(f) <= fa * (1 + 1e-13))
+    off, jj, jac, jab = oracle_mod.jacobian_rows(wm, np.arange(0, w.n_atoms, 5), want_abs=True)
+    assert np.all(np.linalg.norm(jac, axis=-1) <= jab * (1 + 1e-12) + 1e-300)
+
+
+def test_derivative_scale_equals_row_where_nothing_cancels(oracle_mod):
+    # Two atoms: each center sees its own self pair (d = 0: the order -1 and
+    # order 0 terms have zero gradient there) and the other atom.  For orders
+    # -1 and 0 every term and moment is positive, so the row of the other
+    # atom and the center's own row (minus it) have |J| = jac_abs exactly.
+    w = _cluster([[0.0, 0.0, 0.0], [1.1, -0.7, 0.4]], [0, 0], [-1, 0], [0.3, 0.8], [0.6, 0.3], [0.5, 1.7], [2],
+                 cutoff=6.0)
+    off, jj, jac, jab = oracle_mod.jacobian_rows(w, np.arange(2), want_abs=True)
+    assert np.array_equal(off, [0, 2, 4])
+    assert np.all(np.abs(np.linalg.norm(jac, axis=-1) - jab) <= 1e-13 * jab)
