@@ -154,11 +154,13 @@ def run_ours(args, rank, world, local_rank):
         measured = probe_peaks(local_rank)
     except Exception as exc:  # diagnostics only
         measured = {"error": str(exc)}
-    try:  # the moment contraction, packed FP32 (as run) against a TF32x3 tensor-core version
-        from paper_2303_12980_gb300.binding import probe_contraction
-        contraction = probe_contraction(local_rank)
-    except Exception as exc:  # diagnostics only
-        contraction = {"error": str(exc)}
+    contraction = None
+    if args.probes:  # the moment contraction, packed FP32 (as run) against tensor-core versions
+        try:
+            from paper_2303_12980_gb300.binding import probe_contraction
+            contraction = probe_contraction(local_rank)
+        except Exception as exc:  # diagnostics only
+            contraction = {"error": str(exc)}
 
     for _ in range(args.warmup):
         step()
@@ -552,6 +554,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--call", default="vjp", choices=["vjp", "grad", "features"],
                     help="the timed call (default: features + VJP, the headline step)")
+    ap.add_argument("--probes", action="store_true",
+                    help="also run the contraction probe (packed FP32 against tensor-core versions) before the timed region")
     ap.add_argument("--configs", action="store_true",
                     help="measure every workload of the baseline table (one JSON object) instead")
     args = ap.parse_args()

@@ -39,10 +39,11 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
-// floor(a / b) for |a| < 2^20 and 1 <= b <= 1024 without an integer
-// division: the single-precision quotient (approximate reciprocal, error
-// well below 2^-20 relative) is within one of the true one, and the
-// remainder test corrects it.
+// floor(a / b) for |a| < 2^20 and 1 <= b < 2^24 (both exact in FP32)
+// without an integer division: the approximate reciprocal (2 ulp) and the
+// rounded product leave the single-precision quotient within a relative
+// 2^-21 of a / b, i.e. off by less than |a| / b * 2^-21 < 0.5, so its floor
+// is within one of the true one and the remainder test corrects it.
 __device__ __forceinline__ int floor_div_small(int a, int b) {
   int q = __float2int_rd(__fmul_rn(__int2float_rn(a), __fdividef(1.0f, __int2float_rn(b))));
   const int r = a - q * b;

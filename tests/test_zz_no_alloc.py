@@ -34,8 +34,16 @@ def test_noalloc_counts_match_neighbors_two_calls():
     from paper_2303_12980_gb300.binding import GMPFeaturizer
     assert torch.cuda.is_available()
     f = _lib()
-    for name in ["fcc4096", "random64_box"]:
-        w = synth.workload(name)
+    b = synth.batched10k(n_struct=2)   # structure 1 is a non-periodic cluster
+    a0, a1 = int(b.atom_off[1]), int(b.atom_off[2])
+    cluster = b.replace(positions=b.positions[a0:a1], species=b.species[a0:a1],
+                        atom_off=np.array([0, a1 - a0], np.int64), cells=b.cells[1:2], pbc=b.pbc[1:2])
+    assert not cluster.pbc.any()
+    cases = {"fcc4096": synth.workload("fcc4096"), "random64_box": synth.workload("random64_box"),
+             # exactly the 32768-atom limit of the static array
+             "fcc_slab32k": synth.workload("fcc_slab32k"), "cluster": cluster}
+    assert cases["fcc_slab32k"].n_atoms == 32768
+    for name, w in cases.items():
         pos = torch.from_numpy(w.positions).cuda()
         sp = torch.from_numpy(w.species).cuda()
         cell = np.ascontiguousarray(w.cells[0])
