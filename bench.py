@@ -443,7 +443,7 @@ def run_configs(args):
                 a, b = joff[i], joff[i + 1]
                 num = np.linalg.norm(jac[a:b].astype(np.float64) - ojac[ooff[t]:ooff[t + 1]], axis=-1)
                 den = np.maximum(np.maximum(np.linalg.norm(ojac[ooff[t]:ooff[t + 1]], axis=-1),
-                                            1e-2 * oabs[ooff[t]:ooff[t + 1]]), 2.0 ** -126)
+                                            5e-3 * oabs[ooff[t]:ooff[t + 1]]), 2.0 ** -126)
                 worst = max(worst, float((num / den).max()))
             acc["grad_max_rel_err"] = worst
         elif mode == "vjp":

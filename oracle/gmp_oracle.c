@@ -584,6 +584,25 @@ int oracle_num_moment_columns(const oracle_problem *P) {
   return X.ncol;
 }
 
+/* Step 3 per pair, for inspection: the pairs of center i in list order
+ * (oracle_neighbor_lists), each pair's moment contributions t[pair][col]
+ * and their derivatives dt[pair][col][3] with respect to d.  m is the
+ * pair count from oracle_neighbor_counts. */
+int oracle_pair_terms(const oracle_problem *P, int64_t i, int64_t m, double *t_out, double *dt_out) {
+  octx X;
+  if (ctx_init(&X, P)) return -1;
+  opair *buf = NULL;
+  int64_t cap = 0;
+  int64_t got = list_neighbors(P, i, &buf, &cap);
+  if (got != m) { free(buf); return -1; }
+  for (int64_t u = 0; u < m; ++u) {
+    double r, dr[3];
+    pair_terms(&X, P->species[buf[u].j], buf[u].d, t_out + u * X.ncol, dt_out + 3 * u * X.ncol, &r, dr);
+  }
+  free(buf);
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Step 6: Jacobian rows d f_i / d x_j.                                 */
 /* ------------------------------------------------------------------ */

@@ -79,6 +79,7 @@ def lib():
             L.oracle_virial.argtypes = [P, vp, vp, vp]
             L.oracle_jacobian_counts.argtypes = [P, C.c_int64, vp, vp]
             L.oracle_jacobian_rows.argtypes = [P, C.c_int64, vp, vp, vp, vp, vp]
+            L.oracle_pair_terms.argtypes = [P, C.c_int64, C.c_int64, vp, vp]
             _lib = L
     return _lib
 
@@ -209,6 +210,24 @@ def virial(w, g, want_abs=False):
     if lib().oracle_virial(C.byref(P.s), gg.ctypes.data, W.ctypes.data, Wa.ctypes.data if want_abs else None):
         raise ValueError("oracle_virial failed")
     return (W, Wa) if want_abs else W
+
+
+def pair_terms(w, center):
+    """Per-pair moment contributions of one center, in the order of
+    neighbors(w, [center]): t [m, ncol] and dt [m, ncol, 3] = d t / d d, the
+    columns ordered (order slot, sigma, component) as the moments of
+    features(..., want_mu=True)."""
+    P = Problem(w)
+    c = np.array([center], np.int64)
+    counts = np.zeros(1, np.int64)
+    if lib().oracle_neighbor_counts(C.byref(P.s), 1, c.ctypes.data, counts.ctypes.data):
+        raise ValueError("singular periodic cell")
+    m = int(counts[0])
+    t = np.zeros((m, P.ncol), np.float64)
+    dt = np.zeros((m, P.ncol, 3), np.float64)
+    if lib().oracle_pair_terms(C.byref(P.s), int(center), m, t.ctypes.data, dt.ctypes.data):
+        raise RuntimeError("pair terms failed")
+    return t, dt
 
 
 def jacobian_rows(w, centers=None, want_abs=False):

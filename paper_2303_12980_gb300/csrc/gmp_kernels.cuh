@@ -181,6 +181,19 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
   j = __float_as_int(b.z);
 }
 
+// r^2 fed to the MCSH recurrences: formed from the FP32 components
+// themselves, so that the recurrences evaluate the harmonic polynomials of
+// (dx, dy, dz) exactly as written.  The pair record's r^2 (that of the
+// exact displacement, which the exponent arguments use) differs from
+// dx^2 + dy^2 + dz^2 of the rounded components by ~2^-24 relative; with it
+// the recurrences would mix a non-harmonic part of that relative size into
+// every component, and their integer coefficients amplify it: a Jacobian
+// entry then carried ~5 units of 2^-24 of its cancellation-free scale
+// instead of ~1.5.
+__device__ __forceinline__ float mcsh_r2(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
 // Pulls the cache line of a pair record into L1 ahead of its use (no registers held).
 __device__ __forceinline__ void prefetch_pair(const GmpPair* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -394,7 +407,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       float* srow = St + pl * SH::SSTR;
       if (half == 0) {  // MCSH components; r^l in the free slot of each order's last chunk
         float S[SH::NIND];
-        GmpMcsh<L>::eval(dx, dy, dz, r2h, S);
+        GmpMcsh<L>::eval(dx, dy, dz, mcsh_r2(dx, dy, dz), S);
         static_for<SH::NCH>([&](auto cc) {
           constexpr int c = decltype(cc)::value;
           constexpr int k0 = chunk_k0(c);
@@ -726,7 +739,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
       }
     }
     float g[3];
-    pair_gradient<L>(lam, lamd, dx, dy, dz, r2h, g);
+    pair_gradient<L>(lam, lamd, dx, dy, dz, mcsh_r2(dx, dy, dz), g);
     if (P.want_density && gd != 0.0f) {
       float drho;
       density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
@@ -950,7 +963,8 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
       const bool other = j != (int32_t)i;
       if (s_ok) {
         float S1[SH::NIND1];
-        GmpMcsh<L + 1>::eval(dx, dy, dz, r2h, S1);
+        const float r2c = mcsh_r2(dx, dy, dz);
+        GmpMcsh<L + 1>::eval(dx, dy, dz, r2c, S1);
         // radial factors of this lane's sigma, orders 0..L+1 (double-float
         // exponent argument: a row of one neighbor averages no other terms)
         float Rl[L + 2];
@@ -963,7 +977,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
 #pragma unroll
           for (int l = 0; l < L + 2; ++l) Rl[l] = __fmaf_rn(ent[4 * (2 + l)], E, Rl[l]);
         }
-        const float inv = r2h > 0.0f ? 1.0f / r2h : 0.0f;
+        const float inv = r2c > 0.0f ? 1.0f / r2c : 0.0f;
         // d f_{lc,s} / d d of this pair for a compile-time order lc
         auto order_term = [&](auto ll, float (&g)[3]) {
           constexpr int lc = decltype(ll)::value;
@@ -972,7 +986,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           for (int k = lc * lc; k < (lc + 1) * (lc + 1); ++k) pv = __fmaf_rn(lam_s[k], S1[k], pv);
           shift_contract_order<lc>(lam_s, S1, V);
           const float Rv = Rl[lc], Rd = nb * Rl[lc + 1];  // dR_l/dr^2 = -beta R_{l+1}
-          if (r2h > 0.0f) {
+          if (r2c > 0.0f) {
             const float c = 2.0f * Rd * pv + Rv * (float)(2 * lc + 1) * pv * inv;
             g[0] = dx * c - Rv * V[0] * inv;
             g[1] = dy * c - Rv * V[1] * inv;
