@@ -234,6 +234,33 @@ def emit_eval_scaled(L):
     return "\n".join(lines)
 
 
+def emit_eval_top(L):
+    """Only the components of order L, by the same scaled recurrences, given
+    S[0 .. L^2) (orders below L) already evaluated: lets a kernel evaluate
+    the orders it contracts first and the next order later."""
+    lines = [f"__device__ __forceinline__ void gmp_mcsh_top_{L}(float x, float y, float z, float r2, "
+             f"float* __restrict__ S) {{"]
+    scaled = {}
+    body = []
+    for t in indep_components(L):
+        k = flat(t)
+        expr = None
+        for coef, kind, src in recurrence_terms(t):
+            v = "r2" if kind == "r2" else kind
+            if coef == 1:
+                m = v
+            else:
+                m = f"{v}_{'m' if coef < 0 else ''}{abs(coef)}"
+                scaled[m] = f"__fmul_rn({fnum(coef)}, {v})"
+            expr = f"__fmul_rn({m}, S[{flat(src)}])" if expr is None else f"__fmaf_rn({m}, S[{flat(src)}], {expr})"
+        body.append(f"  S[{k}] = {expr};")
+    for m, e in sorted(scaled.items()):
+        lines.append(f"  const float {m} = {e};")
+    lines += body
+    lines.append("}")
+    return "\n".join(lines)
+
+
 def emit_eval_df(L):
     """The same recurrences in double-float arithmetic (gmp_f2, FP32 pairs):
     products of a coordinate and a lower component, integer coefficients
@@ -399,6 +426,8 @@ def generate() -> str:
     ]
     for L in range(LMAX + 2):
         out.append(emit_eval_scaled(L))
+    for L in range(1, LMAX + 2):
+        out.append(emit_eval_top(L))
     for L in range(LMAX + 1):
         out.append(emit_eval_df(L))
     for l in range(LMAX + 1):
@@ -420,6 +449,8 @@ def generate() -> str:
             f"  static constexpr int kInd = {nind(L)};\n"
             f"  static __device__ __forceinline__ void eval(float x, float y, float z, float r2, float* S) "
             f"{{ gmp_mcsh_indep_{L}(x, y, z, r2, S); }}\n"
+            + (f"  static __device__ __forceinline__ void eval_top(float x, float y, float z, float r2, float* S) "
+               f"{{ gmp_mcsh_top_{L}(x, y, z, r2, S); }}\n" if L >= 1 else "")
             + extra +
             f"}};")
     out.append("")

@@ -96,6 +96,9 @@ struct gmp_ctx {
   DevBuf bin_count, bin_cursor, bin_start, bin_y, bin_je, counts, nbr_off, scan_tmp, pairs;
   DevBuf scalars;  // err word, maxm, counter
   DevBuf grad_acc, jac_counts, jac_rows;
+  // VJP sums without float atomics: fixed-point bins per (atom,
+  // component), per-center own terms and strain-derivative sums
+  DevBuf gbins, own, vir_c;
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
   DevBuf exptab; // [64] 2^(-j/64) as double-floats (the refinement's exponential)
@@ -1146,9 +1149,34 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
   if (use_graph && (r = replay_graph(h, key, st)) != GMP_ERR_CAPACITY) return r;
   // buffers first (no allocation may happen while a graph is captured)
   GMP_CK(h->grad_acc.ensure(sizeof(double) * 3 * N), "grad_acc");
+  GMP_CK(h->gbins.ensure(sizeof(unsigned long long) * 3 * gmpk::kGradBins * N), "gradient bins");
+  GMP_CK(h->own.ensure(sizeof(double) * 3 * N), "own");
+  if (vir) GMP_CK(h->vir_c.ensure(sizeof(double) * 9 * N), "vir_c");
   for (const PassData& pd : h->passes)
     GMP_CK(h->mu.ensure(sizeof(float) * (size_t)N * std::max(pd.pass.nsig, 1) * (pd.L + 1) * (pd.L + 1)), "moments");
   if (!feat) GMP_CK(h->stage_feat.ensure(sizeof(float) * N * h->F), "feature scratch");
+  // No float atomics in the VJP: the backward kernel adds each pair's
+  // gradient, exactly, into integer fixed-point bins of its neighbor atom
+  // and writes each center's own term; a finishing kernel combines them in
+  // a fixed order.  Results are bit-reproducible.
+  auto vjp_begin = [&](gmpk::KParams& K) -> gmp_status {
+    K.gbins = h->gbins.as<unsigned long long>();
+    K.own = h->own.as<double>();
+    K.vir_c = vir ? h->vir_c.as<double>() : nullptr;
+    GMP_CK(cudaMemsetAsync(K.gbins, 0, sizeof(unsigned long long) * 3 * gmpk::kGradBins * N, st), "memset bins");
+    GMP_CK(cudaMemsetAsync(K.own, 0, sizeof(double) * 3 * N, st), "memset own");
+    if (vir) GMP_CK(cudaMemsetAsync(K.vir_c, 0, sizeof(double) * 9 * N, st), "memset vir_c");
+    return GMP_OK;
+  };
+  auto vjp_end = [&](const gmpk::KParams& K) -> gmp_status {
+    GMP_CK(gmp_launch_grad_bins_finish(N, K.gbins, K.own, h->grad_acc.as<double>(), st, h->sm_count, &h->launches),
+           "gradient sums");
+    if (vir)
+      GMP_CK(gmp_launch_virial_reduce(n_struct, h->atom_off.as<int64_t>(), K.vir_c, vir, st, h->sm_count,
+                                      &h->launches),
+             "virial sums");
+    return GMP_OK;
+  };
   auto seq = [&](bool capture) -> gmp_status {
   gmp_status q = build_neighbors(h, n_struct, io.pos, io.species, N, st, false, capture);
   if (q != GMP_OK) return q;
@@ -1172,7 +1200,9 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
       K.grad_feat = gf;
       K.grad_acc = h->grad_acc.as<double>();
       GMP_CK(prof_mark(h, 2, true, st), "profile");
+      if ((q = vjp_begin(K)) != GMP_OK) return q;
       GMP_CK(launch_compute(pd.L, GMP_KIND_VJP, pd.NS, K, pd.fused, st, h->sm_count, &h->launches), "vjp");
+      if ((q = vjp_end(K)) != GMP_OK) return q;
       GMP_CK(prof_mark(h, 2, false, st), "profile");
       pending = true;
       continue;
@@ -1210,9 +1240,11 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     K.virial = vir;
     K.center_struct = h->struct_of.as<int32_t>();
     GMP_CK(prof_mark(h, 2, true, st), "profile");
+    if ((q = vjp_begin(K)) != GMP_OK) return q;
     GMP_CK(launch_compute(pd.L, vir ? GMP_KIND_BACKWARD_VIRIAL : GMP_KIND_BACKWARD, pd.NS, K, pd.bwd, st,
                           h->sm_count, &h->launches),
            "backward");
+    if ((q = vjp_end(K)) != GMP_OK) return q;
     GMP_CK(prof_mark(h, 2, false, st), "profile");
   }
   if (feat && pending) {

@@ -308,6 +308,13 @@ cudaError_t gmp_launch_jacobian_count(int64_t N, const int64_t* nbr_beg, const i
                                       int64_t* launches);
 cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* grad_pos,
                                    cudaStream_t stream, int64_t* launches);
+// grad_acc[j] += own[j] + the value of j's exact fixed-point bins (filled by
+// the backward kernels without float atomics; 12 per atom and component).
+cudaError_t gmp_launch_grad_bins_finish(int64_t N, const unsigned long long* bins, const double* own,
+                                        double* grad_acc, cudaStream_t stream, int sm_count, int64_t* launches);
+// virial[s] += sum of vir_c over the centers atom_off[s] .. atom_off[s+1]-1 (fixed order).
+cudaError_t gmp_launch_virial_reduce(int n_struct, const int64_t* atom_off, const double* vir_c, double* virial,
+                                     cudaStream_t stream, int sm_count, int64_t* launches);
 // Double-float recomputation of the flagged features: the queue (count
 // entries center << 16 | column, at most cap) and, when it overflowed, the
 // set bits of `bits` ([n_centers] x flag_words words, bit col % 32 of word

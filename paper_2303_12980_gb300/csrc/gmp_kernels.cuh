@@ -157,6 +157,14 @@ struct KParams {
   int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
   float flag_tau;             // flag when f < flag_tau * l! (2l-1)!! B^2
+  // VJP without float atomics: the gradient of each pair onto its neighbor
+  // atom j is added exactly, as an integer, into one of kGradBins
+  // fixed-point bins of (j, component) (gbins, see bin_add); each center's
+  // own term goes to own[3 i + v] and its strain-derivative sums to
+  // vir_c[9 i + v].  gmp_launch_grad_bins_finish then forms the gradient.
+  unsigned long long* gbins;
+  double* own;
+  double* vir_c;
 };
 
 // l! (2l-1)!!: with B = sum_pairs |R_{l,s}| r^l, the cancellation-free scale
@@ -192,6 +200,30 @@ __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int
 // instead of ~1.5.
 __device__ __forceinline__ float mcsh_r2(float dx, float dy, float dz) {
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Exact, order-independent accumulation of FP32 values.  A finite value is
+// m 2^(e - 150) with m its 24-bit significand and e its biased exponent (1
+// for subnormals).  Bin b = (e - 1) / 24 (0..10) counts in units of
+// 2^(24 b - 149): the value is m << ((e - 1) % 24) < 2^47 of them, an exact
+// integer added with a 64-bit integer atomic, so the bin's total does not
+// depend on the order of the additions; up to 2^16 values per bin stay
+// below 2^63.  Bin 11 collects flags of non-finite values (1 NaN, 2 +inf,
+// 4 -inf).  The bins are combined in a fixed order afterwards.
+constexpr int kGradBins = 12;
+__device__ __forceinline__ void bin_add(unsigned long long* bins, float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned eb = (u >> 23) & 0xffu;
+  if (eb == 0xffu) {
+    atomicOr(bins + 11, (u & 0x7fffffu) ? 1ull : ((u >> 31) ? 4ull : 2ull));
+    return;
+  }
+  const unsigned long long m = eb ? ((u & 0x7fffffu) | 0x800000u) : (u & 0x7fffffu);
+  if (!m) return;
+  const unsigned e = eb ? eb - 1u : 0u;
+  const unsigned b = e / 24u;
+  const unsigned long long x = m << (e - 24u * b);
+  atomicAdd(bins + b, (u >> 31) ? (~x + 1ull) : x);
 }
 
 // Pulls the cache line of a pair record into L1 ahead of its use (no registers held).
@@ -643,25 +675,20 @@ __device__ __forceinline__ void adjoints(const GmpPass& P, const float* __restri
   __syncwarp();
 }
 
-// d/dd of sum_k lam_k R(r^2) S_k(d) pieces for one pair, from
-//   A = sum_k lamd_k S_k, B = sum_k (2l_k+1) lam_k S_k, V = sum_k lam_k S_{k+e}:
-//   grad = d (2 A + B / r^2) - V / r^2      (r^2 > 0)
-// where lam already carries R (and lamd carries dR/dr^2).  At d = 0 only
-// order 1 has a gradient: (lam_x, lam_y, lam_z).
+// d/dd of sum_k lam_k R(r^2) S_k(d) for one pair, from
+//   A = sum_k lamd_k S_k (lamd carries dR/dr^2), B = sum_k (2l_k+1) lam_k S_k,
+//   V = sum_k lam_k S_{k+e}:   grad = d (2 A + B / r^2) - V / r^2   (r^2 > 0)
+// where lam already carries R.  At d = 0 only order 1 has a gradient:
+// (lam_x, lam_y, lam_z).  S1 holds the MCSH values of orders 0..L+1.
 template <int L>
-__device__ __forceinline__ void pair_gradient(const float* lam, const float* lamd, float dx, float dy,
-                                              float dz, float r2, float* g) {
-  float S1[(L + 2) * (L + 2)];
-  GmpMcsh<L + 1>::eval(dx, dy, dz, r2, S1);
-  float A = 0.0f, B = 0.0f;
+__device__ __forceinline__ void pair_gradient(const float* lam, float A, float dx, float dy, float dz, float r2,
+                                              const float* S1, float* g) {
+  float B = 0.0f;
 #pragma unroll
   for (int l = 0; l <= L; ++l) {
     float b = 0.0f;
 #pragma unroll
-    for (int k = l * l; k < (l + 1) * (l + 1); ++k) {
-      A = __fmaf_rn(lamd[k], S1[k], A);
-      b = __fmaf_rn(lam[k], S1[k], b);
-    }
+    for (int k = l * l; k < (l + 1) * (l + 1); ++k) b = __fmaf_rn(lam[k], S1[k], b);
     B = __fmaf_rn((float)(2 * l + 1), b, B);
   }
   float V[3];
@@ -687,8 +714,9 @@ __device__ __forceinline__ void pair_gradient(const float* lam, const float* lam
 // (positions and lattice vectors strained alike move every d to (I+eps) d),
 // each lane's partial sums kept in its column of Wv ([9][32] floats of
 // warp-private shared memory) rather than in registers.
-// PACKED: radial factors on packed FP32 pairs (same results; needs more
-// than the 168 registers of the 12-warp backward launch).
+// PACKED: radial factors on packed FP32 pairs (same results, fewer issue
+// slots; the plain backward kernel uses them, the strain-derivative variant
+// would spill at the 168 registers of the 12-warp launch).
 template <int L, int NS, bool VIRIAL = false, bool PACKED = false>
 __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
@@ -706,9 +734,17 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     int e, j;
     load_pair(K.pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
     if (pp + 32 < M) prefetch_pair(K.pairs + p0 + pp + 32);
-    float lam[SH::NIND], lamd[SH::NIND];
+    // MCSH values of orders 0..L first (order L+1 after the sigma loop):
+    // the sigma loop then contracts them directly, so that only the
+    // radial-weighted adjoints lam (not their derivative counterparts) are
+    // live beside them
+    const float r2c = mcsh_r2(dx, dy, dz);
+    float S[SH::NIND1];
+    GmpMcsh<L>::eval(dx, dy, dz, r2c, S);
+    float lam[SH::NIND];
 #pragma unroll
-    for (int k = 0; k < SH::NIND; ++k) { lam[k] = 0.0f; lamd[k] = 0.0f; }
+    for (int k = 0; k < SH::NIND; ++k) lam[k] = 0.0f;
+    float A = 0.0f;  // sum over sigma and order of dR_l/dr^2 * sum_{k in l} Lam_k S_k
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
@@ -719,10 +755,10 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
-        float Rd[L + 1];  // dR_l/dr^2 = -beta R_{l+1}
-#pragma unroll
-        for (int l = 0; l <= L; ++l) Rd[l] = __fmul_rn(nb, R[u][l + 1]);
         const float* lrow = Lam + (4 * sg + u) * SH::NINDP;
+        float pl[L + 1];
+#pragma unroll
+        for (int l = 0; l <= L; ++l) pl[l] = 0.0f;
         static_for<SH::NINDP / 4>([&](auto cq) {
           constexpr int c4 = decltype(cq)::value;
           const float4 lv4 = *reinterpret_cast<const float4*>(lrow + 4 * c4);
@@ -732,14 +768,20 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
             if constexpr (k < SH::NIND) {
               constexpr int l = order_of(k);
               lam[k] = __fmaf_rn(lv[decltype(tt)::value], R[u][l], lam[k]);
-              lamd[k] = __fmaf_rn(lv[decltype(tt)::value], Rd[l], lamd[k]);
+              pl[l] = __fmaf_rn(lv[decltype(tt)::value], S[k], pl[l]);
             }
           });
         });
+        // dR_l/dr^2 = -beta R_{l+1}: A += -beta sum_l R_{l+1} pl_l
+        float a = 0.0f;
+#pragma unroll
+        for (int l = 0; l <= L; ++l) a = __fmaf_rn(R[u][l + 1], pl[l], a);
+        A = __fmaf_rn(nb, a, A);
       }
     }
+    GmpMcsh<L + 1>::eval_top(dx, dy, dz, r2c, S);
     float g[3];
-    pair_gradient<L>(lam, lamd, dx, dy, dz, mcsh_r2(dx, dy, dz), g);
+    pair_gradient<L>(lam, A, dx, dy, dz, r2c, S, g);
     if (P.want_density && gd != 0.0f) {
       float drho;
       density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
@@ -748,12 +790,16 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
       g[1] = __fmaf_rn(c, dy, g[1]);
       g[2] = __fmaf_rn(c, dz, g[2]);
     }
-    atomicAdd(K.grad_acc + 3 * (int64_t)j + 0, (double)g[0]);
-    atomicAdd(K.grad_acc + 3 * (int64_t)j + 1, (double)g[1]);
-    atomicAdd(K.grad_acc + 3 * (int64_t)j + 2, (double)g[2]);
-    own[0] -= g[0];
-    own[1] -= g[1];
-    own[2] -= g[2];
+    if (j != (int32_t)i) {  // images of the center itself do not move relative to it
+      if (K.gbins) {
+        bin_add(K.gbins + (3 * (int64_t)j + 0) * kGradBins, g[0]);
+        bin_add(K.gbins + (3 * (int64_t)j + 1) * kGradBins, g[1]);
+        bin_add(K.gbins + (3 * (int64_t)j + 2) * kGradBins, g[2]);
+      }
+      own[0] -= g[0];
+      own[1] -= g[1];
+      own[2] -= g[2];
+    }
     if constexpr (VIRIAL) {
       const float d[3] = {dx, dy, dz};
 #pragma unroll
@@ -763,13 +809,12 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     }
   }
   if constexpr (VIRIAL) {
-    double* wrow = K.virial + 9 * (int64_t)K.center_struct[i];
 #pragma unroll
     for (int v = 0; v < 9; ++v) {
       double o = (double)Wv[32 * v + lane];
 #pragma unroll
       for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
-      if (lane == 0) atomicAdd(wrow + v, o);
+      if (lane == 0 && K.vir_c) K.vir_c[9 * i + v] = o;
     }
   }
 #pragma unroll
@@ -777,7 +822,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     double o = (double)own[v];
 #pragma unroll
     for (int s = 16; s; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
-    if (lane == 0) atomicAdd(K.grad_acc + 3 * i + v, o);
+    if (lane == 0 && K.own) K.own[3 * i + v] = o;
   }
 }
 
@@ -839,7 +884,7 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
     const float* grow = K.grad_feat + i * P.F;
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS, VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
+    backward_sweep<L, NS, VIRIAL, !VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
     __syncwarp();
   }
 }

@@ -1,4 +1,5 @@
-// Small helper kernels: structure ids, Jacobian row counts, gradient output.
+// Small helper kernels: structure ids, Jacobian row counts, the
+// order-independent gradient sums, strain-derivative sums, gradient output.
 #include "gmp_internal.cuh"
 
 namespace {
@@ -31,6 +32,54 @@ __global__ void k_jac_count(int64_t N, const int64_t* __restrict__ nbr_beg, cons
     c += __popc(m);
   }
   if (lane == 0) counts[i] = c;
+}
+
+// grad_acc[j] += own[j] + the value of j's fixed-point bins (bin b counts in
+// units of 2^(24 b - 149); added in a fixed order, so the result does not
+// depend on the order in which the bins were filled).  Bin 11 holds flags
+// of non-finite contributions: NaN if any was NaN or infinities of both
+// signs came in, else that infinity.  One thread per (atom, component).
+__global__ void k_grad_bins_finish(int64_t n, const unsigned long long* __restrict__ bins,
+                                   const double* __restrict__ own, double* __restrict__ grad_acc) {
+  constexpr int kBins = 12;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long* bt = bins + t * kBins;
+    const unsigned long long fl = bt[11];
+    double v;
+    if (fl) {
+      v = ((fl & 1ull) || ((fl & 6ull) == 6ull)) ? (double)NAN : ((fl & 2ull) ? (double)INFINITY : -(double)INFINITY);
+    } else {
+      v = 0.0;
+#pragma unroll
+      for (int b = 0; b < 11; ++b) v += ldexp((double)(long long)bt[b], 24 * b - 149);
+    }
+    grad_acc[t] = grad_acc[t] + (own[t] + v);
+  }
+}
+
+// virial[s] += sum over the centers of structure s of vir_c[center] (nine
+// values), one warp per structure, lanes over centers in a fixed order.
+__global__ void k_virial_reduce(int n_struct, const int64_t* __restrict__ atom_off, const double* __restrict__ vir_c,
+                                double* __restrict__ virial) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = w0; s < n_struct; s += nw) {
+    const int64_t a0 = atom_off[s], a1 = atom_off[s + 1];
+    double acc[9];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) acc[v] = 0.0;
+    for (int64_t a = a0 + lane; a < a1; a += 32)
+#pragma unroll
+      for (int v = 0; v < 9; ++v) acc[v] += vir_c[9 * a + v];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) {
+      double x = acc[v];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) virial[9 * s + v] += x;
+    }
+  }
 }
 
 __global__ void k_grad_finish(int64_t n, const double* __restrict__ acc, float* __restrict__ out) {
@@ -67,6 +116,29 @@ cudaError_t gmp_launch_grad_finish(int64_t N, const double* grad_acc, float* gra
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_grad_finish<<<(unsigned)blocks, 256, 0, stream>>>(n, grad_acc, grad_pos);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t gmp_launch_grad_bins_finish(int64_t N, const unsigned long long* bins, const double* own,
+                                        double* grad_acc, cudaStream_t stream, int sm_count, int64_t* launches) {
+  if (N <= 0) return cudaSuccess;
+  const int64_t n = 3 * N;
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  k_grad_bins_finish<<<(unsigned)blocks, 256, 0, stream>>>(n, bins, own, grad_acc);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t gmp_launch_virial_reduce(int n_struct, const int64_t* atom_off, const double* vir_c, double* virial,
+                                     cudaStream_t stream, int sm_count, int64_t* launches) {
+  if (n_struct <= 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)n_struct * 32 + 255) / 256;
+  const int64_t cap = (int64_t)sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  k_virial_reduce<<<(unsigned)blocks, 256, 0, stream>>>(n_struct, atom_off, vir_c, virial);
   ++*launches;
   return cudaGetLastError();
 }
