@@ -130,6 +130,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = synth.workload(args.workload)
+    # A batch of many structures is split across ranks by structure (no
+    # data exchange; strong scaling of the fixed batch); a single structure
+    # runs as one replica per rank (weak scaling).
+    sharded = world > 1 and w.n_struct >= world
+    if sharded:
+        s0, s1 = dist_util.shard_structures(w.atom_off, rank, world)
+        w = dist_util.slice_workload(w, s0, s1)
     N, F_ = w.n_atoms, w.n_features
     Fz = GMPFeaturizer.from_workload(w, device=local_rank)
     pos = torch.from_numpy(w.positions).to(dev)
@@ -155,12 +162,14 @@ def run_ours(args, rank, world, local_rank):
     except Exception as exc:  # diagnostics only
         measured = {"error": str(exc)}
     contraction = None
-    if args.probes:  # the moment contraction, packed FP32 (as run) against tensor-core versions
-        try:
-            from paper_2303_12980_gb300.binding import probe_contraction
-            contraction = probe_contraction(local_rank)
-        except Exception as exc:  # diagnostics only
-            contraction = {"error": str(exc)}
+    if args.probes:  # the moment and adjoint contractions, FP32 (as run) against tensor-core versions
+        from paper_2303_12980_gb300.binding import probe_backward_contraction, probe_contraction
+        contraction = {}
+        for name, fn in (("forward_moments", probe_contraction), ("backward_adjoints", probe_backward_contraction)):
+            try:
+                contraction[name] = fn(local_rank)
+            except Exception as exc:  # diagnostics only
+                contraction[name] = {"error": str(exc)}
 
     for _ in range(args.warmup):
         step()
@@ -241,14 +250,15 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "atoms": N, "structures": w.n_struct, "features": F_,
                    "orders": w.orders, "n_sigmas": len(w.sigmas), "cutoff": w.cutoff, "pairs": pairs,
                    "step": {"vjp": "neighbors + features + VJP (forces), gmp_featurize_vjp",
                             "grad": "neighbors + features + dense Jacobian, gmp_featurize_grad",
                             "features": "neighbors + features, gmp_featurize"}[args.call],
                    "l2": "256 MB buffer written between timed steps (outside the step events)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+                   "parallelism": (f"dp{world}, structures sharded" if sharded else f"replicas{world}")
+                   if world > 1 else "single"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,

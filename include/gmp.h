@@ -313,6 +313,26 @@ gmp_status gmp_probe_peaks(int device, double *fma_tflops, double *fma2_tflops, 
 #define GMP_PROBE_CONTRACT_N 12
 gmp_status gmp_probe_contraction(int device, double *result, int32_t n_result);
 
+/* Measured evaluation of the backward kernel's per-pair adjoint
+ * contraction (paper Examples: the derivatives of the features,
+ * calc_derivatives; per pair lam_k = sum_s Lam[s][k] R_{s,l(k)} and its
+ * radial derivative counterpart, 16 sigmas x 49 components x 2) on the
+ * 5th-generation tensor cores against the FP32 scheme the backward kernel
+ * runs, on seeded data.  tcgen05 version: 128 pairs per tile on the MMA's
+ * M rows (one per tensor-memory lane), K = 16 sigmas, N = 32 columns per
+ * order, kind::tf32 with hi/lo operand splits (3 MMAs per product),
+ * operands in shared memory, accumulators in tensor memory, bounded
+ * mbarrier waits.  Writes GMP_PROBE_BWD_CONTRACT_N doubles into the host
+ * array `result`: [0] FP32 scheme, 10^9 pairs/s; [1] tcgen05, 10^9
+ * pairs/s; [2] [3] FP32 max error of lam / lamd over 128 pairs against
+ * FP64, relative to each sum's cancellation-free scale; [4] [5] the same
+ * for tcgen05; [6] [7] registers per thread of the two kernels; [8]
+ * nonzero if a tcgen05 wait ran out (its results are then incomplete).
+ * Needs no handle; GMP_ERR_CUDA if a launch fails.  The library's kernels
+ * do not use the tcgen05 version. */
+#define GMP_PROBE_BWD_CONTRACT_N 9
+gmp_status gmp_probe_backward_contraction(int device, double *result, int32_t n_result);
+
 #ifdef __cplusplus
 }
 #endif

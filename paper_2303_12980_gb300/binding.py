@@ -30,7 +30,8 @@ _STATUS = {1: "GMP_ERR_INVALID_ARG", 2: "GMP_ERR_CUDA", 3: "GMP_ERR_OOM", 4: "GM
 EXPORTS = ("gmp_create", "gmp_num_features", "gmp_featurize", "gmp_featurize_vjp", "gmp_featurize_vjp_virial",
            "gmp_featurize_grad", "gmp_featurize_grad_centers", "gmp_featurize_points", "gmp_neighbors", "gmp_cutoff", "gmp_set_graph", "gmp_tune", "gmp_tuning_get", "gmp_tuning_set",
            "gmp_sync", "gmp_profile", "gmp_profile_read",
-           "gmp_probe_peaks", "gmp_probe_contraction", "gmp_last_error", "gmp_kernel_launches", "gmp_destroy")
+           "gmp_probe_peaks", "gmp_probe_contraction", "gmp_probe_backward_contraction", "gmp_last_error",
+           "gmp_kernel_launches", "gmp_destroy")
 TUNING_CACHE = os.environ.get("GMP_TUNING_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "gmp_gb300", "tuning.json"))
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         L.gmp_kernel_launches.restype = i64
         L.gmp_probe_peaks.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.gmp_probe_contraction.argtypes = [C.c_int, C.POINTER(C.c_double), i32]
+        L.gmp_probe_backward_contraction.argtypes = [C.c_int, C.POINTER(C.c_double), i32]
         L.gmp_destroy.argtypes = [vp]
         L.gmp_destroy.restype = None
         for name in EXPORTS[:-3]:
@@ -502,6 +504,21 @@ def probe_contraction(device: int = 0) -> dict:
     names = ("fp32", "tf32x3_16w", "tf32x3_8w", "tf32x3_presplit_16w")
     return {n: {"gpairs_per_s": r[k], "max_rel_err": r[4 + k], "registers": int(r[8 + k])}
             for k, n in enumerate(names)}
+
+
+def probe_backward_contraction(device: int = 0) -> dict:
+    """The backward kernel's per-pair adjoint contraction, FP32 as the
+    kernel runs it against a tcgen05 (kind::tf32, hi/lo split) version
+    (gmp_probe_backward_contraction): pairs/s, errors relative to the
+    cancellation-free scale, registers."""
+    L = load_library()
+    r = (C.c_double * 9)()
+    st = L.gmp_probe_backward_contraction(int(device), r, 9)
+    if st != GMP_OK:
+        raise GMPError(st, "gmp_probe_backward_contraction failed")
+    return {"fp32": {"gpairs_per_s": r[0], "max_rel_err_lam": r[2], "max_rel_err_lamd": r[3], "registers": int(r[6])},
+            "tcgen05_tf32x3": {"gpairs_per_s": r[1], "max_rel_err_lam": r[4], "max_rel_err_lamd": r[5],
+                               "registers": int(r[7]), "wait_timed_out": bool(r[8])}}
 
 
 def gmp_features(pos, featurizer, species, atom_off, cell, pbc):
