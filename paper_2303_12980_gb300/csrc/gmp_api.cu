@@ -519,6 +519,10 @@ gmp_status build_neighbors(gmp_ctx* h, int32_t S, const double* pos, const int32
 // in double-float arithmetic (see gmp_refine.cu and the flag test in
 // write_features).
 constexpr float kFlagTau = 3e-4f;
+// ... and above this fraction of the lower bound l! (2l-1)!! B^2 / 3^l of
+// the feature's cancellation-free scale (below it the FP32 value already
+// meets the absolute floor; see write_features).
+constexpr float kFlagLow = 1e-10f;
 
 int64_t flag_capacity(int64_t N) { return 4 * N + 1024; }
 // 64-bit count of flagged features (bytes 24..31 of the scalar block)
@@ -543,6 +547,7 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   K.pair_cap = h->capturing ? h->cap_pairs : h->P;
   K.sig0 = 16 * pass_index;
   K.flag_tau = kFlagTau;
+  K.flag_low = kFlagLow;
   return K;
 }
 

@@ -156,7 +156,8 @@ struct KParams {
   int flag_words;
   int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
-  float flag_tau;             // flag when f < flag_tau * l! (2l-1)!! B^2
+  float flag_tau;             // flag when flag_low * l! (2l-1)!! B^2 / 3^l <= f < flag_tau * l! (2l-1)!! B^2
+  float flag_low;
   // VJP without float atomics: the gradient of each pair onto its neighbor
   // atom j is added exactly, as an integer, into one of kGradBins
   // fixed-point bins of (j, component) (gbins, see bin_add); each center's
@@ -175,6 +176,14 @@ struct KParams {
 __host__ __device__ constexpr float flag_scale(int l) {
   return l == 0 ? 1.0f : l == 1 ? 1.0f : l == 2 ? 6.0f : l == 3 ? 90.0f : l == 4 ? 2520.0f
        : l == 5 ? 113400.0f : 7484400.0f;
+}
+// 3^-l.  From below, F_abs >= l! (2l-1)!! B^2 / 3^l: by Cauchy-Schwarz over
+// the components, F_abs >= (sum_c w_c A_c)^2 / sum_c w_c with sum_c w_c =
+// 3^l, and sum_c w_c A_c = sum_pairs |R| sum_c w_c |S_c| >= sum_pairs |R|
+// sqrt(sum_c w_c S_c^2) = sqrt(l! (2l-1)!!) B, since w_c >= 1.
+__host__ __device__ constexpr float inv_pow3(int l) {
+  return l == 0 ? 1.0f : l == 1 ? 1.0f / 3.0f : l == 2 ? 1.0f / 9.0f : l == 3 ? 1.0f / 27.0f : l == 4 ? 1.0f / 81.0f
+       : l == 5 ? 1.0f / 243.0f : 1.0f / 729.0f;
 }
 
 __device__ __forceinline__ void load_pair(const GmpPair* __restrict__ pairs, int64_t idx, float& dx,
@@ -609,8 +618,18 @@ __device__ __forceinline__ void write_features(const KParams& K, int64_t i, cons
     const int l = P.ord_l[o];
     const float f = gmp_mcsh_invariant(l, Mu + s * SH::NIND + l * l);
     frow[P.ord_col[o] + s] = f;
+    // Refined: the band where FP32 moments (errors of a few 2^-24 of their
+    // cancellation-free scales A_c) cannot hold the relative bound.  Below
+    // it the feature is so small against F_abs that its FP32 value is
+    // already within the absolute floor 1e-11 F_abs: with moment errors
+    // eps A_c and a computed f below t F_abs, the true f is below
+    // (sqrt(t) + eps)^2 F_abs and the computed one off by at most
+    // (2 sqrt(t) eps + 3 eps^2) F_abs, 6.3e-12 F_abs for t = 1e-10 and
+    // eps = 3e-7 (5 units of 2^-24).  Features that vanish by symmetry
+    // (perfect crystals) land there and are not refined.
     const float B = Mu[NS * SH::NIND + s * (L + 1) + l];
-    if (K.flags && f < __fmul_rn(__fmul_rn(K.flag_tau, flag_scale(l)), __fmul_rn(B, B))) {
+    const float U = __fmul_rn(flag_scale(l), __fmul_rn(B, B));  // >= F_abs
+    if (K.flags && f < __fmul_rn(K.flag_tau, U) && !(f < __fmul_rn(__fmul_rn(K.flag_low, inv_pow3(l)), U))) {
       const int col = P.ord_col[o] + s;
       const unsigned long long slot = atomicAdd(K.flag_count, 1ull);
       if (slot < (unsigned long long)K.flag_cap)

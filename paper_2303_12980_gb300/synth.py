@@ -254,6 +254,19 @@ def fcc_slab262k(seed: int = 1004, reps=(32, 32, 64)) -> Workload:
                    [0, 1, 2, 3, 4, 5, 6], np.geomspace(0.05, 1.5, 16), 8.0)
 
 
+def fcc_perfect262k(seed: int = 1004, reps=(32, 32, 64)) -> Workload:
+    """A perfect one-element FCC crystal, a = 3.9 A, 32x32x64 conventional
+    cells (262,144 atoms), periodic, no jitter: every site is equivalent and
+    the orders that vanish by cubic symmetry vanish at every center.  The
+    slab's element table (first element only) and probes."""
+    rng = np.random.default_rng(seed)
+    table = gaussian_table(rng, [3, 4, 5, 6, 7, 8], 6)
+    pos, cell = fcc_supercell(rng, 3.9, reps, 0.0)
+    species = np.zeros(pos.shape[0], np.int32)
+    return _single("fcc_perfect262k", pos, cell, [1, 1, 1], species, table,
+                   [0, 1, 2, 3, 4, 5, 6], np.geomspace(0.05, 1.5, 16), 8.0)
+
+
 def fcc_slab32k(seed: int = 1004) -> Workload:
     """The alloy slab at 1/8 size (16x16x32 conventional cells, 32,768
     atoms), same probes; the small case for kernel profiling."""
@@ -267,6 +280,7 @@ WORKLOADS = {
     "batched10k": batched10k,
     "fcc_slab262k": fcc_slab262k,
     "fcc_slab32k": fcc_slab32k,
+    "fcc_perfect262k": fcc_perfect262k,
 }
 
 

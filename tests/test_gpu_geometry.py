@@ -140,8 +140,10 @@ def test_image_index_limit_reported(torch):
 def test_near_symmetric_crystals(torch, oracle_mod):
     """One-element FCC crystals, perfect and with 1e-4 / 1e-3 A jitter:
     by symmetry the orders 1, 2, 3 and 5 vanish or nearly vanish at every
-    center, so most of each center's 112 features are ill-conditioned in
-    FP32 and take the double-float recomputation (64 per center)."""
+    center.  With jitter most of each center's 112 features are
+    ill-conditioned in FP32 and take the double-float recomputation; in the
+    perfect crystal they vanish below the refinement band and keep their
+    FP32 values.  Features and position gradients against the oracle."""
     base = synth.fcc_slab262k(reps=(3, 3, 3))
     rng = np.random.default_rng(3)
     parts = []
@@ -158,3 +160,14 @@ def test_near_symmetric_crystals(torch, oracle_mod):
     ref, fabs = oracle_mod.features(w, centers, want_abs=True)
     err = feature_errors(f.cpu().numpy()[centers], ref, fabs)
     assert err.max() <= FEAT_TOL, err.max()
+    # the position gradient too: features that vanish by symmetry below the
+    # refinement band keep their FP32 moments, whose adjoints are then noise
+    # of the size of their rounding
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=9)
+    _, gp = F.featurize_vjp(torch.from_numpy(w.positions).cuda(), torch.from_numpy(w.species).cuda(),
+                            w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    atoms = np.array([0, 77, 255, 300, 555, 700])
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    assert gerr.max() <= GRAD_TOL, gerr.max()
