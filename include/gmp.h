@@ -219,7 +219,8 @@ gmp_status gmp_neighbors(gmp_handle h, int32_t n_struct, const int64_t *atom_off
  * The call runs on `stream` and synchronises it before returning (to read
  * the device error word).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current
- * and keeps it for the life of the process.  A device reset
+ * and keeps it for the life of the process; make that first call on a
+ * device before any stream capture.  A device reset
  * (cudaDeviceReset) after that first call would leave the kept address
  * stale: it is not supported.  All calls share the one
  * array and each call resets what must start at zero, so calls that overlap

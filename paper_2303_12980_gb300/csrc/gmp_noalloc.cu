@@ -99,7 +99,8 @@ extern "C" gmp_status gmp_neighbor_counts_noalloc(int32_t n_atoms, const double*
   if (!pos || !counts || !cell || !pbc) return report(GMP_ERR_INVALID_ARG, "pos, cell, pbc and counts are required");
   cudaStream_t st = (cudaStream_t)stream;
 
-  // per-device set-up: the device address of the scratch array
+  // per-device set-up, done by the first call on each device (which should
+  // come before any stream capture): the device address of the scratch array
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
