@@ -76,6 +76,40 @@ __host__ __device__ constexpr int order_of(int k) {
   while ((l + 1) * (l + 1) <= k) ++l;
   return l;
 }
+// The same for a chunk width cw of 4 (above) or 2.  With cw = 2 an order l
+// takes l + 1 chunks: its 2l + 1 components and, in the last slot, r^l.
+__host__ __device__ constexpr int chunks_of_order_w(int l, int cw) { return cw == 4 ? (l + 2) / 2 : l + 1; }
+__host__ __device__ constexpr int nchunks_w(int L, int cw) {
+  int n = 0;
+  for (int l = 0; l <= L; ++l) n += chunks_of_order_w(l, cw);
+  return n;
+}
+__host__ __device__ constexpr int chunk_l_w(int c, int cw) {
+  int l = 0;
+  while (c >= chunks_of_order_w(l, cw)) { c -= chunks_of_order_w(l, cw); ++l; }
+  return l;
+}
+__host__ __device__ constexpr int chunk_k0_w(int c, int cw) {
+  int l = 0;
+  while (c >= chunks_of_order_w(l, cw)) { c -= chunks_of_order_w(l, cw); ++l; }
+  return l * l + cw * c;
+}
+// Chunk width of the moment contraction for orders 0..L and NS sigmas: the
+// one with fewer warp instructions per pair (items of 4 sigmas x cw
+// components, 32 per warp pass; an item issues 2 cw packed FMAs and two
+// shared loads per pair), 2 on a tie (fewer accumulator registers).
+__host__ __device__ constexpr int pick_cw(int L, int NS) {
+  const int q4 = ((NS / 4) * nchunks_w(L, 4) + 31) / 32, q2 = ((NS / 4) * nchunks_w(L, 2) + 31) / 32;
+  return q4 * 10 < q2 * 6 ? 4 : 2;
+}
+// smallest m >= n with m / 2 odd (conflict-free 8-byte stores by 16
+// consecutive lanes at a stride of m floats)
+__host__ __device__ constexpr int odd2(int n) {
+  int h = (n + 1) / 2;
+  if ((h & 1) == 0) ++h;
+  return 2 * h;
+}
+
 // float count rounded to a multiple of 4 holding an odd number of float4s
 // (conflict-free 16-byte stores by 8 consecutive lanes)
 __host__ __device__ constexpr int odd4(int n) {
@@ -88,17 +122,22 @@ template <int L, int NS, int TILE_ = 16>
 struct Shape {
   static constexpr int NIND = (L + 1) * (L + 1);   // independent components, orders 0..L
   static constexpr int NIND1 = (L + 2) * (L + 2);  // ... orders 0..L+1
+  static constexpr int NINDP = (NIND + 3) / 4 * 4; // padded row of per-sigma vectors
   static constexpr int NSB = NS / 4;
-  static constexpr int NCH = nchunks(L);
+  static constexpr int CW = pick_cw(L, NS);        // components per contraction item
+  static constexpr int NCH = nchunks_w(L, CW);
   static constexpr int NITEM = NSB * NCH;
   static constexpr int Q = (NITEM + 31) / 32;
-  static constexpr int RL4 = (L + 1 + 3) / 4 * 4;  // r^l, l = 0..L, after the S chunks (mixed signs)
+  // cw = 4: r^l, l = 0..L, after the S chunks (mixed signs); cw = 2 keeps
+  // r^l in the last slot of every order
+  static constexpr int RL4 = CW == 4 ? (L + 1 + 3) / 4 * 4 : 0;
   static constexpr int RSTR = odd4((L + 1) * NS);
-  static constexpr int SSTR = odd4(NCH * 4 + RL4);
   static constexpr int TILE = TILE_;               // pairs staged per tile: 16 (2 lanes per pair) or 32
+  static constexpr int SSTR = CW == 4 ? odd4(NCH * 4 + RL4)
+                                      : odd2(NCH * 2 > (NS * NINDP + TILE_ - 1) / TILE_ ? NCH * 2
+                                                                                        : (NS * NINDP + TILE_ - 1) / TILE_);
   static constexpr int FOLD = 16;                  // pairs per FP32 partial before the TwoSum fold
   static_assert(TILE_ == 16 || TILE_ == 32, "tile of 16 or 32 pairs");
-  static constexpr int NINDP = (NIND + 3) / 4 * 4; // padded row of per-sigma vectors
   static constexpr int WARP_FLOATS = TILE * RSTR + TILE * SSTR;
   static_assert(NS * NIND + NS * (L + 1) <= TILE * RSTR, "moments and bounds must fit the R tile");
   static_assert(NS * NINDP <= TILE * SSTR, "adjoints must fit the S tile");
@@ -407,10 +446,14 @@ __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_r
 // compensated pair) in Mu[s * NIND + k] and the conditioning bound
 // B_{l,s} = sum_pairs |R_{l,s}| r^l in Mu[NS * NIND + s * (L+1) + l]
 // (warp-private shared memory), and returns the density (all lanes).
-// The last chunk of every order has a free fourth slot (2l+1 = 1 mod 4 or
-// 3 mod 4); with non-negative density coefficients (R >= 0) that slot of the
+// The contraction runs over items of 4 sigmas x CW components (CW = 4 or
+// 2, whichever the shape fills the warp's lanes with in fewer
+// instructions).  The last chunk of every order has a free last slot (2l+1
+// is odd); with non-negative density coefficients (R >= 0) that slot of the
 // S row holds r^l, so the moment accumulator of the slot is B itself.  With
-// mixed signs the slot holds 0 and B is accumulated from |R| explicitly.
+// mixed signs B is accumulated from |R| explicitly (CW = 4: the slot holds 0
+// and a separate loop reads r^l after the chunks; CW = 2: the slot holds r^l
+// and its accumulator takes |R|).
 template <int L, int NS, int TILE = 16>
 __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens,
@@ -421,12 +464,13 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
                                                const int (&it_ch)[Shape<L, NS>::Q],
                                                const bool (&it_ok)[Shape<L, NS>::Q]) {
   using SH = Shape<L, NS, TILE>;
+  constexpr int CW = SH::CW;
   const int lane = threadIdx.x & 31;
-  float hi[SH::Q][16], lo[SH::Q][16];
+  float hi[SH::Q][4 * CW], lo[SH::Q][4 * CW];
 #pragma unroll
   for (int q = 0; q < SH::Q; ++q)
 #pragma unroll
-    for (int v = 0; v < 16; ++v) { hi[q][v] = 0.0f; lo[q][v] = 0.0f; }
+    for (int v = 0; v < 4 * CW; ++v) { hi[q][v] = 0.0f; lo[q][v] = 0.0f; }
   float rho_hi = 0.0f, rho_lo = 0.0f;
   const bool mixed = P.mixed_sign != 0;
 
@@ -446,46 +490,65 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       load_pair(pairs, p0 + base + pl, dx, dy, dz, r2h, r2l, e, j);
       if (half == 0 && base + SH::TILE + pl < M) prefetch_pair(pairs + p0 + base + SH::TILE + pl);
       float* srow = St + pl * SH::SSTR;
-      if (half == 0) {  // MCSH components; r^l in the free slot of each order's last chunk
-        float S[SH::NIND];
-        GmpMcsh<L>::eval(dx, dy, dz, mcsh_r2(dx, dy, dz), S);
-        static_for<SH::NCH>([&](auto cc) {
-          constexpr int c = decltype(cc)::value;
-          constexpr int k0 = chunk_k0(c);
-          constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
-          if constexpr (k0 + 4 < kend + 1 && k0 + 3 < kend) {  // full chunk
-            *reinterpret_cast<float4*>(srow + 4 * c) = make_float4(S[k0], S[k0 + 1], S[k0 + 2], S[k0 + 3]);
-          } else if constexpr (k0 + 1 == kend) {  // last chunk, one component: .y = 0
-            *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], 0.0f);
-          } else {  // last chunk, three components
-            *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], S[(k0 + 1 < kend) ? k0 + 1 : k0]);
-            srow[4 * c + 2] = S[(k0 + 2 < kend) ? k0 + 2 : k0];
-          }
-        });
-      }
-      if (LPP == 1 || half == 1) {  // free slots of the last chunks: r^l (0 with mixed signs)
-        const float r = __fsqrt_rn(r2h);
-        float rpow = mixed ? 0.0f : 1.0f;
-        static_for<L + 1>([&](auto ll) {
-          constexpr int l = decltype(ll)::value;
-          constexpr int c = last_chunk(l);
-          if constexpr (chunk_k0(c) + 1 == (l + 1) * (l + 1))
-            *reinterpret_cast<float2*>(srow + 4 * c + 2) = make_float2(0.0f, rpow);
-          else
-            srow[4 * c + 3] = rpow;
-          rpow = __fmul_rn(rpow, r);
-        });
-      }
-      if (mixed && (LPP == 1 || half == 1)) {  // r^l for the explicit |R| bound
-        const float r = __fsqrt_rn(r2h);
-        float rl[SH::RL4];
-        rl[0] = 1.0f;
+      if constexpr (CW == 2) {
+        if (half == 0) {  // MCSH components, then r^l in the last slot of each order
+          float S[SH::NIND];
+          GmpMcsh<L>::eval(dx, dy, dz, mcsh_r2(dx, dy, dz), S);
+          const float r = __fsqrt_rn(r2h);
+          float rpow = 1.0f;
+          static_for<L + 1>([&](auto ll) {
+            constexpr int l = decltype(ll)::value;
+            static_for<l + 1>([&](auto cc) {
+              constexpr int c = decltype(cc)::value;
+              constexpr int k = l * l + 2 * c;
+              *reinterpret_cast<float2*>(srow + l * (l + 1) + 2 * c) =
+                  make_float2(S[k], c == l ? rpow : S[c == l ? k : k + 1]);
+            });
+            rpow = __fmul_rn(rpow, r);
+          });
+        }
+      } else {
+        if (half == 0) {  // MCSH components; r^l in the free slot of each order's last chunk
+          float S[SH::NIND];
+          GmpMcsh<L>::eval(dx, dy, dz, mcsh_r2(dx, dy, dz), S);
+          static_for<SH::NCH>([&](auto cc) {
+            constexpr int c = decltype(cc)::value;
+            constexpr int k0 = chunk_k0(c);
+            constexpr int kend = (chunk_l(c) + 1) * (chunk_l(c) + 1);
+            if constexpr (k0 + 4 < kend + 1 && k0 + 3 < kend) {  // full chunk
+              *reinterpret_cast<float4*>(srow + 4 * c) = make_float4(S[k0], S[k0 + 1], S[k0 + 2], S[k0 + 3]);
+            } else if constexpr (k0 + 1 == kend) {  // last chunk, one component: .y = 0
+              *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], 0.0f);
+            } else {  // last chunk, three components
+              *reinterpret_cast<float2*>(srow + 4 * c) = make_float2(S[k0], S[(k0 + 1 < kend) ? k0 + 1 : k0]);
+              srow[4 * c + 2] = S[(k0 + 2 < kend) ? k0 + 2 : k0];
+            }
+          });
+        }
+        if (LPP == 1 || half == 1) {  // free slots of the last chunks: r^l (0 with mixed signs)
+          const float r = __fsqrt_rn(r2h);
+          float rpow = mixed ? 0.0f : 1.0f;
+          static_for<L + 1>([&](auto ll) {
+            constexpr int l = decltype(ll)::value;
+            constexpr int c = last_chunk(l);
+            if constexpr (chunk_k0(c) + 1 == (l + 1) * (l + 1))
+              *reinterpret_cast<float2*>(srow + 4 * c + 2) = make_float2(0.0f, rpow);
+            else
+              srow[4 * c + 3] = rpow;
+            rpow = __fmul_rn(rpow, r);
+          });
+        }
+        if (mixed && (LPP == 1 || half == 1)) {  // r^l for the explicit |R| bound
+          const float r = __fsqrt_rn(r2h);
+          float rl[SH::RL4];
+          rl[0] = 1.0f;
 #pragma unroll
-        for (int l = 1; l < SH::RL4; ++l) rl[l] = __fmul_rn(rl[l - 1], r);
+          for (int l = 1; l < SH::RL4; ++l) rl[l] = __fmul_rn(rl[l - 1], r);
 #pragma unroll
-        for (int c = 0; c < SH::RL4 / 4; ++c)
-          *reinterpret_cast<float4*>(srow + 4 * SH::NCH + 4 * c) =
-              make_float4(rl[4 * c], rl[4 * c + 1], rl[4 * c + 2], rl[4 * c + 3]);
+          for (int c = 0; c < SH::RL4 / 4; ++c)
+            *reinterpret_cast<float4*>(srow + 4 * SH::NCH + 4 * c) =
+                make_float4(rl[4 * c], rl[4 * c + 1], rl[4 * c + 2], rl[4 * c + 3]);
+        }
       }
       const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
       float* rrow = Rt + pl * SH::RSTR;
@@ -504,46 +567,72 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
       }
     }
     __syncwarp();
-    // ---- phase 2: lane = (4 sigmas) x (4 components) blocks; FP32 partials
+    // ---- phase 2: lane = (4 sigmas) x (CW components) blocks; FP32 partials
     // over FOLD pairs, folded into (hi, lo) by TwoSum
 #pragma unroll
     for (int q = 0; q < SH::Q; ++q) {
       if (!it_ok[q]) continue;
       const float* rp = Rt + it_l[q] * NS + 4 * it_sb[q];
-      const float* sp = St + 4 * it_ch[q];
-      if (mixed && chunk_k0(it_ch[q]) + 4 >= (it_l[q] + 1) * (it_l[q] + 1)) {
-        // last chunk of order l, mixed signs: B from |R| into the free slot
-        const float* rlp = St + 4 * SH::NCH + it_l[q];
-        for (int pp = 0; pp < np; ++pp) {
-          const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
-          const float rl = rlp[pp * SH::SSTR];
-          hi[q][3] = __fmaf_rn(fabsf(r.x), rl, hi[q][3]);
-          hi[q][7] = __fmaf_rn(fabsf(r.y), rl, hi[q][7]);
-          hi[q][11] = __fmaf_rn(fabsf(r.z), rl, hi[q][11]);
-          hi[q][15] = __fmaf_rn(fabsf(r.w), rl, hi[q][15]);
+      const float* sp = St + CW * it_ch[q];
+      // mixed signs, last chunk of order l: its last slot sums the bound B from |R|
+      const bool mixed_last = mixed && chunk_k0_w(it_ch[q], CW) + CW >= (it_l[q] + 1) * (it_l[q] + 1);
+      if constexpr (CW == 4) {
+        if (mixed_last) {
+          // the free slot holds 0: B from |R| r^l, r^l read after the chunks
+          const float* rlp = St + 4 * SH::NCH + it_l[q];
+          for (int pp = 0; pp < np; ++pp) {
+            const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+            const float rl = rlp[pp * SH::SSTR];
+            hi[q][3] = __fmaf_rn(fabsf(r.x), rl, hi[q][3]);
+            hi[q][7] = __fmaf_rn(fabsf(r.y), rl, hi[q][7]);
+            hi[q][11] = __fmaf_rn(fabsf(r.z), rl, hi[q][11]);
+            hi[q][15] = __fmaf_rn(fabsf(r.w), rl, hi[q][15]);
+          }
         }
       }
       for (int b0 = 0; b0 < np; b0 += SH::FOLD) {
         const int b1 = min(np, b0 + SH::FOLD);
-        // acc2[2u + h] = components (2h, 2h+1) of sigma u, as packed pairs
-        float2 acc2[8];
+        // acc2[v]: components (2h, 2h+1) of sigma u as a packed pair, v = (CW / 2) u + h
+        float2 acc2[2 * CW];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc2[v] = make_float2(0.0f, 0.0f);
+        for (int v = 0; v < 2 * CW; ++v) acc2[v] = make_float2(0.0f, 0.0f);
+        if constexpr (CW == 4) {
 #pragma unroll 4
-        for (int pp = b0; pp < b1; ++pp) {
-          const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
-          const float4 s = *reinterpret_cast<const float4*>(sp + pp * SH::SSTR);
-          const float rv[4] = {r.x, r.y, r.z, r.w};
-          const float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
+          for (int pp = b0; pp < b1; ++pp) {
+            const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+            const float4 s = *reinterpret_cast<const float4*>(sp + pp * SH::SSTR);
+            const float rv[4] = {r.x, r.y, r.z, r.w};
+            const float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float2 ru = make_float2(rv[u], rv[u]);
-            acc2[2 * u] = gmp_fma2(ru, s01, acc2[2 * u]);
-            acc2[2 * u + 1] = gmp_fma2(ru, s23, acc2[2 * u + 1]);
+            for (int u = 0; u < 4; ++u) {
+              const float2 ru = make_float2(rv[u], rv[u]);
+              acc2[2 * u] = gmp_fma2(ru, s01, acc2[2 * u]);
+              acc2[2 * u + 1] = gmp_fma2(ru, s23, acc2[2 * u + 1]);
+            }
+          }
+        } else if (!mixed_last) {
+#pragma unroll 4
+          for (int pp = b0; pp < b1; ++pp) {
+            const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+            const float2 s = *reinterpret_cast<const float2*>(sp + pp * SH::SSTR);
+            const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc2[u] = gmp_fma2(make_float2(rv[u], rv[u]), s, acc2[u]);
+          }
+        } else {  // the r^l slot takes |R|, so that it sums B
+          for (int pp = b0; pp < b1; ++pp) {
+            const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
+            const float2 s = *reinterpret_cast<const float2*>(sp + pp * SH::SSTR);
+            const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              acc2[u].x = __fmaf_rn(rv[u], s.x, acc2[u].x);
+              acc2[u].y = __fmaf_rn(fabsf(rv[u]), s.y, acc2[u].y);
+            }
           }
         }
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < 2 * CW; ++v) {
           float2 l2 = make_float2(lo[q][2 * v], lo[q][2 * v + 1]);
           const float2 sm = gmp_two_sum2(make_float2(hi[q][2 * v], hi[q][2 * v + 1]), acc2[v], l2);
           hi[q][2 * v] = sm.x;
@@ -561,16 +650,18 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
     if (!it_ok[q]) continue;
     const int l = it_l[q];
     const int kend = (l + 1) * (l + 1);
-    const int kbase = chunk_k0(it_ch[q]);
+    const int kbase = chunk_k0_w(it_ch[q], CW);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (kbase + c < kend) Mu[(4 * it_sb[q] + u) * SH::NIND + kbase + c] = __fadd_rn(hi[q][4 * u + c], lo[q][4 * u + c]);
-    if (kbase + 4 >= kend)  // last chunk: the free slot holds B
+      for (int c = 0; c < CW; ++c)
+        if (kbase + c < kend)
+          Mu[(4 * it_sb[q] + u) * SH::NIND + kbase + c] = __fadd_rn(hi[q][CW * u + c], lo[q][CW * u + c]);
+    if (kbase + CW >= kend)  // last chunk: the last slot holds B
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] = __fadd_rn(hi[q][4 * u + 3], lo[q][4 * u + 3]);
+        Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] =
+            __fadd_rn(hi[q][CW * u + CW - 1], lo[q][CW * u + CW - 1]);
   }
   // density: warp total
   float rho = __fadd_rn(rho_hi, rho_lo);
@@ -594,7 +685,7 @@ __device__ __forceinline__ void setup_items(int (&it_l)[Shape<L, NS>::Q], int (&
     // of S values across sigma blocks -> broadcast-friendly loads
     it_sb[q] = it % SH::NSB;
     it_ch[q] = it / SH::NSB;
-    it_l[q] = chunk_l(it_ch[q]);
+    it_l[q] = chunk_l_w(it_ch[q], SH::CW);
   }
 }
 
