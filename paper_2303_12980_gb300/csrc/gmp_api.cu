@@ -102,10 +102,9 @@ struct gmp_ctx {
   DevBuf mu;     // per-center moments between the forward and backward kernels
   DevBuf ktab;   // double-float radial constants [n_el][n_sigmas][kmax][16] for the refinement kernel
   DevBuf exptab; // [64] 2^(-j/64) as double-floats (the refinement's exponential)
-  DevBuf flagq;     // queued ill-conditioned features (center << 16 | column)
-  DevBuf flagbits;  // the rest when the queue is full: [N][flag_words] bitmask
+  DevBuf flagq;     // queued ill-conditioned features, one entry per (center, order)
   DevBuf colinfo;   // per feature column: (order << 16) | sigma, -1 for the density
-  int flag_words = 1;
+  int n_ord_pos = 1;  // orders >= 0: refine queue entries per center and pass
   DevBuf stage_pos, stage_species, stage_feat, stage_gradf, stage_gradp, stage_virial;
   DevBuf pt_off, pt_struct, pt_xh, pt_xl, pt_rng, pt_y, stage_pts;  // reference points
   int64_t P = 0;  // pairs of the last neighbor build
@@ -524,11 +523,12 @@ constexpr float kFlagTau = 3e-4f;
 // meets the absolute floor; see write_features).
 constexpr float kFlagLow = 1e-10f;
 
-int64_t flag_capacity(int64_t N) { return 4 * N + 1024; }
-// 64-bit count of flagged features (bytes 24..31 of the scalar block)
-unsigned long long* flag_counter(gmp_ctx* h) {
-  return reinterpret_cast<unsigned long long*>(h->scalars.as<char>() + 24);
-}
+// Refinement queues, one per requested order: a pass queues at most one
+// entry per (center, order).  The flag buffer holds 8 counts, then the
+// queues.
+int64_t flag_capacity(const gmp_ctx* h, int64_t N) { (void)h; return N + 1024; }
+unsigned long long* flag_counter(gmp_ctx* h) { return h->flagq.as<unsigned long long>(); }
+unsigned long long* flag_queues(gmp_ctx* h) { return h->flagq.as<unsigned long long>() + 8; }
 
 gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_t N) {
   gmpk::KParams K;
@@ -539,11 +539,9 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   K.nbr_end = h->rng_mode ? h->nbr_rng.as<int64_t>() + N : h->nbr_off.as<int64_t>() + 1;
   K.pairs = h->pairs.as<GmpPair>();
   K.counter = reinterpret_cast<int32_t*>(h->scalars.as<uint32_t>() + 2);
-  K.flags = h->flagq.as<unsigned long long>();
+  K.flags = flag_queues(h);
   K.flag_count = flag_counter(h);
-  K.flag_cap = flag_capacity(N);
-  K.flag_bits = h->flagbits.as<uint32_t>();
-  K.flag_words = h->flag_words;
+  K.flag_cap = flag_capacity(h, N);
   K.pair_cap = h->capturing ? h->cap_pairs : h->P;
   K.sig0 = 16 * pass_index;
   K.flag_tau = kFlagTau;
@@ -551,19 +549,17 @@ gmpk::KParams base_params(gmp_ctx* h, const PassData& pd, int pass_index, int64_
   return K;
 }
 
-// Clears the flag queue and bitmask (before a call's compute kernels, and
-// after each refinement so that the next pass queues only its own flags).
+// Clears the flag queue (before a call's compute kernels, and after each
+// refinement so that the next pass queues only its own flags).
 gmp_status reset_flags(gmp_ctx* h, int64_t N, cudaStream_t st) {
-  const size_t bytes = sizeof(uint32_t) * (size_t)h->flag_words * (size_t)std::max<int64_t>(N, 1);
-  GMP_CK(cudaMemsetAsync(flag_counter(h), 0, sizeof(unsigned long long), st), "flag reset");
-  GMP_CK(cudaMemsetAsync(h->flagbits.p, 0, bytes, st), "flag bits reset");
+  (void)N;
+  GMP_CK(cudaMemsetAsync(flag_counter(h), 0, 8 * sizeof(unsigned long long), st), "flag reset");
   return GMP_OK;
 }
 
 gmp_status begin_compute(gmp_ctx* h, int64_t N, cudaStream_t st) {
-  const size_t bytes = sizeof(uint32_t) * (size_t)h->flag_words * (size_t)std::max<int64_t>(N, 1);
-  GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * flag_capacity(N)), "flags");
-  GMP_CK(h->flagbits.ensure(bytes), "flag bits");
+  GMP_CK(h->flagq.ensure(sizeof(unsigned long long) * (8 + (size_t)std::max(h->n_ord_pos, 1) * flag_capacity(h, N))),
+         "flags");
   return reset_flags(h, N, st);
 }
 
@@ -590,12 +586,16 @@ gmp_status refine(gmp_ctx* h, int64_t N, float* features, cudaStream_t st, const
                   MuTarget mt = MuTarget()) {
   GmpRefine A;
   std::memset(&A, 0, sizeof(A));
-  A.queue = h->flagq.as<unsigned long long>();
+  A.queue = flag_queues(h);
   A.count = flag_counter(h);
-  A.cap = flag_capacity(N);
-  A.bits = h->flagbits.as<uint32_t>();
+  A.cap = flag_capacity(h, N);
+  for (int l = 0; l < 7; ++l) A.qidx[l] = -1;
+  {
+    int o = 0;
+    for (int l : h->orders)
+      if (l >= 0) A.qidx[l] = o++;
+  }
   A.n_centers = N;
-  A.flag_words = h->flag_words;
   A.col_info = h->colinfo.as<int32_t>();
   A.features = features;
   A.F = h->F;
@@ -1011,7 +1011,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     for (size_t o = 0; o < h->orders.size(); ++o)
       if (h->orders[o] >= 0)
         for (int s = 0; s < (int)h->sigmas.size(); ++s) ci[col[o] + s] = (h->orders[o] << 16) | s;
-    h->flag_words = (std::max(h->F, 1) + 31) / 32;
+    h->n_ord_pos = 0;
+    for (int l : h->orders) h->n_ord_pos += l >= 0 ? 1 : 0;
     float et[128];
     for (int j = 0; j < 64; ++j) split(std::exp2(-j / 64.0), et + 2 * j);
     if (h->exptab.ensure(sizeof(et)) != cudaSuccess ||

@@ -11,8 +11,8 @@ namespace gmpk {
 static __global__ void k_counter_start(int32_t* counter, int32_t v) { *counter = v; }
 
 template <int L, int NS, int TILE>
-size_t smem_bytes(const GmpPass& P, int warps, int extra_per_warp) {
-  return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax) +
+size_t smem_bytes(const GmpPass& P, int warps, int extra_per_warp, bool pad = true) {
+  return sizeof(float) * (table_floats(P.n_el, L, NS, P.kmax, pad) +
                           (size_t)warps * (Shape<L, NS, TILE>::WARP_FLOATS + extra_per_warp));
 }
 
@@ -29,7 +29,8 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
                                                     : k_jacobian<L, NS>;
   const int extra = kind == GMP_KIND_BACKWARD_VIRIAL ? virial_extra_floats<L, NS>() : 0;
   auto smem_of = [&](int w) {
-    return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w, 0) : smem_bytes<L, NS, 16>(K.pass, w, extra);
+    const bool pad = kind != GMP_KIND_BACKWARD && kind != GMP_KIND_JACOBIAN;  // these two: unpadded table
+    return tile == 32 ? smem_bytes<L, NS, 32>(K.pass, w, 0) : smem_bytes<L, NS, 16>(K.pass, w, extra, pad);
   };
   cudaFuncAttributes fa;
   cudaError_t ea = cudaFuncGetAttributes(&fa, fn);

@@ -315,10 +315,11 @@ cudaError_t gmp_launch_grad_bins_finish(int64_t N, const unsigned long long* bin
 // virial[s] += sum of vir_c over the centers atom_off[s] .. atom_off[s+1]-1 (fixed order).
 cudaError_t gmp_launch_virial_reduce(int n_struct, const int64_t* atom_off, const double* vir_c, double* virial,
                                      cudaStream_t stream, int sm_count, int64_t* launches);
-// Double-float recomputation of the flagged features: the queue (count
-// entries center << 16 | column, at most cap) and, when it overflowed, the
-// set bits of `bits` ([n_centers] x flag_words words, bit col % 32 of word
-// col / 32); col_info[col] = (order << 16) | sigma.  With mu_out, the
+// Double-float recomputation of the flagged features: one queue per
+// order slot o (queue + o * cap, count[o] entries, at most cap; qidx[l] is
+// the slot of order l, -1 when l is not requested), entries center << 32 |
+// first column of the order << 16 | mask of its flagged sigmas;
+// col_info[col] = (order << 16) | sigma.  With mu_out, the
 // recomputed moments of sigmas mu_sig0 .. mu_sig0 + mu_nsig - 1 also
 // overwrite mu_out[center][sigma - mu_sig0][l^2 .. l^2 + 2l] (row length
 // mu_nind), the moments a derivative kernel reads next.
@@ -326,9 +327,8 @@ struct GmpRefine {
   const unsigned long long* queue;
   const unsigned long long* count;
   int64_t cap;
-  const uint32_t* bits;
+  int qidx[7];
   int64_t n_centers;
-  int flag_words;
   const int32_t* col_info;
   float* features;
   int F;

@@ -153,10 +153,18 @@ constexpr int virial_extra_floats() {
   return Shape<L, NS>::TILE * Shape<L, NS>::RSTR >= kVirialFloats ? 0 : kVirialFloats;
 }
 
-// Per-element strides of the shared-memory tables: an odd number of float4s,
-// so lanes reading different elements hit different banks.
-__host__ __device__ inline int rad_elem_stride(int L, int NS, int kmax) {
-  int q = (NS / 4) * kmax * gmp_rad_block(L);
+// Strides of the shared-memory radial table: within an element, the
+// blocks of its 4-sigma groups (kmax primitives x gmp_rad_block(L) float4s
+// each) an odd number of float4s apart (pad), so that lanes reading two
+// groups of one element at once hit different banks; the elements an odd
+// number of float4s apart, for lanes reading different elements.  The
+// plain backward and the Jacobian kernels keep the groups unpadded: the
+// padded stride costs each a register it does not have.
+__host__ __device__ inline int rad_sg_stride(int L, int kmax, bool pad = true) {
+  return pad ? (kmax * gmp_rad_block(L)) | 1 : kmax * gmp_rad_block(L);
+}
+__host__ __device__ inline int rad_elem_stride(int L, int NS, int kmax, bool pad = true) {
+  int q = (NS / 4) * rad_sg_stride(L, kmax, pad);
   if ((q & 1) == 0) ++q;
   return 4 * q;
 }
@@ -186,13 +194,13 @@ struct KParams {
   const int32_t* center_struct;  // [N] structure of each center (virial)
   double* virial;                // [S, 3, 3] strain derivative accumulators (virial)
   // features too ill-conditioned for FP32 (recomputed in double-float
-  // afterwards): queued as (center << 16 | column) while the queue has room,
-  // then as bit (col % 32) of word flag_bits[i * flag_words + col / 32]
+  // afterwards): one queue entry per (center, order) of the pass,
+  // center << 32 | first column of the order << 16 | mask of the sigmas,
+  // in the queue of the order's slot o (flags + o * flag_cap, count
+  // flag_count[o])
   unsigned long long* flags;
   unsigned long long* flag_count;
   int64_t flag_cap;
-  uint32_t* flag_bits;
-  int flag_words;
   int64_t pair_cap;           // pairs buffer capacity: centers beyond it are skipped
   int sig0;                   // global index of this pass's first sigma
   float flag_tau;             // flag when flag_low * l! (2l-1)!! B^2 / 3^l <= f < flag_tau * l! (2l-1)!! B^2
@@ -302,7 +310,7 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
   const float2 nr2h = make_float2(-r2h, -r2h), r2h2 = make_float2(r2h, r2h), r2l2 = make_float2(r2l, r2l);
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
-    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax) + q * RB;
     const float4 bh = blk[0];
     const float4 bl = blk[1];
     float2 E[2];
@@ -330,7 +338,7 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
 // argument; otherwise a single FP32 product, whose error of at most
 // 2^-24 B r^2 (B r^2 < 126 before ex2 underflows) leaves each exponential
 // within ~5e-6 relative: ample for derivatives, checked to 1e-4.
-template <int L, int NL = L + 2, bool PRECISE = true>
+template <int L, int NL = L + 2, bool PRECISE = true, bool PADG = true>
 __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float r2l, float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
@@ -340,7 +348,7 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
     for (int l = 0; l < NL; ++l) R[u][l] = 0.0f;
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
-    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax, PADG) + q * RB;
     const float4 bh = blk[0];
     float E[4];
     if (PRECISE) {
@@ -368,7 +376,7 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
 // The radial factors of radial4s<..., PRECISE = false> (FP32 exponent
 // argument) on packed FP32 pairs, sigmas (0,1) and (2,3) of the group:
 // bit-identical to the scalar form, half the issue slots.
-template <int L, int NL = L + 2>
+template <int L, int NL = L + 2, bool PADG = true>
 __device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
@@ -380,7 +388,7 @@ __device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int km
   const float2 nr2 = make_float2(-r2h, -r2h);
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
-    const float4* blk = reinterpret_cast<const float4*>(tab_e) + (sg * kmax + q) * RB;
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax, PADG) + q * RB;
     const float4 bh = blk[0];
     const float2 x0 = gmp_mul2(make_float2(bh.x, bh.y), nr2), x1 = gmp_mul2(make_float2(bh.z, bh.w), nr2);
     const float2 E0 = make_float2(gmp_ex2(x0.x), gmp_ex2(x0.y)), E1 = make_float2(gmp_ex2(x1.x), gmp_ex2(x1.y));
@@ -417,19 +425,21 @@ __device__ __forceinline__ float density_term(const float* __restrict__ dens_e, 
 // Shared memory: tables first (radial then density), then one region per warp.
 
 
-__host__ __device__ inline size_t table_floats(int n_el, int L, int NS, int kmax) {
-  return (size_t)n_el * rad_elem_stride(L, NS, kmax) + (size_t)n_el * dens_elem_stride(kmax);
+__host__ __device__ inline size_t table_floats(int n_el, int L, int NS, int kmax, bool pad = true) {
+  return (size_t)n_el * rad_elem_stride(L, NS, kmax, pad) + (size_t)n_el * dens_elem_stride(kmax);
 }
 
 // Copies the radial and density tables to shared memory, padding each
-// element's block to its bank-spreading stride.
-template <int L>
+// element's and each sigma group's block to its bank-spreading stride.
+template <int L, bool PADG = true>
 __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_rad, float* s_dens) {
-  const int per = (NS / 4) * P.kmax * gmp_rad_block(L);  // float4s per element in global memory
-  const int es = rad_elem_stride(L, NS, P.kmax) / 4;
+  const int blk = P.kmax * gmp_rad_block(L);  // float4s per sigma group in global memory
+  const int per = (NS / 4) * blk;             // ... per element
+  const int es = rad_elem_stride(L, NS, P.kmax, PADG) / 4, gs = rad_sg_stride(L, P.kmax, PADG);
   for (int t = threadIdx.x; t < P.n_el * per; t += blockDim.x) {
-    const int e = t / per, r = t - e * per;
-    reinterpret_cast<float4*>(s_rad)[e * es + r] = __ldg(reinterpret_cast<const float4*>(P.rad) + t);
+    const int e = t / per, r = t - e * per, g = r / blk;
+    reinterpret_cast<float4*>(s_rad)[e * es + g * gs + (r - g * blk)] =
+        __ldg(reinterpret_cast<const float4*>(P.rad) + t);
   }
   if (P.want_density) {
     const int dper = P.kmax * (GMP_DENS_STRIDE / 4);
@@ -704,30 +714,44 @@ __device__ __forceinline__ void write_features(const KParams& K, int64_t i, cons
   const int lane = threadIdx.x & 31;
   float* frow = K.features + i * P.F;
   const int nf = P.n_ord * P.nsig;
-  for (int t = lane; t < nf; t += 32) {
-    const int o = t / P.nsig, s = t - o * P.nsig;
-    const int l = P.ord_l[o];
-    const float f = gmp_mcsh_invariant(l, Mu + s * SH::NIND + l * l);
-    frow[P.ord_col[o] + s] = f;
-    // Refined: the band where FP32 moments (errors of a few 2^-24 of their
-    // cancellation-free scales A_c) cannot hold the relative bound.  Below
-    // it the feature is so small against F_abs that its FP32 value is
-    // already within the absolute floor 1e-11 F_abs: with moment errors
-    // eps A_c and a computed f below t F_abs, the true f is below
-    // (sqrt(t) + eps)^2 F_abs and the computed one off by at most
-    // (2 sqrt(t) eps + 3 eps^2) F_abs, 6.3e-12 F_abs for t = 1e-10 and
-    // eps = 3e-7 (5 units of 2^-24).  Features that vanish by symmetry
-    // (perfect crystals) land there and are not refined.
-    const float B = Mu[NS * SH::NIND + s * (L + 1) + l];
-    const float U = __fmul_rn(flag_scale(l), __fmul_rn(B, B));  // >= F_abs
-    if (K.flags && f < __fmul_rn(K.flag_tau, U) && !(f < __fmul_rn(__fmul_rn(K.flag_low, inv_pow3(l)), U))) {
-      const int col = P.ord_col[o] + s;
-      const unsigned long long slot = atomicAdd(K.flag_count, 1ull);
-      if (slot < (unsigned long long)K.flag_cap)
-        K.flags[slot] = ((unsigned long long)i << 16) | (unsigned long long)col;
-      else
-        atomicOr(K.flag_bits + i * K.flag_words + (col >> 5), 1u << (col & 31));
+  unsigned omask = 0;  // lane o: the sigmas of order o (this pass) to refine
+  for (int t0 = 0; t0 < nf; t0 += 32) {
+    const int t = t0 + lane;
+    const int o = t < nf ? t / P.nsig : -1, s = t - o * P.nsig;
+    bool flag = false;
+    if (t < nf) {
+      const int l = P.ord_l[o];
+      const float f = gmp_mcsh_invariant(l, Mu + s * SH::NIND + l * l);
+      frow[P.ord_col[o] + s] = f;
+      // Refined: the band where FP32 moments (errors of a few 2^-24 of their
+      // cancellation-free scales A_c) cannot hold the relative bound.  Below
+      // it the feature is so small against F_abs that its FP32 value is
+      // already within the absolute floor 1e-11 F_abs: with moment errors
+      // eps A_c and a computed f below t F_abs, the true f is below
+      // (sqrt(t) + eps)^2 F_abs and the computed one off by at most
+      // (2 sqrt(t) eps + 3 eps^2) F_abs, 6.3e-12 F_abs for t = 1e-10 and
+      // eps = 3e-7 (5 units of 2^-24).  Features that vanish by symmetry
+      // (perfect crystals) land there and are not refined.
+      const float B = Mu[NS * SH::NIND + s * (L + 1) + l];
+      const float U = __fmul_rn(flag_scale(l), __fmul_rn(B, B));  // >= F_abs
+      flag = K.flags && f < __fmul_rn(K.flag_tau, U) && !(f < __fmul_rn(__fmul_rn(K.flag_low, inv_pow3(l)), U));
     }
+    // the orders these 32 features belong to, each gathered into its lane
+    const int o_hi = min(P.n_ord - 1, (t0 + 31) / P.nsig);
+    for (int oo = t0 / P.nsig; oo <= o_hi; ++oo) {
+      const unsigned m = __reduce_or_sync(0xffffffffu, (flag && o == oo) ? 1u << s : 0u);
+      if (lane == oo) omask |= m;
+    }
+  }
+  // one entry per (center, order) with flagged sigmas, in the order's own
+  // queue: center << 32 | first column of the order << 16 | sigma mask.  A
+  // pass has at most one entry per (center, order), and a queue holds that
+  // many.
+  if (lane < P.n_ord && omask) {
+    const unsigned long long slot = atomicAdd(K.flag_count + lane, 1ull);
+    if (slot < (unsigned long long)K.flag_cap)
+      K.flags[lane * K.flag_cap + slot] =
+          ((unsigned long long)i << 32) | ((unsigned long long)P.ord_col[lane] << 16) | omask;
   }
   if (P.want_density && lane == 0) frow[P.dens_col] = rho;
 }
@@ -827,7 +851,7 @@ __device__ __forceinline__ void pair_gradient(const float* lam, float A, float d
 // PACKED: radial factors on packed FP32 pairs (same results, fewer issue
 // slots; the plain backward kernel uses them, the strain-derivative variant
 // would spill at the 168 registers of the 12-warp launch).
-template <int L, int NS, bool VIRIAL = false, bool PACKED = false>
+template <int L, int NS, bool VIRIAL = false, bool PACKED = false, bool PADG = true>
 __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
                                                const float* __restrict__ Lam, float gd, float* Wv = nullptr) {
@@ -855,13 +879,13 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
 #pragma unroll
     for (int k = 0; k < SH::NIND; ++k) lam[k] = 0.0f;
     float A = 0.0f;  // sum over sigma and order of dR_l/dr^2 * sum_{k in l} Lam_k S_k
-    const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
+    const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax, PADG);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
       if constexpr (PACKED)
-        radial4p<L, L + 2>(tab_e, P.kmax, sg, r2h, R);
+        radial4p<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, R);
       else
-        radial4s<L, L + 2, false>(tab_e, P.kmax, sg, r2h, r2l, R);
+        radial4s<L, L + 2, false, PADG>(tab_e, P.kmax, sg, r2h, r2l, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
@@ -974,10 +998,13 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
   using SH = Shape<L, NS>;
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
+  // table layout by register budget: each variant with the one it keeps
+  // 168 registers without spilling
+  constexpr bool PADG = VIRIAL;
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax, PADG);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables<L>(P, NS, s_rad, s_dens);
+  load_tables<L, PADG>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   constexpr int EXTRA = VIRIAL ? virial_extra_floats<L, NS>() : 0;
@@ -994,7 +1021,7 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
     const float* grow = K.grad_feat + i * P.F;
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS, VIRIAL, !VIRIAL>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
+    backward_sweep<L, NS, VIRIAL, !VIRIAL, PADG>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
     __syncwarp();
   }
 }
@@ -1040,10 +1067,12 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
   constexpr int NO = L + 1;   // at most L + 1 orders >= 0 per pass
   extern __shared__ __align__(16) float smem[];
   const GmpPass& P = K.pass;
+  // unpadded table: the padded group stride took the order-6 kernel from
+  // 165 to 169 registers, two resident 4-warp CTAs per SM instead of three
   float* s_rad = smem;
-  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax);
+  float* s_dens = s_rad + (size_t)P.n_el * rad_elem_stride(L, NS, P.kmax, false);
   float* s_warp = s_dens + (size_t)P.n_el * dens_elem_stride(P.kmax);
-  load_tables<L>(P, NS, s_rad, s_dens);
+  load_tables<L, false>(P, NS, s_rad, s_dens);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int pg = lane / NS, s = lane % NS;
@@ -1125,7 +1154,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
         float Rl[L + 2];
 #pragma unroll
         for (int l = 0; l < L + 2; ++l) Rl[l] = 0.0f;
-        const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
+        const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax, false);
         for (int q = 0; q < P.kmax; ++q) {
           const float* ent = tab_e + ((s / 4) * P.kmax + q) * gmp_rad_block(L) * 4 + (s % 4);
           const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);

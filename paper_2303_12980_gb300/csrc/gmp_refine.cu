@@ -47,15 +47,30 @@ __device__ __forceinline__ gmp_f2 df_exp_neg(gmp_f2 x, const float2* __restrict_
   return gmp_f2{ldexpf(e.hi, -(ki >> 6)), ldexpf(e.lo, -(ki >> 6))};
 }
 
-// Moments of order L (2L+1 independent components) of one center and one
-// sigma over its pairs, lane-strided, in double-float arithmetic.
+// Sigmas recomputed together: the displacement and the MCSH components of a
+// pair serve all of them, the radial factor is per sigma.  Only orders 4
+// and 5 take pairs of sigmas.  Below order 4 the components are cheap and
+// a group only takes parallelism from the few flagged features of a
+// typical batch (random alloy slab: refinement 0.30 ms with single sigmas,
+// 0.40 ms with groups of 4); at order 6 a second sigma's accumulators do
+// not fit the kernel's 128 registers (two 256-thread CTAs per SM; at 168
+// registers it ran at half the resident warps and slower, grouping or
+// not).  Perfect FCC crystal (orders 4 and 6 flagged at the widest
+// sigmas): 24.9 ms single, 21.5 ms with pairs at orders 4-5.
 template <int L>
+constexpr int refine_group() { return (L == 4 || L == 5) ? 2 : 1; }
+
+// Moments of order L (2L+1 independent components) of one center for the
+// ng <= G sigmas sig[0 .. ng-1] over its pairs, lane-strided, in
+// double-float arithmetic.
+template <int L, int G>
 __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, const float4& xli,
                                                const GmpStruct& st, const int64_t p0, const int64_t p1,
                                                const GmpPair* __restrict__ pairs,
                                                const float4* __restrict__ atom_xh, const float4* __restrict__ atom_xl,
-                                               const float* __restrict__ ktab, int nsig_total, int sig, int kmax,
-                                               const float2* __restrict__ exp_tab, gmp_f2 (&mu)[2 * L + 1]) {
+                                               const float* __restrict__ ktab, int nsig_total, const int (&sig)[G],
+                                               int ng, int kmax, const float2* __restrict__ exp_tab,
+                                               gmp_f2 (&mu)[G][2 * L + 1]) {
   for (int64_t p = p0 + lane; p < p1; p += 32) {
     const GmpPair pr = pairs[p];
     int nn[3];
@@ -63,103 +78,121 @@ __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, cons
     gmp_f2 d[3], r2;
     float mag;
     gmp_df_disp(xhi, xli, atom_xh[pr.j], atom_xl[pr.j], st, nn, d, r2, mag);
-    // radial factor: sum_q A_{q,L} exp(-b_q r^2); table entry (b, A_0 .. A_6) as double-floats
-    gmp_f2 R{0.0f, 0.0f};
-    const float* te = ktab + ((size_t)pr.e * nsig_total + sig) * kmax * 16;  // [element][sigma][primitive]
-    for (int q = 0; q < kmax; ++q) {
-      const float* ent = te + q * 16;
-      const gmp_f2 E = df_exp_neg(gmp_df_mul(gmp_f2{ent[0], ent[1]}, r2), exp_tab);
-      R = gmp_df_add(R, gmp_df_mul(gmp_f2{ent[2 + 2 * L], ent[3 + 2 * L]}, E));
-    }
     gmp_f2 Sd[(L + 1) * (L + 1)];
     gmp_mcsh_indep_df(L, d[0], d[1], d[2], r2, Sd);
 #pragma unroll
-    for (int k = 0; k <= 2 * L; ++k) mu[k] = gmp_df_add(mu[k], gmp_df_mul(R, Sd[L * L + k]));
-  }
-}
-
-// One flagged feature f_{L,sigma} of one center: moments over the center's
-// pairs (lane-strided), warp-reduced, and the invariant, all double-float;
-// the result (rounded to FP32) is valid in every lane.  mu_dst (optional)
-// receives the 2L+1 moments rounded to FP32.
-template <int L>
-__device__ __forceinline__ float refine_feature(int lane, const GmpRefine& A, const float4& xhi, const float4& xli,
-                                                const GmpStruct& st, int64_t p0, int64_t p1, int sig,
-                                                float* mu_dst) {
-  gmp_f2 mu[2 * L + 1];
+    for (int g = 0; g < G; ++g) {
+      if (g >= ng) break;
+      // radial factor: sum_q A_{q,L} exp(-b_q r^2); table entry (b, A_0 .. A_6) as double-floats
+      gmp_f2 R{0.0f, 0.0f};
+      const float* te = ktab + ((size_t)pr.e * nsig_total + sig[g]) * kmax * 16;  // [element][sigma][primitive]
+      for (int q = 0; q < kmax; ++q) {
+        const float* ent = te + q * 16;
+        const gmp_f2 E = df_exp_neg(gmp_df_mul(gmp_f2{ent[0], ent[1]}, r2), exp_tab);
+        R = gmp_df_add(R, gmp_df_mul(gmp_f2{ent[2 + 2 * L], ent[3 + 2 * L]}, E));
+      }
 #pragma unroll
-  for (int k = 0; k <= 2 * L; ++k) mu[k] = gmp_f2{0.0f, 0.0f};
-  refine_moments<L>(lane, xhi, xli, st, p0, p1, A.pairs, A.atom_xh, A.atom_xl, A.ktab, A.nsig_total, sig, A.kmax,
-                    A.exp_tab, mu);
-#pragma unroll
-  for (int k = 0; k <= 2 * L; ++k)
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const gmp_f2 other{__shfl_xor_sync(0xffffffffu, mu[k].hi, o), __shfl_xor_sync(0xffffffffu, mu[k].lo, o)};
-      mu[k] = gmp_df_add(mu[k], other);
+      for (int k = 0; k <= 2 * L; ++k) mu[g][k] = gmp_df_add(mu[g][k], gmp_df_mul(R, Sd[L * L + k]));
     }
-  if (mu_dst && lane == 0) {
-#pragma unroll
-    for (int k = 0; k <= 2 * L; ++k) mu_dst[k] = mu[k].hi + mu[k].lo;
   }
-  const gmp_f2 f = gmp_mcsh_invariant_df(L, mu);
-  return f.hi + f.lo;
 }
 
-// One flagged feature (center i, column col) of order LO recomputed by the
-// whole warp (entries of other orders are left to that order's launch);
-// col_info[col] = (order << 16) | global sigma.
+// The flagged features of order LO of one task: center i, the order's
+// first column c0 (col_info[c0] = (order << 16) | global sigma of that
+// column) and a mask of flagged sigmas, recomputed by the whole warp G
+// sigmas at a time (entries of other orders are left to that order's
+// launch).  Moments over the center's pairs (lane-strided), warp-reduced,
+// and the invariant, all double-float; the feature is rounded to FP32.  With
+// mu_out, the 2L+1 moments of a sigma of the pass rounded to FP32 overwrite
+// its FP32 moments.
 template <int LO>
-__device__ __forceinline__ void refine_entry(int lane, const GmpRefine& A, int64_t i, int col) {
-  const int info = col < A.F ? A.col_info[col] : -1;
+__device__ __forceinline__ void refine_entry(int lane, const GmpRefine& A, int64_t i, int c0, unsigned mask) {
+  constexpr int G = refine_group<LO>();
+  const int info = c0 < A.F ? A.col_info[c0] : -1;
   if (info < 0 || (info >> 16) != LO) return;
-  const int sig = info & 0xffff;
+  const int sig0 = info & 0xffff;
   const GmpStruct& st = A.structs[A.center_struct[i]];
   const float4 xhi = A.center_xh[i], xli = A.center_xl[i];
   const int64_t p0 = A.nbr_beg[i], p1 = A.nbr_end[i];
-  float* mu_dst = nullptr;
-  if (A.mu_out && sig >= A.mu_sig0 && sig < A.mu_sig0 + A.mu_nsig)
-    mu_dst = A.mu_out + (i * A.mu_nsig + (sig - A.mu_sig0)) * (int64_t)A.mu_nind + LO * LO;
-  const float f = refine_feature<LO>(lane, A, xhi, xli, st, p0, p1, sig, mu_dst);
-  if (lane == 0) A.features[i * A.F + col] = f;
+  while (mask) {  // warp-uniform
+    int sig[G], col[G], ng = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      sig[g] = sig0;
+      col[g] = c0;
+      if (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        sig[g] = sig0 + b;
+        col[g] = c0 + b;
+        ng = g + 1;
+      }
+    }
+    gmp_f2 mu[G][2 * LO + 1];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int k = 0; k <= 2 * LO; ++k) mu[g][k] = gmp_f2{0.0f, 0.0f};
+    refine_moments<LO, G>(lane, xhi, xli, st, p0, p1, A.pairs, A.atom_xh, A.atom_xl, A.ktab, A.nsig_total, sig, ng,
+                          A.kmax, A.exp_tab, mu);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (g >= ng) break;
+#pragma unroll
+      for (int k = 0; k <= 2 * LO; ++k)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const gmp_f2 other{__shfl_xor_sync(0xffffffffu, mu[g][k].hi, o),
+                             __shfl_xor_sync(0xffffffffu, mu[g][k].lo, o)};
+          mu[g][k] = gmp_df_add(mu[g][k], other);
+        }
+      if (A.mu_out && sig[g] >= A.mu_sig0 && sig[g] < A.mu_sig0 + A.mu_nsig && lane == 0) {
+        float* mu_dst = A.mu_out + (i * A.mu_nsig + (sig[g] - A.mu_sig0)) * (int64_t)A.mu_nind + LO * LO;
+#pragma unroll
+        for (int k = 0; k <= 2 * LO; ++k) mu_dst[k] = mu[g][k].hi + mu[g][k].lo;
+      }
+      const gmp_f2 f = gmp_mcsh_invariant_df(LO, mu[g]);
+      if (lane == 0) A.features[i * A.F + col[g]] = f.hi + f.lo;
+    }
+  }
 }
 
 // Flagged features of order LO (one launch per order, so that every warp of
 // a launch runs the same instantiation: the per-order code is large, and
-// warps mixing orders thrash the instruction cache).  First the queue
-// (entries center << 16 | column, spread over the warps one entry each);
-// when it overflowed, the rest are the set bits of the bitmask (bit
-// col % 32 of word i * FW + col / 32), which each warp reads 32 words at a
-// time (lane = word).
+// warps mixing orders thrash the instruction cache).  The order's queue
+// entries (center << 32 | first column of the order << 16 | mask of up to
+// 16 sigmas) are cut into tasks of one group of G flagged sigmas each,
+// numbered group-major (all entries' first groups, then their second
+// groups, ...; empty groups cost a load and a count), so that a center with
+// many flagged sigmas is spread over as many warps as it has groups instead
+// of one warp taking them in turn.
 template <int LO>
-__global__ void k_refine(const GmpRefine A) {
+__global__ void __launch_bounds__(256, 2) k_refine(const GmpRefine A) {
+  constexpr int G = refine_group<LO>();
+  constexpr int S = (16 + G - 1) / G;
+  const int qi = A.qidx[LO];
+  if (qi < 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long n = *A.count;
+  const unsigned long long n = A.count[qi];
   const int64_t nq = n < (unsigned long long)A.cap ? (int64_t)n : A.cap;
-  for (int64_t t = warp; t < nq; t += nw) {
-    const unsigned long long e = A.queue[t];
-    refine_entry<LO>(lane, A, (int64_t)(e >> 16), (int)(e & 0xffffu));
-  }
-  if (n <= (unsigned long long)A.cap) return;
-  const int64_t n_words = A.n_centers * A.flag_words;
-  for (int64_t base = warp * 32; base < n_words; base += nw * 32) {
-    const uint32_t word = base + lane < n_words ? A.bits[base + lane] : 0u;
-    unsigned live = __ballot_sync(0xffffffffu, word != 0u);
-    while (live) {  // warp-uniform from here on
-      const int src = __ffs(live) - 1;
-      live &= live - 1;
-      uint32_t wv = __shfl_sync(0xffffffffu, word, src);
-      const int64_t tw = base + src;
-      const int64_t i = tw / A.flag_words;
-      const int cbase = (int)(tw - i * A.flag_words) * 32;
-      while (wv) {
-        const int col = cbase + __ffs(wv) - 1;
-        wv &= wv - 1;
-        refine_entry<LO>(lane, A, i, col);
-      }
+  const unsigned long long* queue = A.queue + qi * A.cap;
+  // task v = g * nq + t: group g of entry t, so that the groups of one
+  // entry fall to different warps
+  for (int64_t v = warp; v < S * nq; v += nw) {
+    const int g = (int)(v / nq);
+    const int64_t t = v - (int64_t)g * nq;
+    const unsigned long long e = queue[t];
+    unsigned mask = (unsigned)(e & 0xffffu);
+    if (__popc(mask) <= g * G) continue;
+    for (int k = 0; k < g * G; ++k) mask &= mask - 1;  // the groups before this one
+    unsigned grp = 0;
+    for (int k = 0; k < G && mask; ++k) {
+      grp |= mask & (0u - mask);
+      mask &= mask - 1;
     }
+    refine_entry<LO>(lane, A, (int64_t)(e >> 32), (int)((e >> 16) & 0xffffu), grp);
   }
 }
 
