@@ -267,6 +267,13 @@ def fcc_perfect262k(seed: int = 1004, reps=(32, 32, 64)) -> Workload:
                    [0, 1, 2, 3, 4, 5, 6], np.geomspace(0.05, 1.5, 16), 8.0)
 
 
+def fcc_perfect32k(seed: int = 1004) -> Workload:
+    """The perfect crystal at 1/8 size (16x16x32 conventional cells, 32,768
+    atoms), same probes; the small case for profiling its refinement."""
+    w = fcc_perfect262k(seed=seed, reps=(16, 16, 32))
+    return w.replace(name="fcc_perfect32k")
+
+
 def fcc_slab32k(seed: int = 1004) -> Workload:
     """The alloy slab at 1/8 size (16x16x32 conventional cells, 32,768
     atoms), same probes; the small case for kernel profiling."""
@@ -280,6 +287,7 @@ WORKLOADS = {
     "batched10k": batched10k,
     "fcc_slab262k": fcc_slab262k,
     "fcc_slab32k": fcc_slab32k,
+    "fcc_perfect32k": fcc_perfect32k,
     "fcc_perfect262k": fcc_perfect262k,
 }
 
