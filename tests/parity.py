@@ -21,7 +21,10 @@ product of an FP32 radial factor (a sum of SFU exponentials) and an FP32
 MCSH value, and the forward kernel adds 16 pairs in plain FP32 before each
 compensated fold.  Measured over every row of the first 4096 atoms of
 batched300, the worst entry is 3.5 units of 2^-24 G_abs (1.2e-4 at a 1e-3
-floor, which allows 1.68 units; 4.3e-5 at 5e-3).  Position gradients (VJP)
+floor, which allows 1.68 units; 4.3e-5 at 5e-3).  tests/test_fp32_floor.py
+shows the same limit without the GPU: moments formed from the rounded FP32
+radial factors and MCSH values of the FP64 oracle, added in FP32 over
+16-pair blocks, already give Jacobian-row errors of 2.0 units on fcc4096.  Position gradients (VJP)
 and strain derivatives sum many rows, whose moment errors do not add up
 coherently, and keep GRAD_TAU.
 
