@@ -524,9 +524,12 @@ constexpr float kFlagTau = 3e-4f;
 constexpr float kFlagLow = 1e-10f;
 
 // Refinement queues, one per requested order: a pass queues at most one
-// entry per (center, order).  The flag buffer holds 8 counts, then the
-// queues.
-int64_t flag_capacity(const gmp_ctx* h, int64_t N) { (void)h; return N + 1024; }
+// entry per (center, order), and a call refines after each pass (derivative
+// calls) or once after all of them (features), so a queue holds one entry
+// per center and pass.  The flag buffer holds 8 counts, then the queues.
+int64_t flag_capacity(const gmp_ctx* h, int64_t N) {
+  return (int64_t)std::max<size_t>(h->passes.size(), 1) * N + 1024;
+}
 unsigned long long* flag_counter(gmp_ctx* h) { return h->flagq.as<unsigned long long>(); }
 unsigned long long* flag_queues(gmp_ctx* h) { return h->flagq.as<unsigned long long>() + 8; }
 

@@ -171,3 +171,26 @@ def test_near_symmetric_crystals(torch, oracle_mod):
     gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
     gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
     assert gerr.max() <= GRAD_TOL, gerr.max()
+
+
+def test_many_flags_over_two_sigma_passes(torch, oracle_mod):
+    """A jittered (1e-4 A) one-element FCC crystal of 2048 atoms with 24
+    sigmas, two 16-sigma passes: most features of every center are
+    recomputed in double-float, and a features call refines once after both
+    passes, so each order's refinement queue takes an entry per center and
+    pass (more than the atoms plus the queue's slack).  Sampled centers
+    against the oracle."""
+    base = synth.fcc_slab262k(reps=(3, 3, 3))
+    rng = np.random.default_rng(8)
+    pos, cell = synth.fcc_supercell(rng, 3.9, (8, 8, 8), 1e-4)
+    w = _batch(base, [(pos, np.zeros(len(pos), np.int32), cell, (1, 1, 1))],
+               sigmas=list(np.geomspace(0.05, 1.5, 24)))
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    f = F.featurize(torch.from_numpy(w.positions).cuda(), torch.from_numpy(w.species).cuda(),
+                    w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    centers = np.arange(0, w.n_atoms, 41)
+    ref, fabs = oracle_mod.features(w, centers, want_abs=True)
+    err = feature_errors(f.cpu().numpy()[centers], ref, fabs)
+    assert err.max() <= FEAT_TOL, err.max()
