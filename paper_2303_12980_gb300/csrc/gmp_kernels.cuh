@@ -607,7 +607,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
 #pragma unroll
         for (int v = 0; v < 2 * CW; ++v) acc2[v] = make_float2(0.0f, 0.0f);
         if constexpr (CW == 4) {
-#pragma unroll 4
+#pragma unroll 8
           for (int pp = b0; pp < b1; ++pp) {
             const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
             const float4 s = *reinterpret_cast<const float4*>(sp + pp * SH::SSTR);
@@ -621,7 +621,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
             }
           }
         } else if (!mixed_last) {
-#pragma unroll 4
+#pragma unroll 8
           for (int pp = b0; pp < b1; ++pp) {
             const float4 r = *reinterpret_cast<const float4*>(rp + pp * SH::RSTR);
             const float2 s = *reinterpret_cast<const float2*>(sp + pp * SH::SSTR);
