@@ -28,7 +28,9 @@
  *   3. overlap of one density primitive c exp(-alpha |r-d|^2) with the probe
  *      N_sigma S_abc(r) exp(-r^2/(2 sigma^2)), N_sigma = (2 pi sigma^2)^(-3/2):
  *      Gaussian product theorem, then the Gaussian expectation of each
- *      monomial of S_abc from 1-D moments m_{n+1} = P m_n + n/(2 gamma) m_{n-1};
+ *      monomial of S_abc from 1-D moments m_{n+1} = P m_n + n/(2 gamma) m_{n-1}
+ *      (an image at d = 0, the center's own atom, adds exactly 0 to the
+ *      orders l >= 1: S_abc is harmonic without a constant term);
  *   4. moments mu_{l,sigma,abc}(i) = plain FP64 sum over pairs and primitives;
  *   5. feature f_{l,sigma} = sum_abc l!/(a! b! c!) mu_abc^2 (order -1: the
  *      density sum_pairs sum_k c_k exp(-alpha_k |d|^2));
@@ -465,6 +467,15 @@ static void pair_terms(const octx *X, int e, const double d[3], double *t, doubl
       for (int o = 0; o < P->n_orders; ++o) {
         int l = P->orders[o];
         if (l < 0) continue;
+        /* A neighbor image at d = 0 (the center's own atom) is a density
+         * centred on the probe: its overlap with an order l >= 1 probe is
+         * exactly 0 (S_abc is harmonic with no constant term, and a Gaussian
+         * average of a harmonic polynomial is its value at the Gaussian's
+         * centre, here the origin).  The monomial route of step 3 would
+         * leave FP64 cancellation residue of ~2^-53 of its term magnitudes
+         * instead; the derivative there is kept (the center's own images
+         * never enter a gradient). */
+        if (l >= 1 && r2 == 0.0 && !dt) continue;
         for (int ci = 0; ci < X->T.ncomp[l]; ++ci) {
           const ocomp *cp = &X->T.comp[l][ci];
           double v = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
@@ -478,7 +489,7 @@ static void pair_terms(const octx *X, int e, const double d[3], double *t, doubl
             }
           }
           int col = col_of(X, o, s, ci);
-          t[col] += K * v;
+          if (!(l >= 1 && r2 == 0.0)) t[col] += K * v;
           if (dt) {
             /* d/dd exp(-alpha|r-d|^2) = 2 alpha (r - d) exp(...):
              * d I/dd = 2 alpha K (E[X S(X)] - d E[S(X)]) */

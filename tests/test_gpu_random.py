@@ -1,0 +1,83 @@
+"""Seeded random batches against the FP64 oracle: small structures with
+triclinic cells (shear up to 0.3 of a cell length), every mix of periodic
+and open axes, 4-48 atoms of three elements, random order subsets of -1..6
+and 1-24 sigmas (two 16-sigma passes above 16), cutoff 5.5 A.  Neighbor
+sets bit-exact, features of every center and the position gradients of
+sampled atoms within the parity tolerances."""
+import numpy as np
+import pytest
+
+from paper_2303_12980_gb300 import synth
+
+from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2303_12980_gb300 import build
+    build.build()
+    return t
+
+
+def _structure(rng):
+    n = int(rng.integers(4, 49))
+    pbc = rng.integers(0, 2, 3).astype(np.uint8)
+    L = rng.uniform(5.0, 11.0, 3)
+    cell = np.diag(L)
+    cell[1, 0], cell[2, 0], cell[2, 1] = rng.uniform(-0.3, 0.3, 3) * L[[1, 2, 2]]
+    pos = []
+    tries = 0
+    while len(pos) < n and tries < 20000:
+        tries += 1
+        x = rng.uniform(0.0, 1.0, 3) @ cell
+        shifts = [np.array([a, b, c]) @ cell for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)
+                  if all(pbc[k] or (a, b, c)[k] == 0 for k in range(3))]
+        if all(np.linalg.norm(x - p + sh) >= 0.9 for p in pos for sh in shifts):
+            pos.append(x)
+    pos = np.array(pos) + rng.uniform(-20.0, 20.0, 3)  # away from the origin
+    return pos, rng.integers(0, 3, len(pos)).astype(np.int32), cell, pbc
+
+
+@pytest.mark.parametrize("seed,orders,n_sig", [(21, [0, 1, 2, 3, 4, 5, 6], 6),
+                                               (22, [-1, 0, 2, 5], 24),
+                                               (23, [1, 3, 4, 6], 11),
+                                               (24, [-1], 1),
+                                               (25, [6], 17),
+                                               (26, [4, 0, -1, 2], 3),
+                                               (27, [0, 1, 2, 3, 4], 8),
+                                               (28, [-1, 0, 1, 2, 3, 4, 5, 6], 16)])
+def test_random_batches_against_oracle(torch, oracle_mod, seed, orders, n_sig):
+    rng = np.random.default_rng(seed)
+    parts = [_structure(rng) for _ in range(12)]
+    n_gauss, coef, expo = synth.gaussian_table(rng, [2, 5, 7], 3)
+    w = synth.Workload(
+        name="random_batch", positions=np.ascontiguousarray(np.concatenate([p for p, _, _, _ in parts])),
+        cells=np.stack([c for _, _, c, _ in parts]), pbc=np.stack([b for _, _, _, b in parts]),
+        atom_off=np.concatenate([[0], np.cumsum([len(p) for p, _, _, _ in parts])]).astype(np.int64),
+        species=np.concatenate([s for _, s, _, _ in parts]), n_gauss=n_gauss, gauss_coef=coef,
+        gauss_exp=expo, orders=orders, sigmas=[float(s) for s in np.geomspace(0.1, 1.2, n_sig)], cutoff=5.5)
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    noff, nj, nsh = F.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+    ooff, oj, osh, _ = oracle_mod.neighbors(w)
+    assert np.array_equal(noff.cpu().numpy(), ooff)
+    assert np.array_equal(nj.cpu().numpy(), oj)
+    assert np.array_equal(nsh.cpu().numpy(), osh)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=seed)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    f_only = F.featurize(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    for f in (feat, f_only):
+        err = feature_errors(f.cpu().numpy(), ref, fabs)
+        assert err.max() <= FEAT_TOL, err.max()
+    atoms = rng.choice(w.n_atoms, 24, replace=False)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    assert gerr.max() <= GRAD_TOL, gerr.max()

@@ -603,6 +603,29 @@ def test_single_pair_scale_equals_feature_and_closed_form(oracle_mod):
             col += 1
 
 
+def test_center_atom_adds_nothing_to_higher_orders(oracle_mod):
+    # A lone atom (its only neighbor image is itself, at d = 0): a density
+    # centred on the probe has zero overlap with every harmonic probe of
+    # order l >= 1 (mean-value property: the Gaussian average of a harmonic
+    # polynomial without constant term is its value at the centre, 0), so
+    # those features are exactly 0; order 0 is R_0(0)^2 and the density its
+    # own sum of coefficients.  Also a reference point placed exactly on an
+    # atom whose neighbors all lie beyond the cutoff.
+    orders, sigmas = [-1, 0, 1, 2, 3, 4, 5, 6], [0.1, 0.5, 1.2]
+    w = _lone_pair_workload(orders, sigmas)
+    f, fa = oracle_mod.features(w, [0], want_abs=True)
+    fp = oracle_mod.point_features(w, np.array([[0.0, 0.0, 0.0]]), [0])
+    for row in (f[0], fp[0]):
+        assert row[0] == pytest.approx(sum(w.gauss_coef), rel=1e-15)
+        for s, sig in enumerate(sigmas):
+            beta = 1 / (2 * sig * sig)
+            R0 = sum(c * (2 * math.pi * sig * sig) ** -1.5 * (math.pi / (a + beta)) ** 1.5
+                     for c, a in zip(w.gauss_coef, w.gauss_exp))
+            assert row[1 + s] == pytest.approx(R0 * R0, rel=1e-13)
+        assert np.all(row[1 + len(sigmas):] == 0.0)
+    assert np.all(fa[0, 1 + len(sigmas):] == 0.0)
+
+
 def test_scales_bound_features_and_derivatives(oracle_mod):
     w = synth.workload("random64_box").replace(orders=[-1, 0, 1, 2, 3, 4, 5, 6])
     f, fa = oracle_mod.features(w, want_abs=True)
