@@ -204,6 +204,28 @@ __device__ __forceinline__ float gmp_exp_neg(float Bhi, float Blo, float r2hi, f
   return __fmaf_rn(E, -0.69314718055994531f * xl, E);
 }
 
+// 2^32 exp(-B r^2), for the dense Jacobian rows.  A row there holds the
+// terms of one neighbor atom alone, multiplied by adjoints that can be large,
+// so a radial factor that is subnormal in FP32 (few significant bits) or
+// flushed to zero by the SFU would show in the row.  Offsetting the exponent
+// by 32 keeps the factor normal down to exp(-B r^2) = 2^-158; the kernel
+// scales its sums back by 2^-32 when it writes them.  32 - xh is rounded
+// only when xh < 16, and there Fast2Sum (|32| >= |xh|) recovers its rounding
+// error exactly; for xh >= 16 the difference is exact and the recovered
+// error is 0.  The error joins the low part of the argument.
+#define GMP_EXP_SHIFT 32.0f
+#define GMP_EXP_UNSHIFT 0x1p-32f
+__device__ __forceinline__ float gmp_exp_neg_shifted(float Bhi, float Blo, float r2hi, float r2lo) {
+  float xh = __fmul_rn(Bhi, r2hi);
+  float xl = __fmaf_rn(Bhi, r2hi, -xh);
+  xl = __fmaf_rn(Bhi, r2lo, xl);
+  xl = __fmaf_rn(Blo, r2hi, xl);
+  const float d = __fadd_rn(GMP_EXP_SHIFT, -xh);
+  const float e = __fadd_rn(__fadd_rn(GMP_EXP_SHIFT, -d), -xh);  // (32 - xh) - d, exactly
+  const float E = gmp_ex2(d);
+  return __fmaf_rn(E, -0.69314718055994531f * __fadd_rn(xl, -e), E);
+}
+
 // Double-float displacement of j's image n from i, and its r^2.
 __device__ __forceinline__ void gmp_df_disp(const float4& xhi, const float4& xli, const float4& xhj,
                                         const float4& xlj, const GmpStruct& st, const int* n,

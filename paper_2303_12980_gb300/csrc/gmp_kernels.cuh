@@ -332,15 +332,18 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
   }
 }
 
-// The same radial factors with scalar FP32 operations (the backward kernel
-// keeps its 168-register budget with these; packed pairs need aligned
-// register pairs and spill there).  PRECISE: the double-float exponent
-// argument; otherwise a single FP32 product, whose error of at most
-// 2^-24 B r^2 (B r^2 < 126 before ex2 underflows) leaves each exponential
-// within ~5e-6 relative: ample for derivatives, checked to 1e-4.
-template <int L, int NL = L + 2, bool PRECISE = true, bool PADG = true>
+// Radial factors scaled by 2^32 for the backward, with scalar FP32
+// operations (the backward kernel keeps its 168-register budget with these;
+// packed pairs need aligned register pairs and spill there).  The exponent
+// argument 32 - B r^2 is one FMA, rounded once: an absolute error of at most
+// 2^-18 while the scaled factor is normal (|32 - B r^2| < 128), so each
+// exponential is within ~2e-6 relative: ample for derivatives, checked to
+// 1e-4.  The offset keeps the factors normal (not flushed to zero by the SFU)
+// down to exp(-B r^2) = 2^-158: a gradient term of a far pair, multiplied by
+// large adjoints, keeps its digits; the kernel scales its sums back by 2^-32.
+template <int L, int NL = L + 2, bool PADG = true>
 __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
-                                         float r2l, float (&R)[4][NL]) {
+                                         float (&R)[4][NL]) {
   constexpr int RB = gmp_rad_block(L);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -351,18 +354,10 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
     const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax, PADG) + q * RB;
     const float4 bh = blk[0];
     float E[4];
-    if (PRECISE) {
-      const float4 bl = blk[1];
-      E[0] = gmp_exp_neg(bh.x, bl.x, r2h, r2l);
-      E[1] = gmp_exp_neg(bh.y, bl.y, r2h, r2l);
-      E[2] = gmp_exp_neg(bh.z, bl.z, r2h, r2l);
-      E[3] = gmp_exp_neg(bh.w, bl.w, r2h, r2l);
-    } else {
-      E[0] = gmp_ex2(-__fmul_rn(bh.x, r2h));
-      E[1] = gmp_ex2(-__fmul_rn(bh.y, r2h));
-      E[2] = gmp_ex2(-__fmul_rn(bh.z, r2h));
-      E[3] = gmp_ex2(-__fmul_rn(bh.w, r2h));
-    }
+    E[0] = gmp_ex2(__fmaf_rn(bh.x, -r2h, GMP_EXP_SHIFT));
+    E[1] = gmp_ex2(__fmaf_rn(bh.y, -r2h, GMP_EXP_SHIFT));
+    E[2] = gmp_ex2(__fmaf_rn(bh.z, -r2h, GMP_EXP_SHIFT));
+    E[3] = gmp_ex2(__fmaf_rn(bh.w, -r2h, GMP_EXP_SHIFT));
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const float4 a = blk[2 + l];
@@ -373,9 +368,9 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
   }
 }
 
-// The radial factors of radial4s<..., PRECISE = false> (FP32 exponent
-// argument) on packed FP32 pairs, sigmas (0,1) and (2,3) of the group:
-// bit-identical to the scalar form, half the issue slots.
+// The scaled radial factors of radial4s on packed FP32 pairs, sigmas (0,1)
+// and (2,3) of the group: bit-identical to the scalar form, half the issue
+// slots.
 template <int L, int NL = L + 2, bool PADG = true>
 __device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float (&R)[4][NL]) {
@@ -385,12 +380,12 @@ __device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int km
   for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int l = 0; l < NL; ++l) Rp[h][l] = make_float2(0.0f, 0.0f);
-  const float2 nr2 = make_float2(-r2h, -r2h);
+  const float2 nr2 = make_float2(-r2h, -r2h), sh = make_float2(GMP_EXP_SHIFT, GMP_EXP_SHIFT);
 #pragma unroll 1
   for (int q = 0; q < kmax; ++q) {
     const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax, PADG) + q * RB;
     const float4 bh = blk[0];
-    const float2 x0 = gmp_mul2(make_float2(bh.x, bh.y), nr2), x1 = gmp_mul2(make_float2(bh.z, bh.w), nr2);
+    const float2 x0 = gmp_fma2(make_float2(bh.x, bh.y), nr2, sh), x1 = gmp_fma2(make_float2(bh.z, bh.w), nr2, sh);
     const float2 E0 = make_float2(gmp_ex2(x0.x), gmp_ex2(x0.y)), E1 = make_float2(gmp_ex2(x1.x), gmp_ex2(x1.y));
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
@@ -408,13 +403,16 @@ __device__ __forceinline__ void radial4p(const float* __restrict__ tab_e, int km
   }
 }
 
-// Density at the center from one pair: sum_q c_q exp(-alpha_q r^2).
+// Density at the center from one pair, sum_q c_q exp(-alpha_q r^2), and its
+// derivative in r^2, both scaled by 2^32 (a density of a point far from
+// every atom, or one row of a far pair, is linear in the exponentials: it
+// keeps its digits down to exp = 2^-158).
 __device__ __forceinline__ float density_term(const float* __restrict__ dens_e, int kmax, float r2h,
                                               float r2l, float* deriv) {
   float rho = 0.0f, drho = 0.0f;
   for (int q = 0; q < kmax; ++q) {
     const float4 h = *reinterpret_cast<const float4*>(dens_e + q * GMP_DENS_STRIDE);
-    const float t = __fmul_rn(h.w, gmp_exp_neg(h.x, h.y, r2h, r2l));
+    const float t = __fmul_rn(h.w, gmp_exp_neg_shifted(h.x, h.y, r2h, r2l));
     rho = __fadd_rn(rho, t);
     drho = __fmaf_rn(-h.z, t, drho);
   }
@@ -678,7 +676,7 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
 #pragma unroll
   for (int o = 16; o; o >>= 1) rho = __fadd_rn(rho, __shfl_xor_sync(0xffffffffu, rho, o));
   __syncwarp();
-  return rho;
+  return __fmul_rn(rho, GMP_EXP_UNSHIFT);
 }
 
 template <int L, int NS>
@@ -885,7 +883,7 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
       if constexpr (PACKED)
         radial4p<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, R);
       else
-        radial4s<L, L + 2, false, PADG>(tab_e, P.kmax, sg, r2h, r2l, R);
+        radial4s<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, R);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float nb = P.nbeta[4 * sg + u];
@@ -924,6 +922,10 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
       g[1] = __fmaf_rn(c, dy, g[1]);
       g[2] = __fmaf_rn(c, dz, g[2]);
     }
+    // the radial factors carried 2^32
+    g[0] = __fmul_rn(g[0], GMP_EXP_UNSHIFT);
+    g[1] = __fmul_rn(g[1], GMP_EXP_UNSHIFT);
+    g[2] = __fmul_rn(g[2], GMP_EXP_UNSHIFT);
     if (j != (int32_t)i) {  // images of the center itself do not move relative to it
       if (K.gbins) {
         bin_add(K.gbins + (3 * (int64_t)j + 0) * kGradBins, g[0]);
@@ -1118,13 +1120,17 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           constexpr int o = decltype(oo)::value;
           if (o < P.n_ord) {
             float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
-            dst[0] = acc[o][0]; dst[1] = acc[o][1]; dst[2] = acc[o][2];
+            dst[0] = acc[o][0] * GMP_EXP_UNSHIFT;
+            dst[1] = acc[o][1] * GMP_EXP_UNSHIFT;
+            dst[2] = acc[o][2] * GMP_EXP_UNSHIFT;
           }
         });
       }
       if (dens_lane) {
         float* dst = K.jac + (row * P.F + P.dens_col) * 3;
-        dst[0] = dacc[0]; dst[1] = dacc[1]; dst[2] = dacc[2];
+        dst[0] = dacc[0] * GMP_EXP_UNSHIFT;
+        dst[1] = dacc[1] * GMP_EXP_UNSHIFT;
+        dst[2] = dacc[2] * GMP_EXP_UNSHIFT;
       }
     };
     for (int64_t p = pa; p < pb; ++p) {
@@ -1149,15 +1155,16 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
         float S1[SH::NIND1];
         const float r2c = mcsh_r2(dx, dy, dz);
         GmpMcsh<L + 1>::eval(dx, dy, dz, r2c, S1);
-        // radial factors of this lane's sigma, orders 0..L+1 (double-float
-        // exponent argument: a row of one neighbor averages no other terms)
+        // radial factors of this lane's sigma, orders 0..L+1, scaled by 2^32
+        // (double-float exponent argument: a row of one neighbor averages no
+        // other terms)
         float Rl[L + 2];
 #pragma unroll
         for (int l = 0; l < L + 2; ++l) Rl[l] = 0.0f;
         const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax, false);
         for (int q = 0; q < P.kmax; ++q) {
           const float* ent = tab_e + ((s / 4) * P.kmax + q) * gmp_rad_block(L) * 4 + (s % 4);
-          const float E = gmp_exp_neg(ent[0], ent[4], r2h, r2l);
+          const float E = gmp_exp_neg_shifted(ent[0], ent[4], r2h, r2l);
 #pragma unroll
           for (int l = 0; l < L + 2; ++l) Rl[l] = __fmaf_rn(ent[4 * (2 + l)], E, Rl[l]);
         }
@@ -1233,13 +1240,17 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           constexpr int o = decltype(oo)::value;
           if (o < P.n_ord) {
             float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
-            dst[0] = self[o][0]; dst[1] = self[o][1]; dst[2] = self[o][2];
+            dst[0] = self[o][0] * GMP_EXP_UNSHIFT;
+            dst[1] = self[o][1] * GMP_EXP_UNSHIFT;
+            dst[2] = self[o][2] * GMP_EXP_UNSHIFT;
           }
         });
       }
       if (dens_lane) {
         float* dst = K.jac + (row * P.F + P.dens_col) * 3;
-        dst[0] = dself[0]; dst[1] = dself[1]; dst[2] = dself[2];
+        dst[0] = dself[0] * GMP_EXP_UNSHIFT;
+        dst[1] = dself[1] * GMP_EXP_UNSHIFT;
+        dst[2] = dself[2] * GMP_EXP_UNSHIFT;
       }
     }
     __syncwarp();

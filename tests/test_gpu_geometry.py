@@ -1,14 +1,15 @@
 """Geometry stress cases on the GPU against the FP64 oracle: images lying on
 the cutoff sphere to the last bit (and within 1e-11 A of it), coordinates
 far from the origin, and small or strongly skewed cells whose cutoff spans
-several cell widths.  Neighbor sets bit-exact, features and position
+several cell widths, and lone pairs whose exponentials fall below the
+smallest normal FP32 number.  Neighbor sets bit-exact, features and position
 gradients within the parity tolerances."""
 import numpy as np
 import pytest
 
 from paper_2303_12980_gb300 import synth
 
-from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors
+from parity import FEAT_TOL, GRAD_TAU, GRAD_TOL, JAC_TAU, feature_errors, grad_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -194,3 +195,57 @@ def test_many_flags_over_two_sigma_passes(torch, oracle_mod):
     ref, fabs = oracle_mod.features(w, centers, want_abs=True)
     err = feature_errors(f.cpu().numpy()[centers], ref, fabs)
     assert err.max() <= FEAT_TOL, err.max()
+
+
+@pytest.mark.parametrize("sigmas", [[0.1], [0.1, 0.25, 0.6]])
+def test_far_pairs_below_fp32_normal_range(torch, oracle_mod, sigmas):
+    """Two-atom clusters of one element (a single Gaussian, alpha = 4) at
+    4.6, 4.9 and 5.3 A: exp(-alpha r^2) is 2e-37, 2e-42 and 2e-49, the
+    probe's exp(-B r^2) at sigma = 0.1 straddles 2^-126 as well.  A row of
+    the Jacobian (or, with sigma = 0.1 alone, an atom's whole gradient)
+    then consists of those terms only, multiplied by adjoints of order 10,
+    and a density at a point 4.69 A from the atom (exp(-alpha r^2) = 6e-39)
+    is a single such term: a factor flushed to zero, or kept with the few
+    digits of an FP32 subnormal, shows there.  Features, Jacobian rows, the
+    VJP of every atom, the strain derivative and features at such points
+    against the oracle."""
+    u = np.array([0.48, -0.6, 0.64])
+    u /= np.linalg.norm(u)
+    parts = [(np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0] + r * u]), np.zeros(2, np.int32), np.zeros((3, 3)),
+              (0, 0, 0)) for r in (4.6, 4.9, 5.3)]
+    base = synth.Workload(name="far_pairs", positions=np.zeros((0, 3)), cells=np.zeros((0, 3, 3)),
+                          pbc=np.zeros((0, 3), np.uint8), atom_off=np.zeros(1, np.int64),
+                          species=np.zeros(0, np.int32), n_gauss=np.array([1], np.int32),
+                          gauss_coef=np.array([5.0]), gauss_exp=np.array([4.0]), orders=[-1, 0, 1, 2, 3, 4],
+                          sigmas=sigmas, cutoff=5.5)
+    w = _batch(base, parts)
+    # the 4.9 A pair exercises the band: its density row lies below 2^-126
+    # (a flushed zero is off by ~3% of that floor), its order-0 row at
+    # sigma = 0.1 above it (a flushed zero is off by 100%)
+    ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, None, want_abs=True)
+    row = ooff[2] + 1
+    assert oj[row] == 3
+    assert 1e-41 < np.linalg.norm(ojac[row, 0]) < 2.0 ** -126 < np.linalg.norm(ojac[row, 1])
+    _check(torch, oracle_mod, w)
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    _, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=5)
+    _, _, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    # points 4.69 A from one atom of each cluster, beyond the cutoff of the other
+    pts = np.stack([w.positions[2 * s] - 4.69 * u for s in range(3)])
+    poff = np.arange(4, dtype=np.int64)
+    fp = F.featurize_points(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(pts).cuda(), poff)
+    torch.cuda.synchronize()
+    assert np.array_equal(joff.cpu().numpy(), ooff) and np.array_equal(jj.cpu().numpy(), oj)
+    err = grad_errors(jac.cpu().numpy(), ojac, oabs, tau=JAC_TAU)
+    assert err.max() <= GRAD_TOL, err.max()
+    W, Wa = oracle_mod.virial(w, g.astype(np.float64), want_abs=True)
+    verr = np.abs(vir.cpu().numpy() - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    assert verr.max() <= GRAD_TOL, verr.max()
+    ref, fabs = oracle_mod.point_features(w, pts, np.arange(3), want_abs=True)
+    assert 2.0 ** -126 < ref[:, 0].min()  # a flushed density would be off by 100%
+    perr = feature_errors(fp.cpu().numpy(), ref, fabs)
+    assert perr.max() <= FEAT_TOL, perr.max()

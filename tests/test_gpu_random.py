@@ -3,13 +3,15 @@ triclinic cells (shear up to 0.3 of a cell length), every mix of periodic
 and open axes, 4-48 atoms of three elements, random order subsets of -1..6
 and 1-24 sigmas (two 16-sigma passes above 16), cutoff 5.5 A.  Neighbor
 sets bit-exact, features of every center and the position gradients of
-sampled atoms within the parity tolerances."""
+sampled atoms within the parity tolerances; on some of them also the
+dense Jacobian rows, the strain derivatives and features at random
+reference points."""
 import numpy as np
 import pytest
 
 from paper_2303_12980_gb300 import synth
 
-from parity import FEAT_TOL, GRAD_TOL, feature_errors, grad_errors
+from parity import FEAT_TOL, GRAD_TAU, GRAD_TOL, JAC_TAU, feature_errors, grad_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -42,15 +44,7 @@ def _structure(rng):
     return pos, rng.integers(0, 3, len(pos)).astype(np.int32), cell, pbc
 
 
-@pytest.mark.parametrize("seed,orders,n_sig", [(21, [0, 1, 2, 3, 4, 5, 6], 6),
-                                               (22, [-1, 0, 2, 5], 24),
-                                               (23, [1, 3, 4, 6], 11),
-                                               (24, [-1], 1),
-                                               (25, [6], 17),
-                                               (26, [4, 0, -1, 2], 3),
-                                               (27, [0, 1, 2, 3, 4], 8),
-                                               (28, [-1, 0, 1, 2, 3, 4, 5, 6], 16)])
-def test_random_batches_against_oracle(torch, oracle_mod, seed, orders, n_sig):
+def _batch(seed, orders, n_sig):
     rng = np.random.default_rng(seed)
     parts = [_structure(rng) for _ in range(12)]
     n_gauss, coef, expo = synth.gaussian_table(rng, [2, 5, 7], 3)
@@ -60,6 +54,59 @@ def test_random_batches_against_oracle(torch, oracle_mod, seed, orders, n_sig):
         atom_off=np.concatenate([[0], np.cumsum([len(p) for p, _, _, _ in parts])]).astype(np.int64),
         species=np.concatenate([s for _, s, _, _ in parts]), n_gauss=n_gauss, gauss_coef=coef,
         gauss_exp=expo, orders=orders, sigmas=[float(s) for s in np.geomspace(0.1, 1.2, n_sig)], cutoff=5.5)
+    return w, rng
+
+
+@pytest.mark.parametrize("seed,orders,n_sig", [(31, [0, 1, 2, 3, 4], 8), (32, [-1, 2, 6], 5),
+                                               (33, [-1, 0, 1, 2, 3, 4, 5, 6], 18)])
+def test_random_jacobian_virial_points(torch, oracle_mod, seed, orders, n_sig):
+    w, rng = _batch(seed, orders, n_sig)
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    # dense Jacobian rows of every center
+    feat, joff, jj, jac = F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc)
+    torch.cuda.synchronize()
+    joff, jj, jac = joff.cpu().numpy(), jj.cpu().numpy(), jac.cpu().numpy()
+    centers = np.arange(w.n_atoms)
+    ooff, oj, ojac, oabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+    assert np.array_equal(joff, ooff) and np.array_equal(jj, oj)
+    err = grad_errors(jac, ojac, oabs, tau=JAC_TAU)
+    assert err.max() <= GRAD_TOL, err.max()
+    # strain derivative per structure
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=seed)
+    _, _, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    W, Wa = oracle_mod.virial(w, g.astype(np.float64), want_abs=True)
+    verr = np.abs(vir.cpu().numpy() - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    assert verr.max() <= GRAD_TOL, verr.max()
+    # reference points: 4 per structure, anywhere in (or near) the structure
+    pts, poff = [], [0]
+    for s in range(w.n_struct):
+        a0, a1 = w.atom_off[s], w.atom_off[s + 1]
+        c = w.positions[a0:a1].mean(0)
+        pts.append(c + rng.uniform(-4.0, 4.0, (4, 3)))
+        poff.append(poff[-1] + 4)
+    pts = np.concatenate(pts)
+    poff = np.array(poff, np.int64)
+    fp = F.featurize_points(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(pts).cuda(), poff)
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.point_features(w, pts, np.repeat(np.arange(w.n_struct), 4), want_abs=True)
+    perr = feature_errors(fp.cpu().numpy(), ref, fabs)
+    assert perr.max() <= FEAT_TOL, perr.max()
+
+
+@pytest.mark.parametrize("seed,orders,n_sig", [(21, [0, 1, 2, 3, 4, 5, 6], 6),
+                                               (22, [-1, 0, 2, 5], 24),
+                                               (23, [1, 3, 4, 6], 11),
+                                               (24, [-1], 1),
+                                               (25, [6], 17),
+                                               (26, [4, 0, -1, 2], 3),
+                                               (27, [0, 1, 2, 3, 4], 8),
+                                               (28, [-1, 0, 1, 2, 3, 4, 5, 6], 16)])
+def test_random_batches_against_oracle(torch, oracle_mod, seed, orders, n_sig):
+    w, rng = _batch(seed, orders, n_sig)
     from paper_2303_12980_gb300.binding import GMPFeaturizer
     F = GMPFeaturizer.from_workload(w)
     pos = torch.from_numpy(w.positions).cuda()
