@@ -21,8 +21,9 @@ LIB = os.path.join(BUILD, "libgmp.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# -fmad=false: no implicit FMA contraction, so the forward, VJP and Jacobian
-# kernels produce bit-identical features from the same explicit arithmetic
+# -fmad=false: no implicit FMA contraction, so the forward and VJP kernels
+# produce bit-identical features from the same pair records and explicit
+# arithmetic
 NVFLAGS = ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-fmad=false",
                   "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC,
                   "-diag-suppress", "1444"]

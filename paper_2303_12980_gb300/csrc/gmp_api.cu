@@ -972,6 +972,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
         ent[1] = (float)(B - (double)ent[0]);
         ent[2] = (float)a;
         ent[3] = (float)h->coef[off + q];
+        ent[4] = (float)(a - (double)ent[2]);
+        ent[5] = (float)(h->coef[off + q] - (double)ent[3]);
       }
       off += h->n_gauss[e];
     }
@@ -1028,6 +1030,7 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       cudaGetLastError();
       return bad("device allocation for tables failed");
     }
+    for (auto& pd : h->passes) pd.pass.exp_tab = h->exptab.as<float2>();
   }
   if (cudaMallocHost((void**)&h->h_small, 64) != cudaSuccess) { cudaGetLastError(); return bad("pinned alloc failed"); }
   if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return bad("event"); }
@@ -1201,11 +1204,14 @@ static gmp_status vjp_impl(gmp_handle h, int32_t n_struct, const int64_t* atom_o
     float* fout = feat ? feat : h->stage_feat.as<float>();
     gmpk::KParams K = base_params(h, pd, (int)g, N);
     K.features = fout;
-    if (overlap && !waited && (pd.vjp_fused && !vir)) {
+    // (tables with coefficients of both signs take the split kernels: their
+    // backward kernel computes the exponentials exactly, see radial4x)
+    const bool fused = pd.vjp_fused && !vir && !pd.pass.mixed_sign;
+    if (overlap && !waited && fused) {
       GMP_CK(cudaStreamWaitEvent(st, h->ev_in, 0), "wait grad_feat");
       waited = true;
     }
-    if (pd.vjp_fused && !vir) {
+    if (fused) {
       K.grad_feat = gf;
       K.grad_acc = h->grad_acc.as<double>();
       GMP_CK(prof_mark(h, 2, true, st), "profile");
@@ -1516,7 +1522,7 @@ gmp_status gmp_tune(gmp_handle h, int32_t n_struct, const int64_t* atom_off, con
     pd.fwd = fwd_best;
     pd.bwd = bwd_best;
     pd.fused = fused_best;
-    pd.vjp_fused = best_v < best_f + best_b ? 1 : 0;
+    pd.vjp_fused = (best_v < best_f + best_b && !pd.pass.mixed_sign) ? 1 : 0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

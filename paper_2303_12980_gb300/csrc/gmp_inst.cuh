@@ -24,9 +24,11 @@ cudaError_t launch(int kind, const KParams& K, GmpShape shape, cudaStream_t st, 
   const int tile = (kind == GMP_KIND_FORWARD && shape.tile == 32) ? 32 : 16;
   void (*fn)(KParams) = kind == GMP_KIND_FORWARD    ? (tile == 32 ? k_forward<L, NS, 32> : k_forward<L, NS, 16>)
                         : kind == GMP_KIND_VJP      ? k_vjp<L, NS>
-                        : kind == GMP_KIND_BACKWARD ? k_backward<L, NS, false>
-                        : kind == GMP_KIND_BACKWARD_VIRIAL ? k_backward<L, NS, true>
-                                                    : k_jacobian<L, NS>;
+                        : kind == GMP_KIND_BACKWARD
+                            ? (K.pass.mixed_sign ? k_backward<L, NS, false, true> : k_backward<L, NS, false, false>)
+                        : kind == GMP_KIND_BACKWARD_VIRIAL
+                            ? (K.pass.mixed_sign ? k_backward<L, NS, true, true> : k_backward<L, NS, true, false>)
+                            : k_jacobian<L, NS>;
   const int extra = kind == GMP_KIND_BACKWARD_VIRIAL ? virial_extra_floats<L, NS>() : 0;
   auto smem_of = [&](int w) {
     const bool pad = kind != GMP_KIND_BACKWARD && kind != GMP_KIND_JACOBIAN;  // these two: unpadded table

@@ -73,8 +73,11 @@ __host__ __device__ inline void gmp_unpack_shift(int32_t s, int* n) {
 // the derivative: since the exponent rate is alpha*beta/gamma = beta *
 // (alpha/gamma), d R_l / d r^2 = -beta R_{l+1} exactly.
 __host__ __device__ constexpr int gmp_rad_block(int L) { return L + 4; }
-// Density table entry per (element, primitive): Bhi, Blo, b, c with B = alpha*log2(e), b = alpha.
-#define GMP_DENS_STRIDE 4
+// Density table entry per (element, primitive): Bhi, Blo, b, c, b_lo, c_lo, 0, 0
+// with B = alpha*log2(e) split into (hi, lo), b = alpha and c rounded to FP32
+// and their rounding errors b_lo, c_lo (the double-float density of tables
+// with coefficients of both signs).
+#define GMP_DENS_STRIDE 8
 
 // Shapes of one forward/backward pass.
 struct GmpPass {
@@ -93,7 +96,9 @@ struct GmpPass {
   int ord_dense;       // 1 when ord_l[o] == o for every o (orders 0 .. n_ord-1 in order)
   const float* rad;    // [n_el][nsig_pad / 4][kmax][gmp_rad_block(lmax)] float4
   float nbeta[16];     // -beta = -1/(2 sigma^2) per sigma of the pass (0 for padding)
-  const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]
+  const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]: alpha log2(e) (hi, lo),
+                       // alpha, c, alpha's and c's low words, 0, 0
+  const float2* exp_tab;  // [64] 2^(-j/64) as double-floats (gmp_df_exp_neg)
 };
 
 // ---------------------------------------------------------------- double-float
@@ -224,6 +229,35 @@ __device__ __forceinline__ float gmp_exp_neg_shifted(float Bhi, float Blo, float
   const float e = __fadd_rn(__fadd_rn(GMP_EXP_SHIFT, -d), -xh);  // (32 - xh) - d, exactly
   const float E = gmp_ex2(d);
   return __fmaf_rn(E, -0.69314718055994531f * __fadd_rn(xl, -e), E);
+}
+
+// exp(-x) for a double-float x to about 1e-13 relative, in FP32
+// arithmetic, by table-driven reduction (Tang's method):
+// x = k ln2/64 + r with |r| <= ln2/128 (ln2/64 as a double-float), so that
+// exp(-x) = 2^-(k div 64) * 2^-((k mod 64)/64) * exp(-r); the middle factor
+// is a double-float table entry (tab[j] = 2^(-j/64)) and
+// exp(-r) = 1 - r + r^2 w, w = 1/2 + r t, t = -1/6 + r/24 - r^2/120, where
+// |r t| < 1e-3 lets t be FP32 (the omitted r^6/720 term is below 3e-17).
+// Results below the FP32 normal range (x > 87) are returned as 0.  A
+// negative x (down to about -88) works the same way: k and its shift by 6
+// are then negative, the table index k mod 64 stays in 0..63.
+__device__ __forceinline__ gmp_f2 gmp_df_exp_neg(gmp_f2 x, const float2* __restrict__ tab) {
+  if (!(x.hi <= 87.0f)) return gmp_f2{0.0f, 0.0f};
+  const float C_HI = 0.010830424726009369f, C_LO = -2.976022206446771e-11f;  // ln2/64
+  const float k = rintf(__fmul_rn(x.hi, 92.33248261689366f));                  // x * 64/ln2
+  const gmp_f2 kc = gmp_df_add(gmp_two_prod(k, C_HI), gmp_two_prod(k, C_LO));
+  const gmp_f2 r = gmp_df_add(x, gmp_df_neg(kc));
+  const float t = __fmaf_rn(r.hi, __fmaf_rn(r.hi, -0.008333333767950535f, 0.0416666679084301f),
+                            -0.1666666716337204f);
+  const gmp_f2 rt = gmp_two_prod(r.hi, t);
+  gmp_f2 w = gmp_fast_two_sum(0.5f, rt.hi);
+  w = gmp_fast_two_sum(w.hi, __fadd_rn(w.lo, rt.lo));
+  const gmp_f2 q = gmp_df_mul(gmp_df_mul(r, r), w);
+  gmp_f2 e = gmp_df_add(gmp_df_add(gmp_f2{1.0f, 0.0f}, gmp_df_neg(r)), q);
+  const int ki = (int)k;
+  const float2 T = __ldg(tab + (ki & 63));
+  e = gmp_df_mul(e, gmp_f2{T.x, T.y});
+  return gmp_f2{ldexpf(e.hi, -(ki >> 6)), ldexpf(e.lo, -(ki >> 6))};
 }
 
 // Double-float displacement of j's image n from i, and its r^2.

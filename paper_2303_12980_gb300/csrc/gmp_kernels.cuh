@@ -339,8 +339,9 @@ __device__ __forceinline__ void radial4d(const float* __restrict__ tab_e, int km
 // 2^-18 while the scaled factor is normal (|32 - B r^2| < 128), so each
 // exponential is within ~2e-6 relative: ample for derivatives, checked to
 // 1e-4.  The offset keeps the factors normal (not flushed to zero by the SFU)
-// down to exp(-B r^2) = 2^-158: a gradient term of a far pair, multiplied by
-// large adjoints, keeps its digits; the kernel scales its sums back by 2^-32.
+// down to exp(-B r^2) = 2^-158, with room for the amplitudes (alpha/gamma)^l
+// of the higher orders: a gradient term of a far pair, multiplied by large
+// adjoints, keeps its digits; the kernel scales its sums back by 2^-32.
 template <int L, int NL = L + 2, bool PADG = true>
 __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
                                          float (&R)[4][NL]) {
@@ -358,6 +359,39 @@ __device__ __forceinline__ void radial4s(const float* __restrict__ tab_e, int km
     E[1] = gmp_ex2(__fmaf_rn(bh.y, -r2h, GMP_EXP_SHIFT));
     E[2] = gmp_ex2(__fmaf_rn(bh.z, -r2h, GMP_EXP_SHIFT));
     E[3] = gmp_ex2(__fmaf_rn(bh.w, -r2h, GMP_EXP_SHIFT));
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const float4 a = blk[2 + l];
+      const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) R[u][l] = __fmaf_rn(av[u], E[u], R[u][l]);
+    }
+  }
+}
+
+// The same scaled radial factors with the exact offset and the double-float
+// exponent argument (gmp_exp_neg_shifted), for tables with coefficients of
+// both signs: there the radial factor of an element can cancel within the
+// pair, and the exponentials' errors count against sum_q |A_q| E_q rather
+// than against the factor.  (A separate instantiation of the backward
+// kernel: a runtime branch would raise the register count of every one.)
+template <int L, int NL = L + 2, bool PADG = true>
+__device__ __forceinline__ void radial4x(const float* __restrict__ tab_e, int kmax, int sg, float r2h,
+                                         float r2l, float (&R)[4][NL]) {
+  constexpr int RB = gmp_rad_block(L);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int l = 0; l < NL; ++l) R[u][l] = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < kmax; ++q) {
+    const float4* blk = reinterpret_cast<const float4*>(tab_e) + sg * rad_sg_stride(L, kmax, PADG) + q * RB;
+    const float4 bh = blk[0], bl = blk[1];
+    float E[4];
+    E[0] = gmp_exp_neg_shifted(bh.x, bl.x, r2h, r2l);
+    E[1] = gmp_exp_neg_shifted(bh.y, bl.y, r2h, r2l);
+    E[2] = gmp_exp_neg_shifted(bh.z, bl.z, r2h, r2l);
+    E[3] = gmp_exp_neg_shifted(bh.w, bl.w, r2h, r2l);
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const float4 a = blk[2 + l];
@@ -420,6 +454,83 @@ __device__ __forceinline__ float density_term(const float* __restrict__ dens_e, 
   return rho;
 }
 
+// The same density term in double-float arithmetic, scaled by 2^32, for
+// tables with coefficients of both signs: there the primitives of one
+// element can cancel, and FP32 terms (exponentials within 2 ulp, FP32
+// coefficients) would leave errors relative to sum_q |c_q| exp(-alpha_q
+// r^2) rather than to the density.  Each exponential comes from the
+// double-float argument alpha r^2 - 32 ln 2 (gmp_df_exp_neg, ~1e-13), each
+// coefficient is a double-float, and the terms are summed in double-float.
+// (Out of line: it runs only for such tables and its registers would
+// otherwise count against every forward kernel.)
+static __device__ __noinline__ gmp_f2 density_term_df(const float* __restrict__ dens_e, int kmax, float r2h,
+                                                      float r2l, const float2* __restrict__ exp_tab) {
+  const gmp_f2 r2{r2h, r2l}, nshift{-22.180709838867188f, 6.094893478802987e-08f};  // -32 ln 2
+  gmp_f2 rho{0.0f, 0.0f};
+  for (int q = 0; q < kmax; ++q) {
+    const float4 h0 = *reinterpret_cast<const float4*>(dens_e + q * GMP_DENS_STRIDE);
+    const float4 h1 = *reinterpret_cast<const float4*>(dens_e + q * GMP_DENS_STRIDE + 4);
+    const gmp_f2 E = gmp_df_exp_neg(gmp_df_add(gmp_df_mul(gmp_f2{h0.z, h1.x}, r2), nshift), exp_tab);
+    rho = gmp_df_add(rho, gmp_df_mul(gmp_f2{h0.w, h1.y}, E));
+  }
+  return rho;
+}
+
+// Tables with coefficients of both signs: the radial factor R = sum_q A_q
+// E_q of an element whose primitives differ in sign cancels within the
+// pair, and its FP32 rounding is relative to sum_q |A_q| E_q, not to |R|.
+// The refinement bound then takes B_{l,s} = sum_pairs sum_q |A_{l,q,s}| E_q
+// r^l: recomputed here over the center's pairs (lanes = sigma x pair
+// stream, FP32; a bound) and written over the slots that forward_sweep
+// filled from |R|.  The streams are reduced in a fixed order, so the bound,
+// and with it the refinement flags, are the same in every kernel.
+template <int L, int NS>
+__device__ __noinline__ void mixed_sign_bound(const GmpPass& P, const float* __restrict__ s_rad,
+                                              const GmpPair* __restrict__ pairs, int64_t p0, int M,
+                                              float* Mu) {
+  constexpr int RB = gmp_rad_block(L);
+  constexpr int NIND = (L + 1) * (L + 1);
+  constexpr int STREAMS = 32 / NS;
+  const int lane = threadIdx.x & 31;
+  const int s = lane % NS, h = lane / NS;
+  float B[L + 1];
+#pragma unroll
+  for (int l = 0; l <= L; ++l) B[l] = 0.0f;
+  if (s < P.nsig) {
+    for (int pp = h; pp < M; pp += STREAMS) {
+      float dx, dy, dz, r2h, r2l;
+      int e, j;
+      load_pair(pairs, p0 + pp, dx, dy, dz, r2h, r2l, e, j);
+      const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax);
+      float Ra[L + 1];
+#pragma unroll
+      for (int l = 0; l <= L; ++l) Ra[l] = 0.0f;
+      for (int q = 0; q < P.kmax; ++q) {
+        const float* ent = tab_e + ((size_t)(s / 4) * rad_sg_stride(L, P.kmax) + (size_t)q * RB) * 4 + (s % 4);
+        const float E = gmp_ex2(-__fmul_rn(ent[0], r2h));
+#pragma unroll
+        for (int l = 0; l <= L; ++l) Ra[l] = __fmaf_rn(fabsf(ent[4 * (2 + l)]), E, Ra[l]);
+      }
+      const float r = __fsqrt_rn(r2h);
+      float rp = 1.0f;
+#pragma unroll
+      for (int l = 0; l <= L; ++l) {
+        B[l] = __fmaf_rn(Ra[l], rp, B[l]);
+        rp = __fmul_rn(rp, r);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = NS; o < 32; o <<= 1)
+#pragma unroll
+    for (int l = 0; l <= L; ++l) B[l] = __fadd_rn(B[l], __shfl_xor_sync(0xffffffffu, B[l], o));
+  __syncwarp();
+  if (h == 0 && s < P.nsig)
+#pragma unroll
+    for (int l = 0; l <= L; ++l) Mu[NS * NIND + s * (L + 1) + l] = B[l];
+  __syncwarp();
+}
+
 // Shared memory: tables first (radial then density), then one region per warp.
 
 
@@ -453,6 +564,8 @@ __device__ __forceinline__ void load_tables(const GmpPass& P, int NS, float* s_r
 // Forward sweep over one center's pairs: leaves mu (FP32, rounded from the
 // compensated pair) in Mu[s * NIND + k] and the conditioning bound
 // B_{l,s} = sum_pairs |R_{l,s}| r^l in Mu[NS * NIND + s * (L+1) + l]
+// (with coefficients of both signs, sum over pairs and primitives of
+// |A_q E_q| r^l: mixed_sign_bound)
 // (warp-private shared memory), and returns the density (all lanes).
 // The contraction runs over items of 4 sigmas x CW components (CW = 4 or
 // 2, whichever the shape fills the warp's lanes with in fewer
@@ -568,10 +681,18 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
           *reinterpret_cast<float4*>(rrow + l * NS + 4 * sg) = make_float4(R[0][l], R[1][l], R[2][l], R[3][l]);
       }
       if (P.want_density && half == 0) {
-        const float t = density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, nullptr);
-        const gmp_f2 s2 = gmp_two_sum(rho_hi, t);
-        rho_hi = s2.hi;
-        rho_lo += s2.lo;
+        const float* dens_e = s_dens + (size_t)e * dens_elem_stride(P.kmax);
+        if (mixed) {
+          const gmp_f2 t = density_term_df(dens_e, P.kmax, r2h, r2l, P.exp_tab);
+          const gmp_f2 s2 = gmp_two_sum(rho_hi, t.hi);
+          rho_hi = s2.hi;
+          rho_lo = __fadd_rn(rho_lo, __fadd_rn(s2.lo, t.lo));
+        } else {
+          const float t = density_term(dens_e, P.kmax, r2h, r2l, nullptr);
+          const gmp_f2 s2 = gmp_two_sum(rho_hi, t);
+          rho_hi = s2.hi;
+          rho_lo += s2.lo;
+        }
       }
     }
     __syncwarp();
@@ -671,10 +792,21 @@ __device__ __forceinline__ float forward_sweep(const GmpPass& P, const float* __
         Mu[NS * SH::NIND + (4 * it_sb[q] + u) * (L + 1) + l] =
             __fadd_rn(hi[q][CW * u + CW - 1], lo[q][CW * u + CW - 1]);
   }
-  // density: warp total
-  float rho = __fadd_rn(rho_hi, rho_lo);
+  if (mixed) mixed_sign_bound<L, NS>(P, s_rad, pairs, p0, M, Mu);
+  // density: warp total (double-float with coefficients of both signs,
+  // whose lane sums may cancel)
+  float rho;
+  if (mixed) {
+    gmp_f2 t{rho_hi, rho_lo};
 #pragma unroll
-  for (int o = 16; o; o >>= 1) rho = __fadd_rn(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+    for (int o = 16; o; o >>= 1)
+      t = gmp_df_add(t, gmp_f2{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)});
+    rho = __fadd_rn(t.hi, t.lo);
+  } else {
+    rho = __fadd_rn(rho_hi, rho_lo);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rho = __fadd_rn(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+  }
   __syncwarp();
   return __fmul_rn(rho, GMP_EXP_UNSHIFT);
 }
@@ -849,7 +981,7 @@ __device__ __forceinline__ void pair_gradient(const float* lam, float A, float d
 // PACKED: radial factors on packed FP32 pairs (same results, fewer issue
 // slots; the plain backward kernel uses them, the strain-derivative variant
 // would spill at the 168 registers of the 12-warp launch).
-template <int L, int NS, bool VIRIAL = false, bool PACKED = false, bool PADG = true>
+template <int L, int NS, bool VIRIAL = false, bool PACKED = false, bool PADG = true, bool MIXED = false>
 __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __restrict__ s_rad,
                                                const float* __restrict__ s_dens, int64_t i, int64_t p0, int M,
                                                const float* __restrict__ Lam, float gd, float* Wv = nullptr) {
@@ -880,7 +1012,9 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax, PADG);
     for (int sg = 0; sg < SH::NSB; ++sg) {
       float R[4][L + 2];
-      if constexpr (PACKED)
+      if constexpr (MIXED)
+        radial4x<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, r2l, R);
+      else if constexpr (PACKED)
         radial4p<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, R);
       else
         radial4s<L, L + 2, PADG>(tab_e, P.kmax, sg, r2h, R);
@@ -914,18 +1048,18 @@ __device__ __forceinline__ void backward_sweep(const KParams& K, const float* __
     GmpMcsh<L + 1>::eval_top(dx, dy, dz, r2c, S);
     float g[3];
     pair_gradient<L>(lam, A, dx, dy, dz, r2c, S, g);
-    if (P.want_density && gd != 0.0f) {
-      float drho;
-      density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
-      const float c = __fmul_rn(__fmul_rn(gd, 2.0f), drho);
-      g[0] = __fmaf_rn(c, dx, g[0]);
-      g[1] = __fmaf_rn(c, dy, g[1]);
-      g[2] = __fmaf_rn(c, dz, g[2]);
-    }
     // the radial factors carried 2^32
     g[0] = __fmul_rn(g[0], GMP_EXP_UNSHIFT);
     g[1] = __fmul_rn(g[1], GMP_EXP_UNSHIFT);
     g[2] = __fmul_rn(g[2], GMP_EXP_UNSHIFT);
+    if (P.want_density && gd != 0.0f) {
+      float drho;  // scaled by 2^32
+      density_term(s_dens + (size_t)e * dens_elem_stride(P.kmax), P.kmax, r2h, r2l, &drho);
+      const float c = __fmul_rn(__fmul_rn(__fmul_rn(gd, 2.0f), drho), GMP_EXP_UNSHIFT);
+      g[0] = __fmaf_rn(c, dx, g[0]);
+      g[1] = __fmaf_rn(c, dy, g[1]);
+      g[2] = __fmaf_rn(c, dz, g[2]);
+    }
     if (j != (int32_t)i) {  // images of the center itself do not move relative to it
       if (K.gbins) {
         bin_add(K.gbins + (3 * (int64_t)j + 0) * kGradBins, g[0]);
@@ -995,7 +1129,7 @@ __global__ void __launch_bounds__(256) k_vjp(KParams K) {
   }
 }
 
-template <int L, int NS, bool VIRIAL = false>
+template <int L, int NS, bool VIRIAL = false, bool MIXED = false>
 __global__ void __launch_bounds__(384) k_backward(KParams K) {
   using SH = Shape<L, NS>;
   extern __shared__ __align__(16) float smem[];
@@ -1023,7 +1157,7 @@ __global__ void __launch_bounds__(384) k_backward(KParams K) {
     const float* grow = K.grad_feat + i * P.F;
     adjoints<L, NS>(P, Mu, grow, Lam);
     const float gd = P.want_density ? grow[P.dens_col] : 0.0f;
-    backward_sweep<L, NS, VIRIAL, !VIRIAL, PADG>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
+    backward_sweep<L, NS, VIRIAL, !VIRIAL && !MIXED, PADG, MIXED>(K, s_rad, s_dens, i, p0, M, Lam, gd, Wv);
     __syncwarp();
   }
 }

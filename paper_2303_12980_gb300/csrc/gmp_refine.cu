@@ -20,33 +20,6 @@
 
 namespace {
 
-// exp(-x) for a double-float x >= 0 to about 1e-13 relative, in FP32
-// arithmetic, by table-driven reduction (Tang's method):
-// x = k ln2/64 + r with |r| <= ln2/128 (ln2/64 as a double-float), so that
-// exp(-x) = 2^-(k div 64) * 2^-((k mod 64)/64) * exp(-r); the middle factor
-// is a double-float table entry (tab[j] = 2^(-j/64)) and
-// exp(-r) = 1 - r + r^2 w, w = 1/2 + r t, t = -1/6 + r/24 - r^2/120, where
-// |r t| < 1e-3 lets t be FP32 (the omitted r^6/720 term is below 3e-17).
-// Results below the FP32 normal range (x > 87) are returned as 0.
-__device__ __forceinline__ gmp_f2 df_exp_neg(gmp_f2 x, const float2* __restrict__ tab) {
-  if (!(x.hi <= 87.0f)) return gmp_f2{0.0f, 0.0f};
-  const float C_HI = 0.010830424726009369f, C_LO = -2.976022206446771e-11f;  // ln2/64
-  const float k = rintf(__fmul_rn(x.hi, 92.33248261689366f));                  // x * 64/ln2
-  const gmp_f2 kc = gmp_df_add(gmp_two_prod(k, C_HI), gmp_two_prod(k, C_LO));
-  const gmp_f2 r = gmp_df_add(x, gmp_df_neg(kc));
-  const float t = __fmaf_rn(r.hi, __fmaf_rn(r.hi, -0.008333333767950535f, 0.0416666679084301f),
-                            -0.1666666716337204f);
-  const gmp_f2 rt = gmp_two_prod(r.hi, t);
-  gmp_f2 w = gmp_fast_two_sum(0.5f, rt.hi);
-  w = gmp_fast_two_sum(w.hi, __fadd_rn(w.lo, rt.lo));
-  const gmp_f2 q = gmp_df_mul(gmp_df_mul(r, r), w);
-  gmp_f2 e = gmp_df_add(gmp_df_add(gmp_f2{1.0f, 0.0f}, gmp_df_neg(r)), q);
-  const int ki = (int)k;
-  const float2 T = __ldg(tab + (ki & 63));
-  e = gmp_df_mul(e, gmp_f2{T.x, T.y});
-  return gmp_f2{ldexpf(e.hi, -(ki >> 6)), ldexpf(e.lo, -(ki >> 6))};
-}
-
 // Sigmas recomputed together: the displacement and the MCSH components of a
 // pair serve all of them, the radial factor is per sigma.  Only orders 4
 // and 5 take pairs of sigmas.  Below order 4 the components are cheap and
@@ -88,7 +61,7 @@ __device__ __forceinline__ void refine_moments(int lane, const float4& xhi, cons
       const float* te = ktab + ((size_t)pr.e * nsig_total + sig[g]) * kmax * 16;  // [element][sigma][primitive]
       for (int q = 0; q < kmax; ++q) {
         const float* ent = te + q * 16;
-        const gmp_f2 E = df_exp_neg(gmp_df_mul(gmp_f2{ent[0], ent[1]}, r2), exp_tab);
+        const gmp_f2 E = gmp_df_exp_neg(gmp_df_mul(gmp_f2{ent[0], ent[1]}, r2), exp_tab);
         R = gmp_df_add(R, gmp_df_mul(gmp_f2{ent[2 + 2 * L], ent[3 + 2 * L]}, E));
       }
 #pragma unroll

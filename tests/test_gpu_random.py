@@ -128,3 +128,92 @@ def test_random_batches_against_oracle(torch, oracle_mod, seed, orders, n_sig):
     gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
     gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
     assert gerr.max() <= GRAD_TOL, gerr.max()
+
+
+def _random_tables(rng, n_el):
+    """Per-element Gaussian tables of 1-8 primitives, exponents 0.1-20 A^-2,
+    coefficients 0.05-2 with about one in five negative."""
+    n_gauss = rng.integers(1, 9, n_el).astype(np.int32)
+    k = int(n_gauss.sum())
+    expo = np.exp(rng.uniform(np.log(0.1), np.log(20.0), k))
+    coef = rng.uniform(0.05, 2.0, k) * np.where(rng.uniform(size=k) < 0.2, -1.0, 1.0)
+    return n_gauss, coef, expo
+
+
+@pytest.mark.parametrize("seed", [41, 42, 43, 44, 45, 46, 47])
+def test_random_tables_chunks_and_graph_replay(torch, oracle_mod, seed):
+    """Random probe sets on random batches: 1-5 elements with 1-8 Gaussians
+    of either sign, a random order subset, 1-20 sigmas in random order, a
+    cutoff of 3.5-7 A.  Neighbor sets bit-exact; features and the VJP of
+    sampled atoms against the oracle; the Jacobian call's features too, its
+    rows taken in three center chunks bit-identical to the whole-batch call
+    and matching the oracle on sampled centers; CUDA-graph replays on a side stream give the eager
+    results bit for bit."""
+    rng = np.random.default_rng(seed)
+    n_el = int(rng.integers(1, 6))
+    parts = [_structure(rng) for _ in range(10)]
+    n_gauss, coef, expo = _random_tables(rng, n_el)
+    orders = sorted(rng.choice(np.arange(-1, 7), int(rng.integers(1, 9)), replace=False).tolist())
+    rng.shuffle(orders)
+    sig = rng.permutation(np.geomspace(0.08, 1.4, int(rng.integers(1, 21)))).tolist()
+    w = synth.Workload(
+        name="random_tables", positions=np.ascontiguousarray(np.concatenate([p for p, _, _, _ in parts])),
+        cells=np.stack([c for _, _, c, _ in parts]), pbc=np.stack([b for _, _, _, b in parts]),
+        atom_off=np.concatenate([[0], np.cumsum([len(p) for p, _, _, _ in parts])]).astype(np.int64),
+        species=np.concatenate([s % n_el for _, s, _, _ in parts]).astype(np.int32), n_gauss=n_gauss,
+        gauss_coef=coef, gauss_exp=expo, orders=[int(o) for o in orders], sigmas=sig,
+        cutoff=float(rng.uniform(3.5, 7.0)))
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    noff, nj, nsh = F.neighbors(pos, sp, w.atom_off, w.cells, w.pbc)
+    ooff, oj, osh, _ = oracle_mod.neighbors(w)
+    assert np.array_equal(noff.cpu().numpy(), ooff)
+    assert np.array_equal(nj.cpu().numpy(), oj)
+    assert np.array_equal(nsh.cpu().numpy(), osh)
+    g = torch.from_numpy(synth.upstream_gradient(w.n_atoms, w.n_features, seed=seed)).cuda()
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g)
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    err = feature_errors(feat.cpu().numpy(), ref, fabs)
+    assert err.max() <= FEAT_TOL, err.max()
+    atoms = rng.choice(w.n_atoms, 16, replace=False)
+    gref, gscale = oracle_mod.vjp_atoms(w, g.cpu().numpy(), atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    assert gerr.max() <= GRAD_TOL, gerr.max()
+    # the Jacobian whole and in three chunks
+    fw, jo, jj, jac = (t.cpu().numpy() for t in F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc))
+    # (its records are sorted by neighbor atom, not grouped by species: the
+    # features agree to rounding, not bit for bit)
+    err = feature_errors(fw, ref, fabs)
+    assert err.max() <= FEAT_TOL, err.max()
+    cuts = np.sort(rng.choice(np.arange(1, w.n_atoms), 2, replace=False))
+    for b, e in zip([0, cuts[0], cuts[1]], [cuts[0], cuts[1], w.n_atoms]):
+        fc, jc, jjc, jacc = (t.cpu().numpy() for t in
+                             F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc, centers=(int(b), int(e))))
+        assert np.array_equal(fc, fw[b:e])
+        assert np.array_equal(jc, jo[b:e + 1] - jo[b])
+        assert np.array_equal(jjc, jj[jo[b]:jo[e]]) and np.array_equal(jacc, jac[jo[b]:jo[e]])
+    centers = np.sort(rng.choice(w.n_atoms, 24, replace=False))
+    co, cj, cjac, cabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+    for t, i in enumerate(centers):
+        a, b = jo[i], jo[i + 1]
+        assert np.array_equal(jj[a:b], cj[co[t]:co[t + 1]])
+        jerr = grad_errors(jac[a:b], cjac[co[t]:co[t + 1]], cabs[co[t]:co[t + 1]], tau=JAC_TAU)
+        assert jerr.max() <= GRAD_TOL, (i, jerr.max())
+    # graph replays on a side stream, positions moved in place between calls
+    Fg = GMPFeaturizer.from_workload(w)
+    Fg.set_graph(True)
+    s = torch.cuda.Stream()
+    fo = torch.empty_like(feat)
+    go = torch.empty_like(gp)
+    with torch.cuda.stream(s):
+        for step in range(3):
+            if step:
+                pos += 0.01 * torch.randn_like(pos)
+            Fg.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g, out=(fo, go))
+            fe, ge = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, g)
+            s.synchronize()
+            assert torch.equal(fo, fe), step
+            assert torch.equal(go, ge), step
