@@ -304,6 +304,32 @@ def test_vjp_bitwise_reproducible(torch, name):
             assert torch.equal(g1, ref[fused][1]), k
 
 
+@pytest.mark.parametrize("name", ["fcc4096", "batched300", "random64_box"])
+def test_fused_vjp_parity(torch, oracle_mod, name):
+    """The fused forward+backward kernel (an autotuner choice) against the
+    oracle: its adjoints come from the FP32 moments, not the refined ones,
+    so its gradient is checked on its own, on sampled atoms of a jittered
+    crystal (many refined features), a batch and a random box."""
+    w = wl(name)
+    pos, sp = _dev(torch, w)
+    F = _featurizer(w)
+    vals = list(F.tuning())
+    for p in range(len(vals) // 6):
+        vals[6 * p + 3], vals[6 * p + 4] = 1, 4
+    F.set_tuning(vals)
+    g = synth.upstream_gradient(w.n_atoms, w.n_features, seed=23)
+    feat, gp = F.featurize_vjp(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    ferr = feature_errors(feat.cpu().numpy(), ref, fabs)
+    atoms = synth.subset_centers(w.n_atoms, 64, seed=6)
+    gref, gscale = oracle_mod.vjp_atoms(w, g, atoms, want_abs=True)
+    gerr = grad_errors(gp.cpu().numpy()[atoms], gref, gscale)
+    record(f"vjp_fused/{name}", features_max_rel_err=ferr.max(), vjp_max_rel_err=gerr.max())
+    assert ferr.max() <= FEAT_TOL, ferr.max()
+    assert gerr.max() <= GRAD_TOL, gerr.max()
+
+
 def test_graph_replay_matches_eager(torch):
     """Graph mode: replays on the same buffers give the eager results, follow
     in-place position updates, and fall back eagerly when the batch outgrows
