@@ -115,7 +115,7 @@ def work_model(w, pairs: int):
 # dram__bytes_read.sum + dram__bytes_write.sum over its 4,585,082 pairs),
 # scaled by the pairs of the run.  Update with the ncu summaries whenever
 # the kernels change.
-TRAFFIC_PER_PAIR = {"forward": (147.333888e6 + 79.133696e6) / 4585082,
+TRAFFIC_PER_PAIR = {"forward": (147.323648e6 + 78.938368e6) / 4585082,
                     "backward": (272.870400e6 + 6.337536e6) / 4585082}
 
 
