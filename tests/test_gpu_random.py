@@ -147,8 +147,10 @@ def test_random_tables_chunks_and_graph_replay(torch, oracle_mod, seed):
     cutoff of 3.5-7 A.  Neighbor sets bit-exact; features and the VJP of
     sampled atoms against the oracle; the Jacobian call's features too, its
     rows taken in three center chunks bit-identical to the whole-batch call
-    and matching the oracle on sampled centers; CUDA-graph replays on a side stream give the eager
-    results bit for bit."""
+    and matching the oracle on sampled centers; the strain derivatives and
+    features at random points near each structure against the oracle;
+    CUDA-graph replays on a side stream give the eager results bit for
+    bit."""
     rng = np.random.default_rng(seed)
     n_el = int(rng.integers(1, 6))
     parts = [_structure(rng) for _ in range(10)]
@@ -202,6 +204,20 @@ def test_random_tables_chunks_and_graph_replay(torch, oracle_mod, seed):
         assert np.array_equal(jj[a:b], cj[co[t]:co[t + 1]])
         jerr = grad_errors(jac[a:b], cjac[co[t]:co[t + 1]], cabs[co[t]:co[t + 1]], tau=JAC_TAU)
         assert jerr.max() <= GRAD_TOL, (i, jerr.max())
+    # strain derivative of each structure, and features at random points
+    # near each structure (some far from every atom)
+    _, _, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, g)
+    pts = np.concatenate([w.positions[w.atom_off[t]:w.atom_off[t + 1]].mean(0) + rng.uniform(-6.0, 6.0, (3, 3))
+                          for t in range(w.n_struct)])
+    poff = np.arange(0, 3 * w.n_struct + 1, 3, dtype=np.int64)
+    fp = F.featurize_points(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(pts).cuda(), poff)
+    torch.cuda.synchronize()
+    W, Wa = oracle_mod.virial(w, g.cpu().numpy().astype(np.float64), want_abs=True)
+    verr = np.abs(vir.cpu().numpy() - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    assert verr.max() <= GRAD_TOL, verr.max()
+    pref, pabs = oracle_mod.point_features(w, pts, np.repeat(np.arange(w.n_struct), 3), want_abs=True)
+    perr = feature_errors(fp.cpu().numpy(), pref, pabs)
+    assert perr.max() <= FEAT_TOL, perr.max()
     # graph replays on a side stream, positions moved in place between calls
     Fg = GMPFeaturizer.from_workload(w)
     Fg.set_graph(True)
