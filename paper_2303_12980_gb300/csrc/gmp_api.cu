@@ -932,11 +932,24 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
     const int RB = gmp_rad_block(L), NSB = pd.NS / 4;
     std::vector<float> tab((size_t)h->n_el * NSB * h->kmax * RB * 4, 0.0f);
     int64_t off = 0;
+    double rbound[16] = {0};  // per sigma: see GmpPass::jac_exp
+    const double rc = h->cutoff;
     for (int e = 0; e < h->n_el; ++e) {
       for (int s = 0; s < ns; ++s) {
         const double sig = h->sigmas[s0 + s];
         const double beta = 1.0 / (2.0 * sig * sig);
         const double Ns = std::pow(2.0 * M_PI * sig * sig, -1.5);
+        // each primitive's |A_0| exp(-b r^2) max(1, r)^(L+1) at its largest on
+        // [0, rc] (r^2 = (L+1)/(2b) clamped to [1, rc^2]); |A_l| <= |A_0|
+        double bsum = 0.0;
+        for (int q = 0; q < h->n_gauss[e]; ++q) {
+          const double a = h->alpha[off + q], c = h->coef[off + q];
+          const double gam = a + beta, b = a * beta / gam;
+          const double K0 = std::fabs(c * Ns * std::pow(M_PI / gam, 1.5));
+          const double r2 = std::min(std::max((L + 1) / (2.0 * b), 1.0), std::max(rc * rc, 1.0));
+          bsum += std::max(K0, K0 * std::exp(-b * r2) * std::pow(r2, 0.5 * (L + 1)));
+        }
+        rbound[s] = std::max(rbound[s], bsum);
         for (int q = 0; q < h->n_gauss[e]; ++q) {
           const double a = h->alpha[off + q], c = h->coef[off + q];
           const double gam = a + beta;
@@ -958,6 +971,8 @@ gmp_status gmp_create(const gmp_params* p, int device, gmp_handle* out) {
       return bad("device allocation for tables failed");
     }
     P.rad = pd.rad.as<float>();
+    for (int s = 0; s < 16; ++s)
+      P.jac_exp[s] = rbound[s] > 0.0 ? (int)std::ceil(std::log2(rbound[s])) : 0;
     h->passes.push_back(std::move(pd));
   }
   {

@@ -99,6 +99,12 @@ struct GmpPass {
   const float* dens;   // [n_el][kmax][GMP_DENS_STRIDE]: alpha log2(e) (hi, lo),
                        // alpha, c, alpha's and c's low words, 0, 0
   const float2* exp_tab;  // [64] 2^(-j/64) as double-floats (gmp_df_exp_neg)
+  // per sigma of the pass: ceil(log2) of the largest, over elements, of
+  // sum_q max_{0 <= r <= cutoff} |A_{0,q,s}| exp(-B_{q,s} r^2) max(1, r)^(lmax+1)
+  // (a bound on |R_{l,s}(r)| max(1, r)^(lmax+1), orders 0..lmax+1): with the
+  // adjoints' size it bounds the Jacobian kernel's intermediates (its
+  // exponent offset per center and sigma)
+  int jac_exp[16];
 };
 
 // ---------------------------------------------------------------- double-float
@@ -220,15 +226,21 @@ __device__ __forceinline__ float gmp_exp_neg(float Bhi, float Blo, float r2hi, f
 // error is 0.  The error joins the low part of the argument.
 #define GMP_EXP_SHIFT 32.0f
 #define GMP_EXP_UNSHIFT 0x1p-32f
-__device__ __forceinline__ float gmp_exp_neg_shifted(float Bhi, float Blo, float r2hi, float r2lo) {
+// 2^S exp(-B r^2) for an integer S in 0..126 (the same steps: S - xh is
+// rounded only when xh < S, where Fast2Sum applies; beyond it the
+// difference is exact).
+__device__ __forceinline__ float gmp_exp_neg_shifted_by(float Bhi, float Blo, float r2hi, float r2lo, float S) {
   float xh = __fmul_rn(Bhi, r2hi);
   float xl = __fmaf_rn(Bhi, r2hi, -xh);
   xl = __fmaf_rn(Bhi, r2lo, xl);
   xl = __fmaf_rn(Blo, r2hi, xl);
-  const float d = __fadd_rn(GMP_EXP_SHIFT, -xh);
-  const float e = __fadd_rn(__fadd_rn(GMP_EXP_SHIFT, -d), -xh);  // (32 - xh) - d, exactly
+  const float d = __fadd_rn(S, -xh);
+  const float e = __fadd_rn(__fadd_rn(S, -d), -xh);  // (S - xh) - d, exactly
   const float E = gmp_ex2(d);
   return __fmaf_rn(E, -0.69314718055994531f * __fadd_rn(xl, -e), E);
+}
+__device__ __forceinline__ float gmp_exp_neg_shifted(float Bhi, float Blo, float r2hi, float r2lo) {
+  return gmp_exp_neg_shifted_by(Bhi, Blo, r2hi, r2lo, GMP_EXP_SHIFT);
 }
 
 // exp(-x) for a double-float x to about 1e-13 relative, in FP32

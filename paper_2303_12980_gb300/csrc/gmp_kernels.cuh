@@ -1197,7 +1197,7 @@ __device__ __forceinline__ int64_t first_pair_of_row(const int32_t* __restrict__
 }
 
 template <int L, int NS>
-__global__ void __launch_bounds__(256) k_jacobian(KParams K) {
+__global__ void __maxnreg__(L >= 6 ? 168 : 128) k_jacobian(KParams K) {
   using SH = Shape<L, NS>;
   constexpr int G = 32 / NS;  // pair groups per warp
   constexpr int NO = L + 1;   // at most L + 1 orders >= 0 per pass
@@ -1225,6 +1225,21 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
     for (int t = lane; t < NS * SH::NIND; t += 32) Mu[t] = (t < P.nsig * SH::NIND) ? mrow[t] : 0.0f;
     __syncwarp();
     adjoints<L, NS>(P, Mu, nullptr, Lam);  // g = 1 per feature: lam = d f / d mu
+    // Exponent offset of this lane's radial factors (its sigma, this
+    // center): the largest S (at most 90, at least 32) that keeps the scaled
+    // intermediates below 2^126.  They are bounded by 2^S max|lam_s|
+    // 2^jac_exp[s] max(1, beta_s) 2^32 (jac_exp: the radial factors times
+    // max(1, r)^(L+1); MCSH values up to 2^15 r^(L+1) at order 7, 2l+1 terms
+    // and factors, 1/r^2 up to 2^8, the sums).  Large adjoints lift a far
+    // pair's row above 2^-126 even when its exponentials lie below 2^-158
+    // (the fixed offset of 32 alone).
+    float lm = 0.0f;
+    for (int t = 0; t < SH::NIND; ++t) lm = fmaxf(lm, fabsf(lam_s[t]));
+    const int le = ((__float_as_int(lm) >> 23) & 255) - 126;                 // > log2(lm)
+    const int lb = max(0, ((__float_as_int(-nb) >> 23) & 255) - 126);       // >= log2(beta)
+    const int Si = max(32, min(90, 94 - le - lb - P.jac_exp[s]));
+    const float shift = (float)Si;  // 2^-S is formed where a row is written
+    auto unshift_of = [](float s) { return __int_as_float((127 - (int)s) << 23); };
     const int64_t r0 = K.jac_off[i - K.center0];
     const int R = (int)(K.jac_off[i - K.center0 + 1] - r0);
     // the center's own row: the rank of atom i among its neighbor atoms
@@ -1254,9 +1269,10 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           constexpr int o = decltype(oo)::value;
           if (o < P.n_ord) {
             float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
-            dst[0] = acc[o][0] * GMP_EXP_UNSHIFT;
-            dst[1] = acc[o][1] * GMP_EXP_UNSHIFT;
-            dst[2] = acc[o][2] * GMP_EXP_UNSHIFT;
+            const float unshift = unshift_of(shift);
+            dst[0] = acc[o][0] * unshift;
+            dst[1] = acc[o][1] * unshift;
+            dst[2] = acc[o][2] * unshift;
           }
         });
       }
@@ -1289,7 +1305,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
         float S1[SH::NIND1];
         const float r2c = mcsh_r2(dx, dy, dz);
         GmpMcsh<L + 1>::eval(dx, dy, dz, r2c, S1);
-        // radial factors of this lane's sigma, orders 0..L+1, scaled by 2^32
+        // radial factors of this lane's sigma, orders 0..L+1, scaled by 2^S
         // (double-float exponent argument: a row of one neighbor averages no
         // other terms)
         float Rl[L + 2];
@@ -1298,7 +1314,7 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
         const float* tab_e = s_rad + (size_t)e * rad_elem_stride(L, NS, P.kmax, false);
         for (int q = 0; q < P.kmax; ++q) {
           const float* ent = tab_e + ((s / 4) * P.kmax + q) * gmp_rad_block(L) * 4 + (s % 4);
-          const float E = gmp_exp_neg_shifted(ent[0], ent[4], r2h, r2l);
+          const float E = gmp_exp_neg_shifted_by(ent[0], ent[4], r2h, r2l, shift);
 #pragma unroll
           for (int l = 0; l < L + 2; ++l) Rl[l] = __fmaf_rn(ent[4 * (2 + l)], E, Rl[l]);
         }
@@ -1374,9 +1390,10 @@ __global__ void __launch_bounds__(256) k_jacobian(KParams K) {
           constexpr int o = decltype(oo)::value;
           if (o < P.n_ord) {
             float* dst = K.jac + (row * P.F + P.ord_col[o] + s) * 3;
-            dst[0] = self[o][0] * GMP_EXP_UNSHIFT;
-            dst[1] = self[o][1] * GMP_EXP_UNSHIFT;
-            dst[2] = self[o][2] * GMP_EXP_UNSHIFT;
+            const float unshift = unshift_of(shift);
+            dst[0] = self[o][0] * unshift;
+            dst[1] = self[o][1] * unshift;
+            dst[2] = self[o][2] * unshift;
           }
         });
       }

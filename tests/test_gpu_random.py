@@ -233,3 +233,75 @@ def test_random_tables_chunks_and_graph_replay(torch, oracle_mod, seed):
             s.synchronize()
             assert torch.equal(fo, fe), step
             assert torch.equal(go, ge), step
+
+
+def _dense_structure(rng, nmax, jitter=0.0):
+    """2..nmax atoms at 0.04-0.09 atoms/A^3 in a skewed cell plus Gaussian
+    jitter of std `jitter` (closer than 0.7 A dropped), random periodic
+    axes, moved by up to 30 A."""
+    n = int(rng.integers(2, nmax))
+    pbc = rng.integers(0, 2, 3).astype(np.uint8)
+    L = (n / rng.uniform(0.04, 0.09)) ** (1 / 3) * np.exp(rng.uniform(-0.3, 0.3, 3))
+    cell = np.diag(L)
+    cell[1, 0], cell[2, 0], cell[2, 1] = rng.uniform(-0.25, 0.25, 3) * L[[1, 2, 2]]
+    pos = rng.uniform(0, 1, (n, 3)) @ cell + rng.normal(0.0, jitter, (n, 3))
+    keep = [0]
+    for a in range(1, n):
+        if all(np.linalg.norm(pos[a] - pos[b]) > 0.7 for b in keep):
+            keep.append(a)
+    return pos[keep] + rng.uniform(-30, 30, 3), rng.integers(0, 4, len(keep)).astype(np.int32), cell, pbc
+
+
+@pytest.mark.parametrize("seed", [101, 106, 114, 119, 124])
+def test_random_dense_structures(torch, oracle_mod, seed):
+    """1-4 structures of up to 300 atoms at liquid-like densities, 1-4
+    elements, random order subsets in random column order, 1-24 sigmas from
+    0.05-0.2 to 0.5-2 A, cutoff 4-9 A: features, VJP, strain derivatives,
+    features at random points and Jacobian rows of sampled centers against
+    the oracle.  Seeds 106 and 119 have Jacobian rows of far pairs that the
+    center's large adjoints lift above 2^-126 while their exponentials lie
+    below 2^-158 (the per-lane exponent offset of the Jacobian kernel)."""
+    rng = np.random.default_rng(seed)
+    n_el = int(rng.integers(1, 5))
+    parts = [_dense_structure(rng, int(rng.integers(3, 300))) for _ in range(int(rng.integers(1, 5)))]
+    n_gauss, coef, expo = synth.gaussian_table(rng, list(rng.integers(1, 9, n_el)), int(rng.integers(1, 7)))
+    orders = rng.choice(np.arange(-1, 7), int(rng.integers(1, 9)), replace=False).tolist()
+    sig = np.geomspace(rng.uniform(0.05, 0.2), rng.uniform(0.5, 2.0), int(rng.integers(1, 25))).tolist()
+    w = synth.Workload(
+        name="dense", positions=np.ascontiguousarray(np.concatenate([p for p, _, _, _ in parts])),
+        cells=np.stack([c for _, _, c, _ in parts]), pbc=np.stack([b for _, _, _, b in parts]),
+        atom_off=np.concatenate([[0], np.cumsum([len(p) for p, _, _, _ in parts])]).astype(np.int64),
+        species=np.concatenate([s % n_el for _, s, _, _ in parts]).astype(np.int32), n_gauss=n_gauss,
+        gauss_coef=coef, gauss_exp=expo, orders=[int(o) for o in orders], sigmas=sig,
+        cutoff=float(rng.uniform(4.0, 9.0)))
+    from paper_2303_12980_gb300.binding import GMPFeaturizer
+    F = GMPFeaturizer.from_workload(w)
+    pos = torch.from_numpy(w.positions).cuda()
+    sp = torch.from_numpy(w.species).cuda()
+    g = torch.from_numpy(synth.upstream_gradient(w.n_atoms, w.n_features, seed=seed)).cuda()
+    feat, gp, vir = F.featurize_vjp_virial(pos, sp, w.atom_off, w.cells, w.pbc, g)
+    pts = np.concatenate([w.positions[w.atom_off[t]:w.atom_off[t + 1]].mean(0) + rng.uniform(-8, 8, (4, 3))
+                          for t in range(w.n_struct)])
+    poff = np.arange(0, 4 * w.n_struct + 1, 4, dtype=np.int64)
+    fp = F.featurize_points(pos, sp, w.atom_off, w.cells, w.pbc, torch.from_numpy(pts).cuda(), poff)
+    _, jo, jj, jac = (t.cpu().numpy() for t in F.featurize_grad(pos, sp, w.atom_off, w.cells, w.pbc))
+    torch.cuda.synchronize()
+    ref, fabs = oracle_mod.features(w, want_abs=True)
+    assert feature_errors(feat.cpu().numpy(), ref, fabs).max() <= FEAT_TOL
+    atoms = rng.choice(w.n_atoms, min(32, w.n_atoms), replace=False)
+    gref, gscale = oracle_mod.vjp_atoms(w, g.cpu().numpy(), atoms, want_abs=True)
+    assert grad_errors(gp.cpu().numpy()[atoms], gref, gscale).max() <= GRAD_TOL
+    W, Wa = oracle_mod.virial(w, g.cpu().numpy().astype(np.float64), want_abs=True)
+    verr = np.abs(vir.cpu().numpy() - W) / np.maximum(np.maximum(np.abs(W), GRAD_TAU * Wa), 2.0 ** -126)
+    assert verr.max() <= GRAD_TOL, verr.max()
+    pref, pabs = oracle_mod.point_features(w, pts, np.repeat(np.arange(w.n_struct), 4), want_abs=True)
+    assert feature_errors(fp.cpu().numpy(), pref, pabs).max() <= FEAT_TOL
+    centers = np.sort(rng.choice(w.n_atoms, min(12, w.n_atoms), replace=False))
+    if seed == 119:
+        centers = np.arange(w.n_atoms)  # the far rows are spread over the centers
+    co, cj, cjac, cabs = oracle_mod.jacobian_rows(w, centers, want_abs=True)
+    for t, i in enumerate(centers):
+        a, b = jo[i], jo[i + 1]
+        assert np.array_equal(jj[a:b], cj[co[t]:co[t + 1]])
+        jerr = grad_errors(jac[a:b], cjac[co[t]:co[t + 1]], cabs[co[t]:co[t + 1]], tau=JAC_TAU)
+        assert jerr.max() <= GRAD_TOL, (i, jerr.max())
