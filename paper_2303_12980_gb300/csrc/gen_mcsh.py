@@ -300,7 +300,7 @@ def emit_feature_df(l):
              "  gmp_f2 f{0.0f, 0.0f};"]
     for t in all_components(l):
         lines.append(f"  {{ const gmp_f2 m = {combo_expr(T_[t])}; "
-                     f"f = gmp_df_add(gmp_df_mul_f(gmp_df_mul(m, m), {fnum(weight(*t))}), f); }}")
+                     f"f = gmp_df_add(gmp_df_mul(gmp_df_mul_f(m, {fnum(weight(*t))}), m), f); }}")
     lines += ["  return f;", "}"]
     return "\n".join(lines)
 
@@ -330,7 +330,9 @@ def emit_feature(l, dtype="float"):
     lines = [f"__device__ __forceinline__ {T} gmp_mcsh_invariant{sfx}_{l}(const {T}* __restrict__ mu) {{",
              f"  {T} f = {lit(0)};"]
     for t in all_components(l):
-        lines.append(f"  {{ const {T} m = {combo_expr(T_[t])}; f = {fma}({lit(weight(*t))}, {mul}(m, m), f); }}")
+        # (w m) m + f: one rounding where m^2 would be subnormal, instead of
+        # w times a rounded subnormal square
+        lines.append(f"  {{ const {T} m = {combo_expr(T_[t])}; f = {fma}({mul}({lit(weight(*t))}, m), m, f); }}")
     lines += ["  return f;", "}"]
     if d:
         return "\n".join(lines)

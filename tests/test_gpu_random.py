@@ -252,21 +252,26 @@ def _dense_structure(rng, nmax, jitter=0.0):
     return pos[keep] + rng.uniform(-30, 30, 3), rng.integers(0, 4, len(keep)).astype(np.int32), cell, pbc
 
 
-@pytest.mark.parametrize("seed", [101, 106, 114, 119, 124])
-def test_random_dense_structures(torch, oracle_mod, seed):
-    """1-4 structures of up to 300 atoms at liquid-like densities, 1-4
-    elements, random order subsets in random column order, 1-24 sigmas from
-    0.05-0.2 to 0.5-2 A, cutoff 4-9 A: features, VJP, strain derivatives,
-    features at random points and Jacobian rows of sampled centers against
-    the oracle.  Seeds 106 and 119 have Jacobian rows of far pairs that the
-    center's large adjoints lift above 2^-126 while their exponentials lie
-    below 2^-158 (the per-lane exponent offset of the Jacobian kernel)."""
+@pytest.mark.parametrize("seed,many_sigmas", [(101, False), (106, False), (114, False), (119, False),
+                                              (124, False), (201, True), (209, True), (213, True)])
+def test_random_dense_structures(torch, oracle_mod, seed, many_sigmas):
+    """1-4 structures of up to 300 atoms at liquid-like densities (or, with
+    many sigmas, 1-3 of up to 120 atoms and 25-60 sigmas: two to four
+    16-sigma passes), 1-4 elements, random order subsets in random column
+    order, 1-24 sigmas from 0.05-0.2 to 0.5-2 A, cutoff 4-9 A: features, VJP,
+    strain derivatives, features at random points and Jacobian rows of
+    sampled centers against the oracle.  Seeds 106 and 119 have Jacobian
+    rows of far pairs that the center's large adjoints lift above 2^-126
+    while their exponentials lie below 2^-158 (the per-lane exponent offset
+    of the Jacobian kernel); seed 213 has subnormal features at a point far
+    from every atom (the invariant's products are ordered (w m) m)."""
     rng = np.random.default_rng(seed)
     n_el = int(rng.integers(1, 5))
-    parts = [_dense_structure(rng, int(rng.integers(3, 300))) for _ in range(int(rng.integers(1, 5)))]
+    nmax, nst, ns = (120, 4, (25, 61)) if many_sigmas else (300, 5, (1, 25))
+    parts = [_dense_structure(rng, int(rng.integers(3, nmax))) for _ in range(int(rng.integers(1, nst)))]
     n_gauss, coef, expo = synth.gaussian_table(rng, list(rng.integers(1, 9, n_el)), int(rng.integers(1, 7)))
     orders = rng.choice(np.arange(-1, 7), int(rng.integers(1, 9)), replace=False).tolist()
-    sig = np.geomspace(rng.uniform(0.05, 0.2), rng.uniform(0.5, 2.0), int(rng.integers(1, 25))).tolist()
+    sig = np.geomspace(rng.uniform(0.05, 0.2), rng.uniform(0.5, 2.0), int(rng.integers(*ns))).tolist()
     w = synth.Workload(
         name="dense", positions=np.ascontiguousarray(np.concatenate([p for p, _, _, _ in parts])),
         cells=np.stack([c for _, _, c, _ in parts]), pbc=np.stack([b for _, _, _, b in parts]),
