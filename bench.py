@@ -115,8 +115,8 @@ def work_model(w, pairs: int):
 # dram__bytes_read.sum + dram__bytes_write.sum over its 4,585,082 pairs),
 # scaled by the pairs of the run.  Update with the ncu summaries whenever
 # the kernels change.
-TRAFFIC_PER_PAIR = {"forward": (147.323648e6 + 78.938368e6) / 4585082,
-                    "backward": (272.870400e6 + 6.337536e6) / 4585082}
+TRAFFIC_PER_PAIR = {"forward": (147.334656e6 + 79.260672e6) / 4585082,
+                    "backward": (272.902656e6 + 6.698496e6) / 4585082}
 
 
 # ------------------------------------------------------------------ our arm
