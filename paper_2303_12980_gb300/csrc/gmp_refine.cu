@@ -185,6 +185,12 @@ cudaError_t gmp_launch_refine(const GmpRefine& A, unsigned order_mask, int sm_co
     const cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernels[l], 256, 0);
     if (eo != cudaSuccess) return eo;
     if (per_sm < 1) per_sm = 1;
+    // order 6: one CTA (8 warps) per SM.  Its pair loop is bound by
+    // instruction fetch, and fewer warps at different points of that code
+    // fetch less: perfect FCC 262k refinement 21.5 -> 20.4 ms against two
+    // CTAs (12 warps in two 6-warp CTAs: 22.9 ms; 4 warps: 30.6 ms; one CTA
+    // per SM for orders 4 and 5 as well: 21.3 ms)
+    if (l == 6) per_sm = 1;
     kernels[l]<<<(unsigned)(sm_count * per_sm), 256, 0, stream>>>(A);
     ++*launches;
     const cudaError_t e = cudaGetLastError();
